@@ -1,0 +1,194 @@
+"""Seeded synthetic graph generators shared by the tests, the bench and the oracle.
+
+This module only produces inputs: symmetric CSR graphs with integer weights
+(rows sorted ascending, duplicates merged, each undirected edge stored in both
+rows, a self-loop stored once).  It holds none of the community-detection
+arithmetic, so both the CUDA path and the serial oracle may consume what it
+makes.
+
+The heavy lifting is in ``graphgen.c`` (built with gcc by :func:`build`).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_LIB = os.path.join(_HERE, "libgraphgen.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``libgraphgen.so`` next to the source (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-shared",
+                               "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        vp = ctypes.c_void_p
+        i64, i32, f64, u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
+        lib.gg_planted.restype = vp
+        lib.gg_planted.argtypes = [i64, i32, f64, f64, i32, i32, u64]
+        lib.gg_rmat.restype = vp
+        lib.gg_rmat.argtypes = [i32, i64, f64, f64, f64, u64]
+        lib.gg_chunglu.restype = vp
+        lib.gg_chunglu.argtypes = [i64, f64, f64, i64, f64, u64]
+        lib.gg_from_edges.restype = vp
+        lib.gg_from_edges.argtypes = [i64, i64, vp, vp, vp]
+        lib.gg_size.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.gg_stats.argtypes = [vp] + [ctypes.POINTER(i64)] * 3
+        lib.gg_copy.argtypes = [vp, vp, vp, vp]
+        lib.gg_free.argtypes = [vp]
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Graph:
+    """Symmetric CSR: ``rowptr`` int64[n+1], ``col`` int32[arcs], ``w`` int32[arcs]."""
+
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    w: np.ndarray
+    name: str = ""
+    stats: dict = field(default_factory=dict)
+
+    @property
+    def arcs(self) -> int:
+        return int(self.rowptr[-1])
+
+    @property
+    def two_m(self) -> int:
+        return int(self.w.astype(np.int64).sum())
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.rowptr)
+
+
+def _take(h, name: str) -> Graph:
+    if not h:
+        raise ValueError(f"generator {name}: invalid arguments")
+    lib = _load()
+    n, a = ctypes.c_int64(), ctypes.c_int64()
+    lib.gg_size(h, ctypes.byref(n), ctypes.byref(a))
+    rowptr = np.empty(n.value + 1, dtype=np.int64)
+    col = np.empty(max(a.value, 0), dtype=np.int32)
+    w = np.empty(max(a.value, 0), dtype=np.int32)
+    lib.gg_copy(h, rowptr.ctypes.data, col.ctypes.data, w.ctypes.data)
+    d, s, m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    lib.gg_stats(h, ctypes.byref(d), ctypes.byref(s), ctypes.byref(m))
+    lib.gg_free(h)
+    return Graph(int(n.value), rowptr, col, w, name,
+                 {"draws": d.value, "self_draws": s.value, "dup_merged": m.value})
+
+
+def planted(n: int, blocks: int, p_in: float, p_out: float, wmin: int = 1, wmax: int = 1,
+            seed: int = 1) -> Graph:
+    """Planted partition: ``blocks`` contiguous near-equal blocks, independent
+    pairs with probability ``p_in`` inside a block and ``p_out`` across."""
+    lib = _load()
+    return _take(lib.gg_planted(n, blocks, p_in, p_out, wmin, wmax, seed),
+                 f"planted(n={n},B={blocks},seed={seed})")
+
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         seed: int = 2) -> Graph:
+    """R-MAT with ``edge_factor * 2**scale`` draws; self draws dropped,
+    duplicates merged into integer weights (multiplicity)."""
+    lib = _load()
+    draws = edge_factor * (1 << scale)
+    return _take(lib.gg_rmat(scale, draws, a, b, c, seed), f"rmat(scale={scale},seed={seed})")
+
+
+def chunglu(n: int, gamma: float = 2.1, core_frac: float = 0.7, edges: int = 250_000_000,
+            dmax: float = 1.0e5, seed: int = 3) -> Graph:
+    """Chung-Lu power-law core plus pendant (degree-1) layer, ids shuffled."""
+    lib = _load()
+    return _take(lib.gg_chunglu(n, gamma, core_frac, edges, dmax, seed),
+                 f"chunglu(n={n},seed={seed})")
+
+
+def from_edges(n: int, edges, name: str = "") -> Graph:
+    """CSR from an undirected edge list of (u, v) or (u, v, w) tuples.
+    Duplicate edges are summed; (u, u) is a self-loop stored once."""
+    lib = _load()
+    rows = [tuple(e) if len(e) == 3 else (e[0], e[1], 1) for e in edges]
+    if not rows:
+        return _empty(n)
+    arr = np.asarray(rows, dtype=np.int64)
+    u = np.ascontiguousarray(arr[:, 0], dtype=np.int32)
+    v = np.ascontiguousarray(arr[:, 1], dtype=np.int32)
+    w = np.ascontiguousarray(arr[:, 2], dtype=np.int32)
+    h = lib.gg_from_edges(n, len(u), u.ctypes.data, v.ctypes.data, w.ctypes.data)
+    return _take(h, name or f"edges(n={n})")
+
+
+def random_graph(n: int, p: float, wmax: int = 1, loops: float = 0.0, seed: int = 0) -> Graph:
+    """Small Erdos-Renyi-style test graph with weights in [1, wmax] and each
+    vertex given a self-loop with probability ``loops`` (numpy generator)."""
+    rng = np.random.default_rng(seed)
+    iu, ju = np.triu_indices(n, k=1)
+    keep = rng.random(iu.shape[0]) < p
+    iu, ju = iu[keep], ju[keep]
+    ww = rng.integers(1, wmax + 1, size=iu.shape[0])
+    edges = list(zip(iu.tolist(), ju.tolist(), ww.tolist()))
+    if loops > 0:
+        for v in np.nonzero(rng.random(n) < loops)[0].tolist():
+            edges.append((v, v, int(rng.integers(1, wmax + 1))))
+    if not edges:
+        return _empty(n)
+    return from_edges(n, edges, name=f"random(n={n},p={p},seed={seed})")
+
+
+def _empty(n: int) -> Graph:
+    return Graph(n, np.zeros(n + 1, dtype=np.int64), np.zeros(0, dtype=np.int32),
+                 np.zeros(0, dtype=np.int32), f"empty(n={n})")
+
+
+# ----------------------------------------------------------------------------
+# Named workloads.  Each entry gives the generator recipe and the heuristic
+# switches it is run with (vertex following, colouring, threshold schedule).
+# ----------------------------------------------------------------------------
+WORKLOADS = {
+    # 1,000 vertices in 10 blocks of 100, p_in 0.1, p_out 0.002, weight 1
+    "planted1k": dict(gen=lambda: planted(1000, 10, 0.1, 0.002, 1, 1, seed=1),
+                      params=dict(vertex_following=1, coloring=0, theta_low=1e-6,
+                                  theta_high=0.0, color_cutoff=100_000)),
+    # R-MAT scale 20, edge factor 16, (0.57, 0.19, 0.19, 0.05)
+    "rmat20": dict(gen=lambda: rmat(20, 16, 0.57, 0.19, 0.19, seed=2),
+                   params=dict(vertex_following=1, coloring=1, theta_low=1e-6,
+                               theta_high=1e-2, color_cutoff=100_000)),
+    # Chung-Lu, 2^24 vertices, exponent 2.1, 30% pendant, ~2.5e8 edges
+    "chunglu24": dict(gen=lambda: chunglu(1 << 24, 2.1, 0.7, 250_000_000, 1.0e5, seed=3),
+                      params=dict(vertex_following=1, coloring=1, theta_low=1e-6,
+                                  theta_high=1e-2, color_cutoff=100_000)),
+    # smaller members of the same families, for parity tests and ncu captures
+    "rmat16": dict(gen=lambda: rmat(16, 16, 0.57, 0.19, 0.19, seed=2),
+                   params=dict(vertex_following=1, coloring=1, theta_low=1e-6,
+                               theta_high=1e-2, color_cutoff=10_000)),
+    "chunglu20": dict(gen=lambda: chunglu(1 << 20, 2.1, 0.7, 15_000_000, 1.0e4, seed=3),
+                      params=dict(vertex_following=1, coloring=1, theta_low=1e-6,
+                                  theta_high=1e-2, color_cutoff=100_000)),
+}
+
+
+def workload(name: str):
+    """Return (Graph, run-parameter dict) for a named workload."""
+    wl = WORKLOADS[name]
+    g = wl["gen"]()
+    g.name = name
+    return g, dict(wl["params"])

@@ -1,0 +1,424 @@
+"""Pins of the serial oracle against what the paper and the mathematics fix.
+
+Each test ties one part of the oracle to something other than itself: closed
+forms of Eq. 3 evaluated by hand (tests/golden), the exact change of the
+modularity numerator under single and paired moves (Eqs. 4 and 6), the
+worked minimum-label cases of Sec. 4.1, the vertex-following lemma of
+Sec. 4.3, brute-force optima on graphs of at most 10 vertices, an
+independent colouring routine, and structural invariants.
+"""
+import itertools
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+GOLDEN_Q = ["two_triangles.txt", "two_k5.txt", "ring3_triangles.txt"]
+
+
+def _g(fx):
+    return gg.from_edges(fx["n"], fx["edges"])
+
+
+# ------------------------------------------------------------------ Eq. 3
+@pytest.mark.parametrize("name", GOLDEN_Q)
+def test_q_closed_form(golden, name):
+    fx = golden(name)
+    g = _g(fx)
+    assert oracle.modularity(g.rowptr, g.col, g.w, fx["partition"]) == fx["q"]
+
+
+@pytest.mark.parametrize("r,s", [(3, 3), (4, 3), (5, 4), (6, 5), (3, 6)])
+def test_q_ring_of_cliques(r, s):
+    # ring of r cliques K_s joined by single edges; partition = the cliques:
+    # Q = l/(l+1) - 1/r with l = s(s-1)/2 (each clique has l edges plus one
+    # ring edge per clique), evaluated from Eq. 3 by hand
+    edges = []
+    for b in range(r):
+        base = b * s
+        edges += [(base + i, base + j) for i in range(s) for j in range(i + 1, s)]
+        edges.append((base + s - 1, ((b + 1) % r) * s))
+    g = gg.from_edges(r * s, edges)
+    part = [v // s for v in range(r * s)]
+    l = s * (s - 1) // 2
+    assert oracle.modularity(g.rowptr, g.col, g.w, part) == Fraction(l, l + 1) - Fraction(1, r)
+
+
+def test_q_singletons_and_single_community():
+    g = gg.random_graph(30, 0.2, wmax=5, loops=0.3, seed=4)
+    k = np.add.reduceat(g.w.astype(np.int64), g.rowptr[:-1]) if g.arcs else np.zeros(g.n)
+    k = np.array([g.w[g.rowptr[i]:g.rowptr[i + 1]].sum() for i in range(g.n)], dtype=np.int64)
+    loops = sum(int(g.w[e]) for i in range(g.n) for e in range(g.rowptr[i], g.rowptr[i + 1])
+                if g.col[e] == i)
+    two_m = int(k.sum())
+    # singletons: N = 2m * (sum of self-loops) - sum k_i^2
+    N, tm = oracle.modularity_num(g.rowptr, g.col, g.w, np.arange(g.n))
+    assert tm == two_m
+    assert N == two_m * loops - int((k * k).sum())
+    # one community: every arc is intra, a = 2m, N = 2m*2m - (2m)^2 = 0
+    N1, _ = oracle.modularity_num(g.rowptr, g.col, g.w, np.zeros(g.n))
+    assert N1 == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_q_bounds(seed):
+    rng = np.random.default_rng(seed)
+    g = gg.random_graph(25, 0.25, wmax=9, loops=0.2, seed=seed)
+    for _ in range(20):
+        lab = rng.integers(0, rng.integers(1, 26), size=g.n)
+        q = oracle.modularity(g.rowptr, g.col, g.w, lab)
+        assert Fraction(-1, 2) <= q < 1
+
+
+# ------------------------------------------------------------------ Eq. 4
+def _move(lab, i, c):
+    lab = np.array(lab, dtype=np.int32)
+    lab[i] = c
+    return lab
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_gain_is_half_the_numerator_change(seed):
+    # Moving i alone from C(i) to c changes N = (2m)^2 Q by exactly 2G, G the
+    # scaled gain of Eq. 4.  A dropped term, a wrong sign or a self-loop
+    # counted in e_{i->C} breaks this identity.
+    rng = np.random.default_rng(100 + seed)
+    g = gg.random_graph(18, 0.3, wmax=7, loops=0.4, seed=seed)
+    for _ in range(40):
+        lab = rng.integers(0, 6, size=g.n).astype(np.int32)
+        i = int(rng.integers(0, g.n))
+        c = int(rng.integers(0, g.n))
+        if c == lab[i]:
+            continue
+        G = oracle.gain(g.rowptr, g.col, g.w, lab, i, c)
+        N0, tm = oracle.modularity_num(g.rowptr, g.col, g.w, lab)
+        N1, _ = oracle.modularity_num(g.rowptr, g.col, g.w, _move(lab, i, c))
+        assert N1 - N0 == 2 * G
+        # and the same gain in the paper's own scaling (Eq. 4)
+        m = Fraction(tm, 2)
+        k = [int(g.w[g.rowptr[v]:g.rowptr[v + 1]].sum()) for v in range(g.n)]
+        row = range(g.rowptr[i], g.rowptr[i + 1])
+        e_c = sum(int(g.w[e]) for e in row if g.col[e] != i and lab[g.col[e]] == c)
+        e_o = sum(int(g.w[e]) for e in row if g.col[e] != i and lab[g.col[e]] == lab[i])
+        a_c = sum(k[v] for v in range(g.n) if lab[v] == c)
+        a_o = sum(k[v] for v in range(g.n) if lab[v] == lab[i]) - k[i]
+        dq = Fraction(e_c - e_o) / m + Fraction(2 * k[i] * a_o - 2 * k[i] * a_c) / (2 * m) ** 2
+        assert dq == Fraction(2 * G, tm * tm)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_two_movers_eq6(seed):
+    # Eq. 6 (negative-gain scenario): i and j, in two different communities,
+    # both move to a third community C(k).  Scaled by (2m)^2:
+    #   dN_ij = 2G_i + 2G_j + 2 (2m w(i,j) - k_i k_j)
+    rng = np.random.default_rng(200 + seed)
+    g = gg.random_graph(16, 0.35, wmax=5, loops=0.3, seed=50 + seed)
+    k = [int(g.w[g.rowptr[v]:g.rowptr[v + 1]].sum()) for v in range(g.n)]
+    wmap = {}
+    for u in range(g.n):
+        for e in range(g.rowptr[u], g.rowptr[u + 1]):
+            wmap[(u, int(g.col[e]))] = int(g.w[e])
+    checked = 0
+    for _ in range(200):
+        lab = rng.integers(0, 5, size=g.n).astype(np.int32)
+        i, j = (int(x) for x in rng.choice(g.n, size=2, replace=False))
+        c = int(rng.integers(0, 5))
+        if len({int(lab[i]), int(lab[j]), c}) < 3:
+            continue
+        Gi = oracle.gain(g.rowptr, g.col, g.w, lab, i, c)
+        Gj = oracle.gain(g.rowptr, g.col, g.w, lab, j, c)
+        N0, tm = oracle.modularity_num(g.rowptr, g.col, g.w, lab)
+        lab2 = _move(_move(lab, i, c), j, c)
+        N2, _ = oracle.modularity_num(g.rowptr, g.col, g.w, lab2)
+        assert N2 - N0 == 2 * Gi + 2 * Gj + 2 * (tm * wmap.get((i, j), 0) - k[i] * k[j])
+        checked += 1
+    assert checked > 20
+
+
+# --------------------------------------------------------- Sec. 4.1 cases
+def test_k2_singlet_rule(golden):
+    fx = golden("k2_singlet.txt")
+    g = _g(fx)
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0, trace=1)
+    p0 = r.phases[0]
+    assert list(p0.iter_labels[0]) == fx["iter1"]
+    assert Fraction(p0.N_start, p0.two_m ** 2) == fx["q_start"]
+    assert Fraction(r.phases[-1].N_end, r.two_m ** 2) == fx["q"]
+
+
+def test_k4_generalised_min_label(golden):
+    fx = golden("k4_minlabel.txt")
+    g = _g(fx)
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0, trace=1)
+    assert list(r.phases[0].iter_labels[0]) == fx["iter1"]
+    assert Fraction(r.phases[-1].N_end, r.two_m ** 2) == fx["q"]
+
+
+def test_star_vertex_following(golden):
+    fx = golden("star_vf.txt")
+    g = _g(fx)
+    (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+    assert len(rp) - 1 == fx["vf_n"]
+    assert list(col) == [0] and list(w) == [fx["vf_loop"]]
+    assert list(m) == [0] * 6
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0)
+    assert r.vf_n == 1
+    assert Fraction(r.phases[-1].N_end, r.two_m ** 2) == fx["q"]
+
+
+def test_swap_without_singlet_rule_would_oscillate():
+    # Sec. 3.2: two singletons joined by an edge would swap forever without
+    # the rule; with it the pair merges in one iteration and then stops.
+    g = gg.from_edges(2, [(0, 1, 3)])
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0)
+    assert r.phases[0].iterations == 2  # one move, then a no-move iteration
+    assert list(r.final_labels) == [0, 0]
+
+
+# ------------------------------------------------------------ Sec. 4.3 VF
+def test_vf_cases():
+    # path 0-1-2-3: ends merge into 1 and 2, each gets self-loop 2
+    g = gg.from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+    assert list(rp) == [0, 2, 4] and list(col) == [0, 1, 0, 1] and list(w) == [2, 1, 1, 2]
+    assert list(m) == [0, 0, 1, 1]
+    # isolated edge: only the smaller id merges (R3); plus a triangle
+    g = gg.from_edges(5, [(0, 1, 4), (2, 3), (3, 4), (2, 4)])
+    (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+    assert list(m) == [0, 0, 1, 2, 3]
+    assert list(col[rp[0]:rp[1]]) == [0] and list(w[rp[0]:rp[1]]) == [8]
+    # a degree-one vertex with a self-loop has two entries and is kept
+    g = gg.from_edges(3, [(0, 0, 2), (0, 1), (1, 2)])
+    (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+    assert len(rp) - 1 == 2 and list(m) == [0, 1, 1]
+    # 2m is preserved
+    for seed in range(4):
+        g = gg.chunglu(2000, 2.1, 0.7, 6000, 50.0, seed=seed)
+        (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+        assert int(w.astype(np.int64).sum()) == g.two_m
+        assert oracle.validate(rp, col, w)[0] == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_vf_preserves_modularity_of_expanded_partition(seed):
+    # VF is an exact coarsening (R2): Q of any partition of G' equals Q of the
+    # partition of G obtained through the VF map.
+    rng = np.random.default_rng(seed)
+    g = gg.chunglu(300, 2.1, 0.7, 700, 30.0, seed=seed)
+    (rp, col, w), m = oracle.vertex_following(g.rowptr, g.col, g.w)
+    for _ in range(10):
+        lab = rng.integers(0, 12, size=len(rp) - 1).astype(np.int32)
+        assert oracle.modularity(rp, col, w, lab) == oracle.modularity(g.rowptr, g.col, g.w,
+                                                                      lab[m])
+
+
+def test_lemma3_fixed_point():
+    # Lemma 3: at a no-move fixed point, a single-degree vertex i shares its
+    # neighbour's community unless the singlet rule blocks the move (both
+    # singletons and the neighbour's label larger).
+    hits = 0
+    for seed in range(6):
+        g = gg.chunglu(400, 2.1, 0.75, 1500, 40.0, seed=seed)
+        r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=1, color_cutoff=0,
+                       theta_high=0.0, theta_low=-1e300, max_phases=1, max_iters=500, trace=1)
+        p = r.phases[0]
+        if r.iters[-1][2] != 0:
+            continue  # did not reach a fixed point
+        C = p.iter_labels[-1]
+        size = np.bincount(C, minlength=g.n)
+        for i in range(g.n):
+            if g.rowptr[i + 1] - g.rowptr[i] == 1 and g.col[g.rowptr[i]] != i:
+                j = int(g.col[g.rowptr[i]])
+                if C[i] != C[j]:
+                    assert size[C[i]] == 1 and size[C[j]] == 1 and C[j] > C[i]
+                hits += 1
+    assert hits > 50
+
+
+# ------------------------------------------------------- brute force n<=10
+def _set_partitions(n):
+    # restricted growth strings
+    a = [0] * n
+
+    def rec(i, mx):
+        if i == n:
+            yield list(a)
+            return
+        for v in range(mx + 2):
+            a[i] = v
+            yield from rec(i + 1, max(mx, v))
+    if n == 0:
+        yield []
+        return
+    a[0] = 0
+    yield from rec(1, 0)
+
+
+def _brute_best_q(g):
+    P = np.array(list(_set_partitions(g.n)), dtype=np.int64)
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    k = np.bincount(src, weights=g.w, minlength=g.n).astype(np.int64)
+    two_m = int(k.sum())
+    intra = (P[:, src] == P[:, g.col]).astype(np.int64) @ g.w.astype(np.int64)
+    onehot = np.zeros((P.shape[0], g.n), dtype=np.int64)
+    for v in range(g.n):
+        onehot[np.arange(P.shape[0]), P[:, v]] += k[v]
+    N = two_m * intra - (onehot ** 2).sum(axis=1)
+    best = int(N.max())
+    return Fraction(best, two_m * two_m), P[int(N.argmax())]
+
+
+@pytest.mark.parametrize("name", GOLDEN_Q)
+def test_bruteforce_optimum_worked_cases(golden, name):
+    fx = golden(name)
+    g = _g(fx)
+    best, _ = _brute_best_q(g)
+    assert best == fx["q"]  # the hand partition is optimal
+    for vf, col in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        r = oracle.run(g.rowptr, g.col, g.w, vertex_following=vf, coloring=col, color_cutoff=0)
+        q = Fraction(r.phases[-1].N_end, r.two_m ** 2)
+        assert q <= best
+        assert q == best, (vf, col, q)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_bruteforce_upper_bound(seed):
+    n = 6 + seed % 4
+    g = gg.random_graph(n, 0.45, wmax=4, loops=0.2, seed=300 + seed)
+    if g.two_m == 0:
+        return
+    best, _ = _brute_best_q(g)
+    for vf, col in [(0, 0), (1, 1)]:
+        r = oracle.run(g.rowptr, g.col, g.w, vertex_following=vf, coloring=col, color_cutoff=0)
+        assert Fraction(r.phases[-1].N_end, r.two_m ** 2) <= best
+
+
+# ------------------------------------------------------------- invariants
+def _independent_greedy_colouring(g, seed):
+    # Plain restatement in Python: decreasing (h(v^seed), v), smallest free colour.
+    M = (1 << 64) - 1
+
+    def h(x):
+        x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M
+        x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M
+        return x ^ (x >> 31)
+    order = sorted(range(g.n), key=lambda v: (h(v ^ seed), v), reverse=True)
+    col = [-1] * g.n
+    for v in order:
+        used = {col[u] for u in g.col[g.rowptr[v]:g.rowptr[v + 1]] if u != v and col[u] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[v] = c
+    return col
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_colouring_matches_independent_greedy(seed):
+    g = gg.rmat(9, 8, seed=seed)
+    K, c = oracle.color(g.rowptr, g.col, 77 + seed)
+    ref = _independent_greedy_colouring(g, 77 + seed)
+    assert list(c) == ref and K == max(ref) + 1
+    src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    off = src != g.col
+    assert np.all(c[src[off]] != c[g.col[off]])  # proper
+
+
+@pytest.mark.parametrize("wl", ["planted1k", "rmat_small", "chunglu_small"])
+def test_phase_invariants(wl):
+    if wl == "planted1k":
+        g, prm = gg.workload("planted1k")
+    elif wl == "rmat_small":
+        g = gg.rmat(12, 8, seed=5)
+        prm = dict(vertex_following=1, coloring=1, theta_low=1e-6, theta_high=1e-2,
+                   color_cutoff=500)
+    else:
+        g = gg.chunglu(5000, 2.1, 0.7, 20000, 200.0, seed=6)
+        prm = dict(vertex_following=1, coloring=1, theta_low=1e-6, theta_high=1e-2,
+                   color_cutoff=1000)
+    r = oracle.run(g.rowptr, g.col, g.w, trace=1, **prm)
+    assert r.two_m == g.two_m
+    prev_end = None
+    for pi, p in enumerate(r.phases):
+        rp, col, w = p.graph
+        assert oracle.validate(rp, col, w) == (0, g.two_m)  # m preserved, CSR valid
+        if prev_end is not None:
+            assert p.N_start == prev_end  # singleton Q of G_{p+1} == final Q of G_p
+        for lab in p.iter_labels:
+            assert lab.min() >= 0 and lab.max() < p.n
+        # labels of original vertices: valid partition into n_next communities
+        assert set(np.unique(p.labels)) == set(range(p.n_next))
+        # Q on the phase graph equals Q of the composed labels on the input graph
+        N, _ = oracle.modularity_num(g.rowptr, g.col, g.w, p.labels)
+        assert N == p.N_end
+        assert -0.5 <= p.q < 1
+        if p.colored:
+            assert list(p.colors) == _independent_greedy_colouring(
+                type(g)(p.n, rp, col, w), 0x5EED + pi)
+        prev_end = p.N_end
+    # recorded per-iteration numerators are the modularity of the labels
+    for ph, it, moved, N, _ in r.iters:
+        p = r.phases[ph]
+        Nchk, _ = oracle.modularity_num(*p.graph, p.iter_labels[it - 1])
+        assert Nchk == N
+
+
+def test_rebuild_matches_definition():
+    rng = np.random.default_rng(9)
+    g = gg.random_graph(40, 0.15, wmax=6, loops=0.3, seed=9)
+    lab = rng.integers(0, 7, size=g.n).astype(np.int32)
+    rp, col, w = oracle.rebuild(g.rowptr, g.col, g.w, lab)
+    used = sorted(set(lab.tolist()))
+    nid = {c: i for i, c in enumerate(used)}
+    W = {}
+    for u in range(g.n):
+        for e in range(g.rowptr[u], g.rowptr[u + 1]):
+            key = (nid[int(lab[u])], nid[int(lab[g.col[e]])])
+            W[key] = W.get(key, 0) + int(g.w[e])
+    got = {}
+    for c in range(len(rp) - 1):
+        for e in range(rp[c], rp[c + 1]):
+            got[(c, int(col[e]))] = int(w[e])
+        assert list(col[rp[c]:rp[c + 1]]) == sorted(col[rp[c]:rp[c + 1]])
+    assert got == W
+    # coarsening keeps Q of the induced partition: singletons of the coarse graph
+    N1, _ = oracle.modularity_num(rp, col, w, np.arange(len(rp) - 1))
+    N0, _ = oracle.modularity_num(g.rowptr, g.col, g.w, lab)
+    assert N0 == N1
+
+
+# --------------------------------------------------------------- boundary
+def test_validation_codes():
+    ok = gg.from_edges(3, [(0, 1), (1, 2)])
+    assert oracle.validate(ok.rowptr, ok.col, ok.w) == (0, 4)
+    rp, col, w = ok.rowptr.copy(), ok.col.copy(), ok.w.copy()
+    w2 = w.copy(); w2[0] = 0
+    assert oracle.validate(rp, col, w2)[0] == -3  # weight
+    w3 = w.copy(); w3[0] = 2
+    assert oracle.validate(rp, col, w3)[0] == -2  # asymmetric weight
+    col2 = col.copy(); col2[1] = 7
+    assert oracle.validate(rp, col2, w)[0] == -1  # column out of range
+    g = gg.from_edges(3, [(0, 1), (0, 2)])
+    col3 = g.col.copy(); col3[0], col3[1] = col3[1], col3[0]
+    assert oracle.validate(g.rowptr, col3, g.w)[0] == -1  # unsorted
+    col4 = g.col.copy(); col4[1] = col4[0]
+    assert oracle.validate(g.rowptr, col4, g.w)[0] == -4  # duplicate
+    e = gg.from_edges(3, [])
+    assert oracle.validate(e.rowptr, e.col, e.w)[0] == -6  # empty
+    big = gg.from_edges(2, [(0, 1, 2 ** 30)])
+    assert oracle.validate(big.rowptr, big.col, big.w)[0] == -5  # 2m >= 2^31
+    bad = np.array([0, 2, 1, 2], dtype=np.int64)
+    assert oracle.validate(bad, ok.col, ok.w)[0] == -1  # decreasing rowptr
+    with pytest.raises(oracle.OracleError):
+        oracle.run(e.rowptr, e.col, e.w)
+
+
+def test_isolated_vertices_stay():
+    g = gg.from_edges(8, [(0, 1), (1, 2), (0, 2), (5, 6, 2)])
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0)
+    lab = r.final_labels
+    assert len({lab[3], lab[4], lab[7]}) == 3
+    assert lab[0] == lab[1] == lab[2] and lab[5] == lab[6]
