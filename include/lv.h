@@ -1,0 +1,201 @@
+/*
+ * lv.h -- C ABI of the GB300 parallel-Louvain library (liblv.so).
+ *
+ * The library runs the parallel Louvain community-detection method of Lu,
+ * Halappanavar and Kalyanaraman, "Parallel Heuristics for Scalable Community
+ * Detection" (arXiv 1410.1237), on one CUDA GPU: vertex following (Sec. 4.3),
+ * distance-1 colouring (Sec. 4.2), phases of parallel sweeps with the
+ * minimum-label heuristics (Algorithm 1, Sec. 4.1), the modularity of Eq. 3,
+ * and the coarse-graph rebuild between phases (Sec. 4.4 step 4, Sec. 4.5).
+ *
+ * Arithmetic is exact: weights are integers, gains are compared as
+ * 2m*e_{i->C} - k_i*a_C in 64-bit integers (Eq. 4 scaled by (2m)^2/2) and
+ * modularity is carried as the integer numerator N = (2m)^2 Q; the only
+ * floating-point operations are the threshold tests and the final Q = N /
+ * (2m)^2.  Results are deterministic: the same input and parameters give
+ * the same labels on every run and launch configuration.
+ *
+ * Conventions for every entry point:
+ *   - Every function returns lv_status; nothing throws across the ABI.
+ *   - Pointers flagged "on device" are CUDA device pointers; otherwise host.
+ *   - The caller keeps ownership of every buffer it passes.  Input arrays
+ *     are copied during lv_graph_create and may be freed when it returns.
+ *     Output arrays are caller-allocated.
+ *   - Calls on one handle must not run concurrently; distinct handles are
+ *     independent.  All GPU work of a handle is ordered on the stream given
+ *     at creation, and each entry point returns after that work completes.
+ *   - On LV_ERR_CUDA the handle's state is undefined; destroy it.
+ */
+#ifndef LV_H_
+#define LV_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lv_graph lv_graph; /* opaque, owned by the library */
+
+typedef enum {
+    LV_OK = 0,
+    LV_ERR_ARG = -1,           /* bad argument, rowptr not non-decreasing from 0,
+                                  column out of range or columns not ascending */
+    LV_ERR_NOT_SYMMETRIC = -2, /* (i,j,w) stored without (j,i,w) */
+    LV_ERR_WEIGHT = -3,        /* a weight < 1 (Sec. 2: weights are positive) */
+    LV_ERR_DUPLICATE = -4,     /* a column repeated in a row (Sec. 2: no multi-edges) */
+    LV_ERR_OVERFLOW = -5,      /* 2m >= 2^31, or more than 2^31-1 stored arcs */
+    LV_ERR_EMPTY = -6,         /* m == 0 */
+    LV_ERR_CUDA = -7,          /* a CUDA call failed; see lv_last_error() */
+    LV_ERR_OOM = -8,           /* device allocation failed */
+    LV_ERR_TIMEOUT = -9,       /* a bounded device wait gave up */
+    LV_ERR_STATE = -10,        /* no run yet, or phase index out of range */
+    LV_ERR_HASH = -11          /* a hash table probe exceeded its bound (internal) */
+} lv_status;
+
+/* Heuristic switches and threshold schedule of Sec. 5.1 (variant
+ * "baseline+VF+Color"), plus guards the paper leaves implicit. */
+typedef struct {
+    int32_t vertex_following; /* 0/1: merge single-degree vertices once, before phase 0 (Sec. 4.3) */
+    int32_t coloring;         /* 0/1: sweep one distance-1 colour class at a time (Sec. 4.2) */
+    double theta_low;         /* threshold of uncoloured phases, 1e-6 in Sec. 5.1 */
+    double theta_high;        /* threshold of coloured phases, 1e-2 in Sec. 5.1; 0 = use theta_low */
+    int64_t color_cutoff;     /* colour only phases whose graph has >= this many vertices (100,000) */
+    int32_t max_iters;        /* guard: iterations per phase (default 10,000) */
+    int32_t max_phases;       /* guard: phases (default 64) */
+    uint64_t color_seed;      /* seed of the colouring priority hash; phase p uses seed + p */
+    int32_t collect_timing;   /* 0/1: record CUDA-event times per stage and per iteration */
+    int32_t keep_graphs;      /* 0/1: keep every phase graph and colouring for inspection */
+    int32_t bin_small_max;    /* degree bins of the sweep; results do not depend on them */
+    int32_t bin_warp_max;     /*   (0 = defaults 16 / 128 / 4096; limits 32 / 256 / 4096) */
+    int32_t bin_cta_max;
+    int32_t reserved;
+} lv_params;
+
+/* Per-phase record.  N values are exact modularity numerators: Q = N/(2m)^2. */
+typedef struct {
+    int64_t n;          /* vertices of the phase graph G_p */
+    int64_t arcs;       /* stored arcs of G_p (each edge twice, each self-loop once) */
+    int64_t n_next;     /* non-empty communities = vertices of G_{p+1} */
+    int64_t two_m;      /* 2m (the same for every phase) */
+    int64_t N_start;    /* numerator of the singleton partition of G_p */
+    int64_t N_end;      /* numerator after the phase's last iteration */
+    double q;           /* N_end / (2m)^2 */
+    double theta;       /* threshold used by the phase */
+    int32_t colored;    /* 1 if the phase swept colour classes */
+    int32_t num_colors; /* colour classes (0 if not coloured) */
+    int32_t iterations; /* iterations of Alg. 1's while-loop */
+    int32_t reserved;
+    double ms_color;    /* CUDA-event times (collect_timing), else -1 */
+    double ms_iterate;
+    double ms_rebuild;
+} lv_phase_info;
+
+/* Per-iteration record. */
+typedef struct {
+    int32_t phase;
+    int32_t iter;        /* 1-based iteration within the phase */
+    int32_t color_steps; /* colour classes swept (1 when uncoloured) */
+    int32_t reserved;
+    int64_t moved;       /* vertices that changed community */
+    int64_t N;           /* modularity numerator after the iteration */
+    int64_t arcs;        /* arcs scanned by the iteration's sweep */
+    double ms;           /* CUDA-event time of the iteration (collect_timing), else -1 */
+} lv_iter_stat;
+
+/* Whole-run totals. */
+typedef struct {
+    int32_t num_phases;
+    int32_t total_iterations;
+    int64_t edge_visits;   /* sum over iterations of the arcs scanned */
+    int64_t vf_n;          /* vertices after vertex following (n if off) */
+    int64_t sweep_launches;
+    double ms_total;       /* CUDA-event times (collect_timing), else -1 */
+    double ms_vf;
+    double ms_color;
+    double ms_iterate;
+    double ms_rebuild;
+    int64_t kernel_launches; /* CUDA kernels this run launched */
+} lv_stats;
+
+/* Fill *p with the defaults of Sec. 5.1: VF on, colouring on, theta_low 1e-6,
+ * theta_high 1e-2, cutoff 100,000 vertices, max_iters 10,000, max_phases 64. */
+void lv_params_default(lv_params *p);
+
+/* Create a handle from a symmetric CSR with integer weights (Sec. 2: an
+ * undirected graph, positive weights, self-loops allowed, no multi-edges).
+ *   n        vertices, 0 <= n < 2^31 - 1
+ *   rowptr   int64[n+1], rowptr[0] = 0, non-decreasing
+ *   col      int32[rowptr[n]], ascending within each row, each in [0, n)
+ *   w        int32[rowptr[n]], each >= 1; (i,j,w) stored iff (j,i,w) stored;
+ *            a self-loop (i,i,w) is stored once in row i and counts once in k_i
+ *   ptrs_on_device  0: the three arrays are host memory; 1: device memory
+ *   cuda_stream     cudaStream_t (NULL = legacy default stream) for all work
+ * Requires 2m = sum of all stored weights < 2^31.  The input is validated on
+ * the device; when it breaks several rules the first of ARG, DUPLICATE,
+ * WEIGHT, NOT_SYMMETRIC, OVERFLOW, EMPTY is returned and *out is NULL. */
+lv_status lv_graph_create(lv_graph **out, int64_t n, const int64_t *rowptr, const int32_t *col,
+                          const int32_t *w, int ptrs_on_device, void *cuda_stream);
+
+/* Run the whole method (Sec. 4.4 steps 1-4) with parameters *p (NULL =
+ * defaults).  Replaces the results of any earlier run on the handle.  Phase
+ * control: phase p is coloured when coloring && n_p >= color_cutoff and no
+ * earlier coloured phase gained less than theta_high; the iteration loop of a
+ * phase stops when nothing moved, when (N_C - N_P) < theta |N_P| after the
+ * second iteration, or at max_iters; phases stop when nothing merged, when an
+ * uncoloured phase gained less than theta_low relative to its singleton start,
+ * or at max_phases. */
+lv_status lv_run(lv_graph *g, const lv_params *p);
+
+/* Number of recorded phases of the last run. */
+lv_status lv_num_phases(const lv_graph *g, int32_t *out);
+
+/* Community of every ORIGINAL vertex after phase `phase` (-1 = last phase):
+ * int32[n] written to `out` (host, or device when ptr_on_device = 1).
+ * Communities are numbered 0..n_next-1 in ascending order of their label in
+ * the phase graph. */
+lv_status lv_get_labels(const lv_graph *g, int32_t phase, int32_t *out, int ptr_on_device);
+
+/* Modularity after phase `phase` (-1 = last): q = N/(2m)^2 (Eq. 3), and the
+ * exact numerator as a 128-bit two's-complement value (num_hi:num_lo) with
+ * den = (2m)^2.  Any output pointer may be NULL. */
+lv_status lv_get_modularity(const lv_graph *g, int32_t phase, double *q, int64_t *num_hi,
+                            uint64_t *num_lo, int64_t *den);
+
+/* Per-phase record (phase -1 = last). */
+lv_status lv_get_phase_info(const lv_graph *g, int32_t phase, lv_phase_info *out);
+
+/* Per-iteration records of the last run: count, then copy up to `count`. */
+lv_status lv_get_num_iterations(const lv_graph *g, int64_t *count);
+lv_status lv_get_iteration_stats(const lv_graph *g, lv_iter_stat *out, int64_t count);
+
+/* Whole-run totals of the last run. */
+lv_status lv_get_stats(const lv_graph *g, lv_stats *out);
+
+/* Map of vertex following: int32[n] giving each original vertex's vertex in
+ * the phase-0 graph (identity when vertex following is off). */
+lv_status lv_get_vf_map(const lv_graph *g, int32_t *out, int ptr_on_device);
+
+/* Phase graph G_p of the last run (requires keep_graphs = 1): first call
+ * with NULL arrays to read n and arcs, then with int64[n+1], int32[arcs] x 2. */
+lv_status lv_get_phase_graph(const lv_graph *g, int32_t phase, int64_t *n, int64_t *arcs,
+                             int64_t *rowptr, int32_t *col, int32_t *w, int ptrs_on_device);
+
+/* Colour of each vertex of G_p (requires keep_graphs = 1 and a coloured
+ * phase): int32[n_p]. */
+lv_status lv_get_phase_colors(const lv_graph *g, int32_t phase, int32_t *out, int ptr_on_device);
+
+/* Static description of a status code. */
+const char *lv_status_string(lv_status s);
+
+/* Text of the last CUDA error seen by this thread (empty if none). */
+const char *lv_last_error(void);
+
+/* Release the handle and all its device memory (NULL is a no-op). */
+void lv_graph_destroy(lv_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LV_H_ */

@@ -1,0 +1,369 @@
+// lv_graph.cu -- input validation, weighted degrees, vertex following.
+//
+// Validation follows the problem statement of Sec. 2 (positive weights,
+// self-loops allowed, no multi-edges, undirected => symmetric storage).
+// Vertex following is the preprocessing of Sec. 4.3 / Sec. 4.4 step 1:
+// every single-degree vertex is merged into its only neighbour once, before
+// the first phase.
+#include "lv_ops.cuh"
+
+namespace lv {
+
+// severity ranks; the most severe violation found is reported
+__device__ __forceinline__ void raise_sev(int *sev, int rank) { atomicMax(sev, rank); }
+constexpr int kSevArg = 6, kSevDup = 5, kSevWeight = 4, kSevSym = 3;
+
+lv_status severity_to_status(int sev) {
+    switch (sev) {
+    case kSevArg: return LV_ERR_ARG;
+    case kSevDup: return LV_ERR_DUPLICATE;
+    case kSevWeight: return LV_ERR_WEIGHT;
+    case kSevSym: return LV_ERR_NOT_SYMMETRIC;
+    default: return LV_OK;
+    }
+}
+
+namespace {
+
+__global__ void rowptr_check_kernel(const int64_t *__restrict__ rowptr, int64_t n, int *sev) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (rowptr[i + 1] < rowptr[i]) raise_sev(sev, kSevArg);
+}
+
+__global__ void convert_kernel(const int64_t *__restrict__ rowptr, const int32_t *__restrict__ col,
+                               const int32_t *__restrict__ w, int32_t n, int32_t A,
+                               int32_t *off, int2 *arcs) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += stride)
+        off[i] = (int32_t)rowptr[i];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A; e += stride)
+        arcs[e] = make_int2(col[e], w[e]);
+}
+
+// one warp per row: column range, ascending order, weights, degrees
+__global__ void __launch_bounds__(256) row_check_kernel(DGraph g, int *sev, int32_t *k,
+                                                        int32_t *loop,
+                                                        unsigned long long *two_m) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
+        const int beg = g.off[i], end = g.off[i + 1];
+        long long s = 0;
+        int lp = 0;
+        for (int e = beg + lane; e < end; e += 32) {
+            const int2 a = g.arcs[e];
+            if (a.x < 0 || a.x >= g.n) raise_sev(sev, kSevArg);
+            if (e > beg) {
+                const int prev = g.arcs[e - 1].x;
+                if (a.x == prev) raise_sev(sev, kSevDup);
+                else if (a.x < prev) raise_sev(sev, kSevArg);
+            }
+            if (a.y < 1) raise_sev(sev, kSevWeight);
+            s += a.y;
+            if (a.x == i) lp = a.y;
+        }
+        s = warp_sum(s);
+        lp = warp_sum(lp);
+        if (lane == 0) {
+            k[i] = s > 0x7fffffffll ? 0x7fffffff : (int32_t)s;
+            loop[i] = lp;
+            acc += (unsigned long long)s;
+        }
+    }
+    if (lane == 0 && acc) atomicAdd(two_m, acc);
+}
+
+// one warp per row: every (i, j, w), j != i, must have (j, i, w)
+__global__ void __launch_bounds__(256) symmetry_kernel(DGraph g, int *sev) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
+        const int beg = g.off[i], end = g.off[i + 1];
+        for (int e = beg + lane; e < end; e += 32) {
+            const int2 a = g.arcs[e];
+            if (a.x == i) continue;
+            int lo = g.off[a.x], hi = g.off[a.x + 1];
+            const int hend = hi;
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (g.arcs[mid].x < i) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= hend || g.arcs[lo].x != i || g.arcs[lo].y != a.y) raise_sev(sev, kSevSym);
+        }
+    }
+}
+
+// one warp per row: weighted degree k_i and self-loop weight (R1: once)
+__global__ void __launch_bounds__(256) degree_kernel(DGraph g, int32_t *k, int32_t *loop) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
+        const int beg = g.off[i], end = g.off[i + 1];
+        int s = 0, lp = 0;
+        for (int e = beg + lane; e < end; e += 32) {
+            const int2 a = g.arcs[e];
+            s += a.y;
+            if (a.x == i) lp = a.y;
+        }
+        s = warp_sum(s);
+        lp = warp_sum(lp);
+        if (lane == 0) {
+            k[i] = s;
+            loop[i] = lp;
+        }
+    }
+}
+
+// ------------------------------------------------------ vertex following
+// single-degree: exactly one stored arc and it is not a self-loop
+__global__ void vf_mark_kernel(DGraph g, uint8_t *d1) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        const int beg = g.off[i];
+        d1[i] = (g.off[i + 1] - beg == 1) && (g.arcs[beg].x != i);
+    }
+}
+
+// removal decision; the survivor gets self-loop weight 2*w(i,j) (R2); of two
+// mutually single-degree vertices the smaller id is removed (R3)
+__global__ void vf_decide_kernel(DGraph g, const uint8_t *__restrict__ d1, int32_t *keep,
+                                 int32_t *target, int32_t *extra, int32_t *nrem) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        int kp = 1;
+        if (d1[i]) {
+            const int2 a = g.arcs[g.off[i]];
+            const int j = a.x;
+            if (!(d1[j] && j < i)) {
+                kp = 0;
+                target[i] = j;
+                atomicAdd(&extra[j], 2 * a.y);
+                atomicAdd(&nrem[j], 1);
+            }
+        }
+        keep[i] = kp;
+    }
+}
+
+__global__ void vf_rowlen_kernel(DGraph g, const int32_t *__restrict__ keep,
+                                 const int32_t *__restrict__ newid, const int32_t *__restrict__ loop,
+                                 const int32_t *__restrict__ extra, const int32_t *__restrict__ nrem,
+                                 int32_t *rowlen) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        if (!keep[i]) continue;
+        const int deg = g.off[i + 1] - g.off[i];
+        rowlen[newid[i]] = deg - nrem[i] + ((loop[i] == 0 && extra[i] > 0) ? 1 : 0);
+    }
+}
+
+// one warp per kept row: drop arcs to removed vertices, renumber, add the
+// merged weight to the self-loop (inserting it at its sorted place if absent)
+__global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *__restrict__ keep,
+                                                      const int32_t *__restrict__ newid,
+                                                      const int32_t *__restrict__ loop,
+                                                      const int32_t *__restrict__ extra,
+                                                      const int32_t *__restrict__ off2,
+                                                      int2 *arcs2) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t ii = blockIdx.x * 8 + (threadIdx.x >> 5); ii < g.n; ii += nw) {
+        const int i = (int)ii;
+        if (!keep[i]) continue;  // warp-uniform
+        const int ni = newid[i];
+        const int ex = extra[i];
+        bool pending = (loop[i] == 0 && ex > 0);  // self-loop to insert
+        int run = off2[ni];
+        int sh = 0;  // 1 once the inserted loop precedes the current arcs
+        const int beg = g.off[i], end = g.off[i + 1];
+        for (int base = beg; base < end; base += 32) {
+            const int e = base + lane;
+            const bool valid = e < end;
+            const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
+            const bool kp = valid && (a.x == i || keep[a.x]);
+            const unsigned bk = __ballot_sync(0xffffffffu, kp);
+            int lsh = sh;
+            if (pending) {
+                const unsigned bgt = __ballot_sync(0xffffffffu, kp && a.x > i);
+                if (bgt) {
+                    const int f = __ffs(bgt) - 1;
+                    if (lane == 0) arcs2[run + __popc(bk & ((1u << f) - 1u))] = make_int2(ni, ex);
+                    if (lane >= f) lsh = 1;
+                    pending = false;
+                    sh = 1;
+                }
+            }
+            if (kp) {
+                const int pos = run + __popc(bk & lt) + lsh;
+                arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
+            }
+            run += __popc(bk);
+        }
+        if (pending && lane == 0) arcs2[run + sh] = make_int2(ni, ex);
+    }
+}
+
+__global__ void vf_map_kernel(int32_t n, const int32_t *__restrict__ keep,
+                              const int32_t *__restrict__ newid, const int32_t *__restrict__ target,
+                              int32_t *map) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        map[v] = keep[v] ? newid[v] : newid[target[v]];
+}
+
+__global__ void iota_kernel(int32_t n, int32_t *out) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        out[v] = v;
+}
+
+}  // namespace
+
+static int grid_rows(int64_t rows) { return grid_for(rows, 8, g_num_sms * 16); }
+static int grid_items(int64_t items) { return grid_for(items, 256, g_num_sms * 16); }
+
+lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *col,
+                             const int32_t *w, DGraph *out, int32_t **k_out, int32_t **loop_out,
+                             int64_t *two_m_out, int *scratch_pinned, cudaStream_t s) {
+    *out = DGraph();
+    *k_out = nullptr;
+    *loop_out = nullptr;
+    if (n < 0 || n > 0x7ffffffell) return LV_ERR_ARG;
+    int64_t ends[2];
+    LV_CUDA(cudaMemcpyAsync(&ends[0], rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(&ends[1], rowptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    if (ends[0] != 0) return LV_ERR_ARG;
+    int *dsev = nullptr;
+    unsigned long long *d2m = nullptr;
+    LV_TRY(dalloc_n(&dsev, 1, s));
+    LV_TRY(dalloc_n(&d2m, 1, s));
+    LV_CUDA(cudaMemsetAsync(dsev, 0, sizeof(int), s));
+    LV_CUDA(cudaMemsetAsync(d2m, 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        rowptr_check_kernel<<<grid_items(n), 256, 0, s>>>(rowptr, n, dsev);
+        LV_LAUNCH_CHECK();
+    }
+    LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    lv_status st = LV_OK;
+    if (scratch_pinned[0] != 0 || ends[1] < 0) st = LV_ERR_ARG;
+    else if (ends[1] > 0x7fffffffll) st = LV_ERR_OVERFLOW;
+    if (st != LV_OK) {
+        dfree(dsev, s);
+        dfree(d2m, s);
+        return st;
+    }
+    DGraph g;
+    g.n = (int32_t)n;
+    g.A = (int32_t)ends[1];
+    LV_TRY(dalloc_n(&g.off, (size_t)n + 1, s));
+    LV_TRY(dalloc_n(&g.arcs, (size_t)g.A, s));
+    int32_t *k = nullptr, *loop = nullptr;
+    LV_TRY(dalloc_n(&k, (size_t)n, s));
+    LV_TRY(dalloc_n(&loop, (size_t)n, s));
+    convert_kernel<<<grid_items((int64_t)g.A + n + 1), 256, 0, s>>>(rowptr, col, w, g.n, g.A,
+                                                                    g.off, g.arcs);
+    LV_LAUNCH_CHECK();
+    if (n > 0) {
+        row_check_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev, k, loop, d2m);
+        LV_LAUNCH_CHECK();
+    }
+    LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    if (scratch_pinned[0] < kSevSym && n > 0) {
+        symmetry_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev);
+        LV_LAUNCH_CHECK();
+    }
+    unsigned long long tm = 0;
+    LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(&tm, d2m, sizeof(tm), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    st = severity_to_status(scratch_pinned[0]);
+    if (st == LV_OK) {
+        if (tm >= (1ull << 31)) st = LV_ERR_OVERFLOW;
+        else if (tm == 0) st = LV_ERR_EMPTY;
+    }
+    dfree(dsev, s);
+    dfree(d2m, s);
+    if (st != LV_OK) {
+        dfree(g.off, s);
+        dfree(g.arcs, s);
+        dfree(k, s);
+        dfree(loop, s);
+        return st;
+    }
+    *out = g;
+    *k_out = k;
+    *loop_out = loop;
+    *two_m_out = (int64_t)tm;
+    return LV_OK;
+}
+
+lv_status compute_degrees(const DGraph &g, int32_t *k, int32_t *loop, cudaStream_t s) {
+    if (g.n == 0) return LV_OK;
+    degree_kernel<<<grid_rows(g.n), 256, 0, s>>>(g, k, loop);
+    LV_LAUNCH_CHECK();
+    return LV_OK;
+}
+
+lv_status iota(int32_t n, int32_t *out, cudaStream_t s) {
+    if (n == 0) return LV_OK;
+    iota_kernel<<<grid_items(n), 256, 0, s>>>(n, out);
+    LV_LAUNCH_CHECK();
+    return LV_OK;
+}
+
+lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, int32_t *map,
+                           int *scratch_pinned, cudaStream_t s) {
+    const int n = g.n;
+    uint8_t *d1 = nullptr;
+    int32_t *keep = nullptr, *target = nullptr, *extra = nullptr, *nrem = nullptr,
+            *newid = nullptr, *rowlen = nullptr;
+    LV_TRY(dalloc_n(&d1, (size_t)n, s));
+    LV_TRY(dalloc_n(&keep, (size_t)n + 1, s));
+    LV_TRY(dalloc_n(&target, (size_t)n, s));
+    LV_TRY(dalloc_n(&extra, (size_t)n, s));
+    LV_TRY(dalloc_n(&nrem, (size_t)n, s));
+    LV_TRY(dalloc_n(&newid, (size_t)n + 1, s));
+    LV_CUDA(cudaMemsetAsync(extra, 0, sizeof(int32_t) * n, s));
+    LV_CUDA(cudaMemsetAsync(nrem, 0, sizeof(int32_t) * n, s));
+    vf_mark_kernel<<<grid_items(n), 256, 0, s>>>(g, d1);
+    LV_LAUNCH_CHECK();
+    vf_decide_kernel<<<grid_items(n), 256, 0, s>>>(g, d1, keep, target, extra, nrem);
+    LV_LAUNCH_CHECK();
+    LV_TRY(scan_excl_i32(keep, newid, n, s));
+    LV_CUDA(cudaMemcpyAsync(scratch_pinned, newid + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const int n2 = scratch_pinned[0];
+    LV_TRY(dalloc_n(&rowlen, (size_t)n2 + 1, s));
+    DGraph h;
+    h.n = n2;
+    LV_TRY(dalloc_n(&h.off, (size_t)n2 + 1, s));
+    vf_rowlen_kernel<<<grid_items(n), 256, 0, s>>>(g, keep, newid, loop, extra, nrem, rowlen);
+    LV_LAUNCH_CHECK();
+    LV_TRY(scan_excl_i32(rowlen, h.off, n2, s));
+    LV_CUDA(cudaMemcpyAsync(scratch_pinned, h.off + n2, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    h.A = scratch_pinned[0];
+    LV_TRY(dalloc_n(&h.arcs, (size_t)h.A, s));
+    vf_fill_kernel<<<grid_rows(n), 256, 0, s>>>(g, keep, newid, loop, extra, h.off, h.arcs);
+    LV_LAUNCH_CHECK();
+    vf_map_kernel<<<grid_items(n), 256, 0, s>>>(n, keep, newid, target, map);
+    LV_LAUNCH_CHECK();
+    dfree(d1, s);
+    dfree(keep, s);
+    dfree(target, s);
+    dfree(extra, s);
+    dfree(nrem, s);
+    dfree(newid, s);
+    dfree(rowlen, s);
+    *out = h;
+    return LV_OK;
+}
+
+void free_graph(DGraph &g, cudaStream_t s) {
+    dfree(g.off, s);
+    dfree(g.arcs, s);
+    g = DGraph();
+}
+
+}  // namespace lv

@@ -1,0 +1,157 @@
+// lv_internal.cuh -- shared declarations of the CUDA implementation.
+//
+// Device data layout (all in HBM):
+//   graph   off   int32[n+1]   row offsets (arcs < 2^31 because 2m < 2^31, w >= 1)
+//           arcs  int2[A]      {col, w} interleaved, so one 8-byte load brings
+//                              both halves of an arc and rows stream as 16-byte
+//                              vectors
+//   vertex  k     int32[n]     weighted degree (Sec. 2), < 2m < 2^31
+//           loop  int32[n]     self-loop weight (0 if none)
+//           C     int32[n]     community label; labels are vertex ids of G_p
+//   community comm u64[n]      packed {a_C (low 32 bits), |C| (high 32 bits)};
+//                              one 8-byte gather serves the gain (a_C) and the
+//                              singlet rule (|C|), and one 64-bit atomicAdd
+//                              moves a vertex's degree and count together
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lv.h"
+
+namespace lv {
+
+constexpr int kEmpty = -1;           // empty hash slot (labels are >= 0)
+constexpr int kBins = 4;             // sweep bins: group / warp / CTA / hub
+constexpr int kBinSkip = kBins;      // isolated vertices (no arcs)
+constexpr int kSmallMaxLimit = 32;   // group-bin table holds 2x this
+constexpr int kWarpMaxLimit = 256;   // warp-bin table holds 2x this
+constexpr int kCtaMaxLimit = 4096;   // CTA-bin table holds 2x this (64 KB)
+constexpr int kGroupLanes = 8;       // lanes per vertex in the group bin
+constexpr int kGroupSlots = 2 * kSmallMaxLimit;
+constexpr int kWarpSlots = 2 * kWarpMaxLimit;
+constexpr int kCtaSlots = 2 * kCtaMaxLimit;
+
+// ------------------------------------------------------------------ errors
+void set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+#define LV_CUDA(x)                                                       \
+    do {                                                                 \
+        cudaError_t e_ = (x);                                            \
+        if (e_ != cudaSuccess) {                                         \
+            ::lv::set_cuda_error(e_, #x, __FILE__, __LINE__);            \
+            return e_ == cudaErrorMemoryAllocation ? LV_ERR_OOM : LV_ERR_CUDA; \
+        }                                                                \
+    } while (0)
+
+#define LV_TRY(x)                         \
+    do {                                  \
+        lv_status s_ = (x);               \
+        if (s_ != LV_OK) return s_;       \
+    } while (0)
+
+// every kernel launch is followed by this check, which also counts it
+extern unsigned long long g_kernel_launches;
+#define LV_LAUNCH_CHECK()                 \
+    do {                                  \
+        ++::lv::g_kernel_launches;        \
+        LV_CUDA(cudaGetLastError());      \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered allocation from a library-owned pool (kept cached between
+// calls, so repeated runs do not return memory to the driver).
+lv_status dalloc(void **p, size_t bytes, cudaStream_t s);
+void dfree(void *p, cudaStream_t s);
+
+template <typename T>
+lv_status dalloc_n(T **p, size_t count, cudaStream_t s) {
+    return dalloc(reinterpret_cast<void **>(p), count * sizeof(T) + 16, s);
+}
+
+// ------------------------------------------------------------------ graph
+struct DGraph {
+    int32_t n = 0;
+    int32_t A = 0;
+    int32_t *off = nullptr;   // n+1
+    int2 *arcs = nullptr;     // A
+};
+
+// ----------------------------------------------------------- device utils
+__device__ __forceinline__ unsigned hash32(int c) {
+    return (unsigned)c * 0x9E3779B1u;  // Fibonacci hashing (Knuth 6.4)
+}
+
+__device__ __forceinline__ int comm_a(unsigned long long v) { return (int)(unsigned)v; }
+__device__ __forceinline__ int comm_size(unsigned long long v) { return (int)(v >> 32); }
+__device__ __forceinline__ unsigned long long comm_pack(int a, int sz) {
+    return ((unsigned long long)(unsigned)sz << 32) | (unsigned)a;
+}
+// delta that adds (+k, +1) / removes (-k, -1) a vertex of degree k
+__device__ __forceinline__ unsigned long long comm_join(int k) {
+    return (1ull << 32) + (unsigned long long)(unsigned)k;
+}
+__device__ __forceinline__ unsigned long long comm_leave(int k) {
+    return (unsigned long long)(-(long long)((1ll << 32) + (long long)k));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a 256-thread block; result valid in thread 0.
+template <typename T>
+__device__ __forceinline__ T block_sum_256(T v, T *smem8) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) smem8[w] = v;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 8; ++i) r += smem8[i];
+    return r;
+}
+
+// splitmix64 output function (Steele, Lea, Flood 2014): colouring priority
+__device__ __forceinline__ unsigned long long prio_hash(unsigned long long x) {
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+// pi(u) > pi(v) with pi(v) = (h(v ^ seed), v) compared lexicographically
+__device__ __forceinline__ bool prio_greater(unsigned long long hu, int u, unsigned long long hv,
+                                             int v) {
+    return hu > hv || (hu == hv && u > v);
+}
+
+// ------------------------------------------------------------- primitives
+// out[0..n] = exclusive prefix sums of in[0..n), out[n] = total (in == out allowed).
+lv_status scan_excl_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort on the low `nbits` bits of the keys, values carried.
+// Sorted data ends in (keys, vals); (keys_alt, vals_alt) are scratch of the same size.
+lv_status radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                         int n, int nbits, cudaStream_t s);
+lv_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                         int n, int nbits, cudaStream_t s);
+
+inline int bits_for(uint64_t maxval) {  // bits needed to represent values <= maxval
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+inline int grid_for(int64_t work, int per_block, int max_blocks) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > max_blocks) g = max_blocks;
+    return (int)g;
+}
+
+extern int g_num_sms;  // set once per process from the current device
+
+}  // namespace lv

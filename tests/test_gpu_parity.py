@@ -1,0 +1,179 @@
+"""GPU path vs the serial oracle, through the C ABI.
+
+Labels, exact modularity numerators, iteration and phase counts must be
+identical at every phase; with keep_graphs the phase graphs (vertex
+following output and every coarse graph) and colourings must be identical
+too.  Sizes run from hand-made graphs through several tiles with ragged
+tails up to the full R-MAT scale-20 workload; the 2^24-vertex Chung-Lu
+workload is checked on its first iterations in full and on invariants and
+exact modularity at full length.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1410_1237_gb300 import _build, lv as lvmod
+    _build.build()
+    lvmod.load()
+    return lvmod
+
+
+def compare(lv, g, graphs=True, iters=True, **params):
+    res = lv.run(g.rowptr, g.col, g.w, keep_graphs=int(graphs), **params)
+    ref = oracle.run(g.rowptr, g.col, g.w, trace=int(graphs), **params)
+    assert res.two_m == ref.two_m
+    assert np.array_equal(res.vf_map, ref.vf_map)
+    assert len(res.phases) == len(ref.phases), ([p.n for p in res.phases], [p.n for p in ref.phases])
+    for pi, (a, b) in enumerate(zip(res.phases, ref.phases)):
+        assert (a.n, a.arcs, a.n_next) == (b.n, b.arcs, b.n_next), pi
+        assert (a.colored, a.num_colors) == (b.colored, b.num_colors), pi
+        assert a.N_start == b.N_start, pi
+        assert a.N_end == b.N_end, pi
+        assert a.iterations == b.iterations, pi
+        assert a.q == b.q
+        assert np.array_equal(a.labels, b.labels), pi
+    if iters:
+        got = [(t[0], t[1], t[3], t[4]) for t in res.iters]
+        want = [(t[0], t[1], t[2], t[3]) for t in ref.iters]
+        assert got == want
+    if graphs:
+        h = lv.lv_graph_create(g.n, g.rowptr, g.col, g.w)
+        try:
+            lv.lv_run(h, lv.make_params(keep_graphs=1, **params))
+            for pi, b in enumerate(ref.phases):
+                rp, col, w = lv.lv_get_phase_graph(h, pi)
+                assert np.array_equal(rp, b.graph[0]) and np.array_equal(col, b.graph[1])
+                assert np.array_equal(w, b.graph[2])
+                if b.colored:
+                    assert np.array_equal(lv.lv_get_phase_colors(h, pi, b.n), b.colors)
+        finally:
+            lv.lv_graph_destroy(h)
+    return res, ref
+
+
+VARIANTS = [
+    dict(vertex_following=0, coloring=0),
+    dict(vertex_following=1, coloring=0),
+    dict(vertex_following=0, coloring=1, color_cutoff=0),
+    dict(vertex_following=1, coloring=1, color_cutoff=0, theta_high=1e-2),
+]
+
+
+@pytest.mark.parametrize("name", ["two_triangles.txt", "two_k5.txt", "ring3_triangles.txt",
+                                  "k2_singlet.txt", "k4_minlabel.txt", "star_vf.txt"])
+@pytest.mark.parametrize("vi", range(len(VARIANTS)))
+def test_golden_graphs(lv, golden, name, vi):
+    fx = golden(name)
+    g = gg.from_edges(fx["n"], fx["edges"])
+    compare(lv, g, **VARIANTS[vi])
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_small(lv, seed):
+    n = [37, 100, 257, 511, 1000, 1537, 2049, 3001][seed]
+    g = gg.random_graph(n, min(0.5, 12.0 / n), wmax=1 + seed, loops=0.1 * (seed % 3), seed=seed)
+    if g.two_m == 0:
+        pytest.skip("empty draw")
+    for v in VARIANTS:
+        compare(lv, g, **v)
+
+
+@pytest.mark.parametrize("bins", [(1, 2, 3), (2, 4, 8), (4, 32, 64), (16, 128, 4096),
+                                  (32, 256, 4096)])
+def test_every_bin_path(lv, bins):
+    # tiny bin limits push ordinary vertices through the CTA and hub kernels
+    g = gg.chunglu(4000, 2.1, 0.7, 16000, 300.0, seed=7)
+    s, w_, c = bins
+    compare(lv, g, vertex_following=1, coloring=1, color_cutoff=0,
+            bin_small_max=s, bin_warp_max=w_, bin_cta_max=c)
+    compare(lv, g, graphs=False, vertex_following=0, coloring=0,
+            bin_small_max=s, bin_warp_max=w_, bin_cta_max=c)
+
+
+def test_hub_vertex(lv):
+    # a hub of degree 12,000 (> CTA bin) joined to a ring; VF off keeps it
+    n = 12001
+    edges = [(0, i, 1 + i % 5) for i in range(1, n)] + [(i, i + 1) for i in range(1, n - 1)]
+    g = gg.from_edges(n, edges)
+    compare(lv, g, vertex_following=0, coloring=0)
+    compare(lv, g, vertex_following=1, coloring=1, color_cutoff=0)
+
+
+def test_planted1k(lv):
+    g, prm = gg.workload("planted1k")
+    compare(lv, g, **prm)
+
+
+def test_rmat16(lv):
+    g, prm = gg.workload("rmat16")
+    compare(lv, g, **prm)
+
+
+def test_chunglu_small(lv):
+    g = gg.chunglu(50_000, 2.1, 0.7, 400_000, 2000.0, seed=3)
+    compare(lv, g, vertex_following=1, coloring=1, color_cutoff=10_000, theta_high=1e-2)
+
+
+def test_rmat20_full(lv):
+    g, prm = gg.workload("rmat20")
+    compare(lv, g, graphs=False, **prm)
+
+
+def test_determinism(lv):
+    g, prm = gg.workload("rmat16")
+    a = lv.run(g.rowptr, g.col, g.w, **prm)
+    b = lv.run(g.rowptr, g.col, g.w, bin_small_max=4, bin_warp_max=64, bin_cta_max=512, **prm)
+    for x, y in zip(a.phases, b.phases):
+        assert np.array_equal(x.labels, y.labels) and x.N_end == y.N_end
+
+
+def test_device_pointers_and_stream(lv):
+    torch = pytest.importorskip("torch")
+    g, prm = gg.workload("planted1k")
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream()
+    t = [torch.from_numpy(x).to(dev) for x in (g.rowptr, g.col, g.w)]
+    torch.cuda.synchronize()
+    h = lv.lv_graph_create(g.n, *t, stream=s.cuda_stream)
+    try:
+        lv.lv_run(h, lv.make_params(**prm))
+        out = torch.empty(g.n, dtype=torch.int32, device=dev)
+        lv.lv_get_labels(h, -1, out)
+        ref = oracle.run(g.rowptr, g.col, g.w, **prm)
+        assert np.array_equal(out.cpu().numpy(), ref.final_labels)
+        q, num, den = lv.lv_get_modularity(h, -1)
+        assert num == ref.phases[-1].N_end and den == ref.two_m ** 2
+    finally:
+        lv.lv_graph_destroy(h)
+
+
+@pytest.mark.slow
+def test_chunglu24_first_iterations(lv):
+    g, prm = gg.workload("chunglu24")
+    for it in (1, 2):
+        compare(lv, g, graphs=False, max_phases=1, max_iters=it, **prm)
+
+
+@pytest.mark.slow
+def test_chunglu24_full_invariants(lv):
+    g, prm = gg.workload("chunglu24")
+    res = lv.run(g.rowptr, g.col, g.w, **prm)
+    prev = None
+    for p in res.phases:
+        assert set(np.unique(p.labels).tolist()) == set(range(p.n_next))
+        N, tm = oracle.modularity_num(g.rowptr, g.col, g.w, p.labels)
+        assert tm == res.two_m and N == p.N_end
+        if prev is not None:
+            assert p.N_start == prev.N_end
+        assert -0.5 <= p.q < 1
+        prev = p
