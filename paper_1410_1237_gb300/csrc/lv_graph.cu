@@ -75,23 +75,37 @@ __global__ void __launch_bounds__(256) row_check_kernel(DGraph g, int *sev, int3
     if (lane == 0 && acc) atomicAdd(two_m, acc);
 }
 
-// one warp per row: every (i, j, w), j != i, must have (j, i, w)
+// every (i, j, w), j != i, must have (j, i, w): row j is bisected
+__device__ __forceinline__ void check_mirror(const DGraph &g, int i, int2 a, int *sev) {
+    if (a.x == i) return;
+    int lo = g.off[a.x], hi = g.off[a.x + 1];
+    const int hend = hi;
+    while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (g.arcs[mid].x < i) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= hend || g.arcs[lo].x != i || g.arcs[lo].y != a.y) raise_sev(sev, kSevSym);
+}
+
+constexpr int kBigRow = 1024;
+
+// one warp per row of fewer than kBigRow arcs
 __global__ void __launch_bounds__(256) symmetry_kernel(DGraph g, int *sev) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
         const int beg = g.off[i], end = g.off[i + 1];
-        for (int e = beg + lane; e < end; e += 32) {
-            const int2 a = g.arcs[e];
-            if (a.x == i) continue;
-            int lo = g.off[a.x], hi = g.off[a.x + 1];
-            const int hend = hi;
-            while (lo < hi) {
-                const int mid = lo + ((hi - lo) >> 1);
-                if (g.arcs[mid].x < i) lo = mid + 1; else hi = mid;
-            }
-            if (lo >= hend || g.arcs[lo].x != i || g.arcs[lo].y != a.y) raise_sev(sev, kSevSym);
-        }
+        if (end - beg >= kBigRow) continue;
+        for (int e = beg + lane; e < end; e += 32) check_mirror(g, (int)i, g.arcs[e], sev);
+    }
+}
+
+// one 1024-thread block per row of at least kBigRow arcs
+__global__ void __launch_bounds__(1024) symmetry_big_kernel(DGraph g, int *sev) {
+    for (int64_t i = blockIdx.x; i < g.n; i += gridDim.x) {
+        const int beg = g.off[i], end = g.off[i + 1];
+        if (end - beg < kBigRow) continue;
+        for (int e = beg + threadIdx.x; e < end; e += 1024) check_mirror(g, (int)i, g.arcs[e], sev);
     }
 }
 
@@ -271,6 +285,8 @@ lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *co
     LV_CUDA(cudaStreamSynchronize(s));
     if (scratch_pinned[0] < kSevSym && n > 0) {
         symmetry_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev);
+        LV_LAUNCH_CHECK();
+        symmetry_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, dsev);
         LV_LAUNCH_CHECK();
     }
     unsigned long long tm = 0;

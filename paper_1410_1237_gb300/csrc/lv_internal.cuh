@@ -128,6 +128,47 @@ __device__ __forceinline__ bool prio_greater(unsigned long long hu, int u, unsig
     return hu > hv || (hu == hv && u > v);
 }
 
+// ------------------------------------------------------------ grid barrier
+// Barrier across all blocks of a cooperative (co-resident) launch.  The wait
+// is bounded: a block that waits longer than the limit sets *err and gets
+// false, and callers then return, so a fault can never hang the device.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 26;  // x ~50-100 ns sleeps
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int *vgen = &gb->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&gb->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&gb->count, 0u);
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*vgen == g) {
+                if (++spins > kBarrierSpinLimit) {
+                    ok = 0;
+                    atomicExch(err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok && (*(volatile int *)err == 0);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 // ------------------------------------------------------------- primitives
 // out[0..n] = exclusive prefix sums of in[0..n), out[n] = total (in == out allowed).
 lv_status scan_excl_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);

@@ -33,9 +33,14 @@ struct Buckets {
     int32_t *bucket_off = nullptr;   // device
     int32_t *hub_off = nullptr;      // device, n+1: hub hash-table offset per position
     int64_t hub_slots = 0;           // total hub table slots
-    int2 *hub_table = nullptr;       // device
+    int2 *hub_table = nullptr;       // device, {label, weight}, kept empty between uses
+    int32_t *hub_occ = nullptr;      // device, occupied-slot list per hub (same offsets)
+    int32_t *hub_cnt = nullptr;      // device, n: occupied count per position
+    int32_t *hub_chunk_off = nullptr;  // device, n+1: first arc chunk of each position
     int32_t *host_off = nullptr;     // host copy of bucket_off
+    int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
 };
+constexpr int kHubChunk = 4096;      // arcs per block of the hub accumulate kernel
 struct BinLimits {
     int small_max = 16, warp_max = 128, cta_max = 4096;
 };

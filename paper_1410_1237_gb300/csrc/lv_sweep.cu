@@ -15,7 +15,8 @@
 //   bin 0  8 lanes per vertex, hash table of <= 64 slots in shared memory
 //   bin 1  one warp per vertex, <= 512 slots in shared memory
 //   bin 2  one CTA per vertex, <= 8192 slots (64 KB) in shared memory
-//   bin 3  one CTA per vertex, table in global memory (hubs)
+//   bin 3  hubs: a table in global memory, filled by several CTAs per
+//          vertex (chunks of kHubChunk arcs) and evaluated by one CTA
 // Tables are open-addressing (linear probing) keyed by community label and
 // sized to the next power of two >= 2 * degree, so the load factor is <= 1/2
 // and every probe sequence ends; a probe count above the table size is an
@@ -42,6 +43,9 @@ struct SweepArgs {
     int nverts;
     int2 *hub_table;
     const int32_t *__restrict__ hub_off;  // table offset per position of `verts`
+    int32_t *hub_occ;                     // occupied-slot lists (same offsets)
+    int32_t *hub_cnt;                     // occupied count per position of `verts`
+    const int32_t *__restrict__ hub_chunk_off;  // first arc chunk per position of `verts`
 };
 
 __device__ __forceinline__ int pow2_at_least(int x) {
@@ -314,6 +318,126 @@ __global__ void __launch_bounds__(256) sweep_cta_kernel(SweepArgs a) {
     flush_stats(a, ein, dein, moved, err);
 }
 
+// ------------------------------------------------------------------ hubs
+// Hub vertices (degree above the CTA bin) are split into chunks of kHubChunk
+// arcs.  hub_accum: one block per chunk inserts its arcs into the hub's
+// global table, after merging equal labels within each warp; a thread that
+// claims an empty slot appends the slot to the hub's occupied list.
+// hub_decide: one block per hub evaluates only the occupied slots, resets
+// them to empty (so the table is clean for the next use) and decides.
+__global__ void __launch_bounds__(256) hub_accum_kernel(SweepArgs a) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int chunk = a.hub_chunk_off[0] + (int)blockIdx.x;
+    // position p of the hub owning this chunk: last p with hub_chunk_off[p] <= chunk
+    int lo = 0, hi = a.nverts;  // hub_chunk_off[nverts] > chunk
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (a.hub_chunk_off[mid] <= chunk) lo = mid; else hi = mid;
+    }
+    const int p = lo;
+    const int i = a.verts[p];
+    const int beg = a.off[i], end = a.off[i + 1];
+    const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+    int2 *tab = a.hub_table + a.hub_off[p];
+    int32_t *occ = a.hub_occ + a.hub_off[p];
+    int32_t *occ_cnt = a.hub_cnt + p;
+    const int start = beg + (chunk - a.hub_chunk_off[p]) * kHubChunk;
+    const int stop = min(end, start + kHubChunk);
+    int err = 0;
+    for (int base = start + w * 32; base < stop; base += 256) {
+        const int e = base + lane;
+        bool valid = e < stop;
+        int c = 0, wt = 0;
+        if (valid) {
+            const int2 arc = a.arcs[e];
+            valid = arc.x != i;
+            if (valid) {
+                c = a.C[arc.x];
+                wt = arc.y;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : -1 - lane);
+        const int sum = __reduce_add_sync(peers, wt);
+        if (valid && lane == __ffs(peers) - 1) {
+            unsigned h = hash32(c) & mask;
+            bool done = false;
+            for (unsigned probe = 0; probe <= mask; ++probe) {
+                int *kp = &tab[h].x;
+                const int cur = *((volatile int *)kp);
+                if (cur == c) {
+                    atomicAdd(&tab[h].y, sum);
+                    done = true;
+                    break;
+                }
+                if (cur == kEmpty) {
+                    const int prev = atomicCAS(kp, kEmpty, c);
+                    if (prev == kEmpty) occ[atomicAdd(occ_cnt, 1)] = (int)h;
+                    if (prev == kEmpty || prev == c) {
+                        atomicAdd(&tab[h].y, sum);
+                        done = true;
+                        break;
+                    }
+                }
+                h = (h + 1) & mask;
+            }
+            if (!done) err = 1;
+        }
+    }
+    if (err) atomicOr(&a.stats->err, 1);
+}
+
+__global__ void __launch_bounds__(1024) hub_decide_kernel(SweepArgs a) {
+    __shared__ long long rs[32];
+    __shared__ int rc[32], rz[32], re[32], reo[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p = blockIdx.x;
+    const int i = a.verts[p];
+    const int ci = a.C[i], ki = a.k[i];
+    int2 *tab = a.hub_table + a.hub_off[p];
+    const int32_t *occ = a.hub_occ + a.hub_off[p];
+    const int cnt = a.hub_cnt[p];
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    for (int t = threadIdx.x; t < cnt; t += 1024) {
+        const int h = occ[t];
+        const int2 kv = tab[h];
+        tab[h] = make_int2(kEmpty, 0);
+        eval_slot(a, kv.x, kv.y, ci, ki, b, e_old);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
+        best_shfl_xor(b, o);
+    }
+    if (lane == 0) {
+        rs[w] = b.s;
+        rc[w] = b.c;
+        rz[w] = b.size;
+        re[w] = b.e;
+        reo[w] = e_old;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Best t;
+        best_init(t);
+        int eo = 0;
+        for (int q = 0; q < 32; ++q) {
+            best_take(t, rs[q], rc[q], rz[q], re[q]);
+            eo += reo[q];
+        }
+        a.hub_cnt[p] = 0;
+        long long ein = 0, dein = 0;
+        if (decide(a, i, ci, ki, t, eo, ein, dein)) {
+            const int pos = atomicAdd(a.move_count, 1);
+            a.moves[pos] = make_int2(i, t.c);
+            atomicAdd(&a.stats->moved, 1);
+        }
+        if (ein) atomicAdd(&a.stats->sum_ein, (unsigned long long)ein);
+        if (dein) atomicAdd(&a.stats->delta_ein, (unsigned long long)dein);
+    }
+}
+
 // ------------------------------------------------------------ apply, a^2
 __global__ void apply_moves_kernel(int32_t *C, unsigned long long *comm,
                                    const int32_t *__restrict__ k, const int2 *__restrict__ moves,
@@ -387,6 +511,7 @@ lv_status sweep_class(PhaseState &ps, const Buckets &b, int cls, const BinLimits
     a.move_count = ps.move_count + cls;
     a.stats = ps.stats;
     a.hub_table = b.hub_table;
+    a.hub_occ = b.hub_occ;
     for (int bin = 0; bin < kBins; ++bin) {
         const int lo = b.host_off[cls * (kBins + 1) + bin];
         const int hi = b.host_off[cls * (kBins + 1) + bin + 1];
@@ -407,9 +532,16 @@ lv_status sweep_class(PhaseState &ps, const Buckets &b, int cls, const BinLimits
             sweep_cta_kernel<false>
                 <<<grid_for(cnt, 1, g_num_sms * 3), 256, 2 * kCtaSlots * sizeof(int), s>>>(a);
             break;
-        default:
-            sweep_cta_kernel<true><<<grid_for(cnt, 1, 65535), 256, 0, s>>>(a);
+        default: {
+            const int bq = cls * (kBins + 1) + bin;
+            const int nchunks = b.host_chunk[bq + 1] - b.host_chunk[bq];
+            a.hub_chunk_off = b.hub_chunk_off + lo;
+            a.hub_cnt = b.hub_cnt + lo;
+            hub_accum_kernel<<<nchunks, 256, 0, s>>>(a);
+            LV_LAUNCH_CHECK();
+            hub_decide_kernel<<<cnt, 1024, 0, s>>>(a);
             break;
+        }
         }
         LV_LAUNCH_CHECK();
         ++*launches;
