@@ -66,9 +66,13 @@ typedef struct {
     uint64_t color_seed;      /* seed of the colouring priority hash; phase p uses seed + p */
     int32_t collect_timing;   /* 0/1: record CUDA-event times per stage and per iteration */
     int32_t keep_graphs;      /* 0/1: keep every phase graph and colouring for inspection */
-    int32_t bin_small_max;    /* degree bins of the sweep; results do not depend on them */
-    int32_t bin_warp_max;     /*   (0 = defaults 16 / 128 / 4096; limits 32 / 256 / 4096) */
-    int32_t bin_cta_max;
+    /* Degree bins of the sweep (0 = default); results do not depend on them.
+     * A vertex of degree d <= bin_warp_max is swept by the smallest group of
+     * G = 1, 2, ..., 32 lanes with d <= G * bin_lane_arcs (else 32 lanes);
+     * d <= bin_cta_max by one CTA; larger (hubs) by several CTAs. */
+    int32_t bin_lane_arcs;    /* 1..8, default 4 */
+    int32_t bin_warp_max;     /* 1..256, default 128 */
+    int32_t bin_cta_max;      /* bin_warp_max+1 .. 4096, default 4096 */
     int32_t reserved;
 } lv_params;
 
@@ -85,7 +89,7 @@ typedef struct {
     int32_t colored;    /* 1 if the phase swept colour classes */
     int32_t num_colors; /* colour classes (0 if not coloured) */
     int32_t iterations; /* iterations of Alg. 1's while-loop */
-    int32_t reserved;
+    int32_t color_rounds; /* rounds of the Jones-Plassmann colouring (0 if not coloured) */
     double ms_color;    /* CUDA-event times (collect_timing), else -1 */
     double ms_iterate;
     double ms_rebuild;

@@ -228,6 +228,7 @@ lv_status read_stats(lv_graph *h, const PhaseState &ps, IterStats *hs) {
     LV_CUDA(cudaMemcpyAsync(h->pinned, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, h->stream));
     LV_CUDA(cudaStreamSynchronize(h->stream));
     std::memcpy(hs, h->pinned, sizeof(IterStats));
+    if (hs->bar_err) return LV_ERR_TIMEOUT;
     if (hs->err) return LV_ERR_HASH;
     return LV_OK;
 }
@@ -263,9 +264,9 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
         LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
         LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t), s));
         const int e0 = h->timer.mark();
-        LV_TRY(sweep_class(ps, b, 0, lim, &h->stats.sweep_launches, s));
+        LV_TRY(sweep_iteration(ps, b, s));
+        ++h->stats.sweep_launches;
         const int e1 = h->timer.mark();
-        LV_TRY(sum_a2(ps, s));
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
         const int64_t N_prev = ps.two_m * (int64_t)hs.sum_ein - (int64_t)hs.sum_a2;  // N(C^{step-1})
@@ -294,7 +295,7 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
                 return LV_OK;
             }
         }
-        LV_TRY(apply_moves(ps, 0, s));
+        LV_TRY(apply_moves(ps, s));
         moved_prev = moved;
         ev_prev0 = e0;
         ev_prev1 = e1;
@@ -306,24 +307,16 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
                           double theta, int32_t max_iters, int phase, int64_t sum_loops,
                           std::vector<IterRecord> &recs, IterResult *out) {
     cudaStream_t s = h->stream;
-    const int K = b.classes;
-    // classes holding at least one vertex with arcs
-    std::vector<int> active;
-    for (int c = 0; c < K; ++c)
-        if (b.host_off[c * (kBins + 1) + kBins] > b.host_off[c * (kBins + 1)]) active.push_back(c);
     bool have_np = false;
     int64_t n_p = 0;
     int64_t sum_ein = sum_loops;
     for (int t = 1;; ++t) {
         LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * (size_t)K, s));
+        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * (size_t)ps.n_act, s));
         const int e0 = h->timer.mark();
-        for (int c : active) {
-            LV_TRY(sweep_class(ps, b, c, lim, &h->stats.sweep_launches, s));
-            LV_TRY(apply_moves(ps, c, s));
-        }
+        LV_TRY(sweep_iteration(ps, b, s));
+        ++h->stats.sweep_launches;
         const int e1 = h->timer.mark();
-        LV_TRY(sum_a2(ps, s));
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
         sum_ein += (int64_t)hs.delta_ein;
@@ -331,7 +324,7 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
         IterRecord r;
         r.st.phase = phase;
         r.st.iter = t;
-        r.st.color_steps = (int32_t)active.size();
+        r.st.color_steps = (int32_t)ps.n_act;
         r.st.moved = hs.moved;
         r.st.N = N;
         r.st.arcs = ps.g.A;
@@ -365,10 +358,10 @@ lv_status copy_graph(const DGraph &src, DGraph *dst, cudaStream_t s) {
 lv_status run_impl(lv_graph *h, const lv_params &P) {
     cudaStream_t s = h->stream;
     BinLimits lim;
-    if (P.bin_small_max) lim.small_max = P.bin_small_max;
+    if (P.bin_lane_arcs) lim.lane_arcs = P.bin_lane_arcs;
     if (P.bin_warp_max) lim.warp_max = P.bin_warp_max;
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
-    if (lim.small_max < 1 || lim.small_max > kSmallMaxLimit || lim.warp_max <= lim.small_max ||
+    if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
         lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit)
         return LV_ERR_ARG;
     if (P.max_iters < 1 || P.max_phases < 1 || !(P.theta_low >= -1e300) ||
@@ -412,9 +405,13 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     PhaseState ps;
     int32_t *newid = nullptr, *color = nullptr;
     LV_TRY(dalloc_n(&ps.C, (size_t)nmax, s));
-    LV_TRY(dalloc_n(&ps.comm, (size_t)nmax, s));
-    LV_TRY(dalloc_n(&ps.moves, (size_t)nmax, s));
+    LV_TRY(dalloc_n(&ps.comm[0], (size_t)nmax, s));
+    LV_TRY(dalloc_n(&ps.comm[1], (size_t)nmax, s));
+    LV_TRY(dalloc_n(&ps.moves[0], (size_t)nmax, s));
+    LV_TRY(dalloc_n(&ps.moves[1], (size_t)nmax, s));
     LV_TRY(dalloc_n(&ps.stats, 1, s));
+    ps.bar = &ps.stats->bar;
+    ps.bar_err = &ps.stats->bar_err;
     LV_TRY(dalloc_n(&newid, (size_t)nmax + 1, s));
     LV_TRY(dalloc_n(&color, (size_t)nmax, s));
     ps.two_m = h->two_m;
@@ -441,7 +438,10 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         // ---- colouring and vertex order
         const int ev_c0 = h->timer.mark();
         int32_t K = 1;
-        if (colour_on) LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, color, &K, h->pinned, s));
+        int32_t rounds = 0;
+        if (colour_on)
+            LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, color, &K, &rounds, h->pinned, s));
+        info.color_rounds = rounds;
         info.num_colors = colour_on ? K : 0;
         Buckets b;
         LV_TRY(bucket_vertices(G, colour_on ? color : nullptr, K, lim, &b, h->pinned, s));
@@ -459,7 +459,19 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         ps.g = G;
         ps.k = k;
         ps.loop = loop;
-        LV_TRY(dalloc_n(&ps.move_count, (size_t)K, s));
+        ps.coloured = colour_on;
+        {
+            // classes holding at least one vertex with arcs, in ascending colour
+            std::vector<int32_t> act;
+            for (int c = 0; c < K; ++c)
+                if (b.host_off[c * (kBins + 1) + kBins] > b.host_off[c * (kBins + 1)]) act.push_back(c);
+            if (act.empty()) act.push_back(0);
+            ps.n_act = (int)act.size();
+            LV_TRY(dalloc_n(&ps.act, act.size(), s));
+            LV_CUDA(cudaMemcpyAsync(ps.act, act.data(), sizeof(int32_t) * act.size(),
+                                    cudaMemcpyHostToDevice, s));
+        }
+        LV_TRY(dalloc_n(&ps.move_count, (size_t)ps.n_act + 1, s));
         const int ev_i0 = h->timer.mark();
         LV_TRY(init_phase(ps, s));
         IterStats hs0;
@@ -478,7 +490,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
 
         // ---- rebuild (Sec. 4.5): renumber, labels, coarse graph
         const int ev_r0 = h->timer.mark();
-        LV_TRY(renumber(G.n, ps.comm, newid, s));
+        LV_TRY(renumber(G.n, current_comm(ps), newid, s));
         LV_CUDA(cudaMemcpyAsync(h->pinned, newid + G.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LV_CUDA(cudaStreamSynchronize(s));
         const int32_t n_next = h->pinned[0];
@@ -511,8 +523,11 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
             loop = loop_own = l2;
         }
         const int ev_r1 = h->timer.mark();
+        LV_CUDA(cudaStreamSynchronize(s));  // the host copy of act must outlive its transfer
         dfree(ps.move_count, s);
         ps.move_count = nullptr;
+        dfree(ps.act, s);
+        ps.act = nullptr;
         free_buckets(b, s);
         info.ms_color = -1.0;
         info.ms_iterate = -1.0;
@@ -558,8 +573,10 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     dfree(loop_own, s);
     dfree(map, s);
     dfree(ps.C, s);
-    dfree(ps.comm, s);
-    dfree(ps.moves, s);
+    dfree(ps.comm[0], s);
+    dfree(ps.comm[1], s);
+    dfree(ps.moves[0], s);
+    dfree(ps.moves[1], s);
     dfree(ps.stats, s);
     dfree(newid, s);
     dfree(color, s);
@@ -630,7 +647,6 @@ lv_status lv_get_phase_info(const lv_graph *g, int32_t phase, lv_phase_info *out
     const PhaseRec *r = phase_at(g, phase);
     if (!r) return LV_ERR_STATE;
     *out = r->info;
-    out->reserved = 0;
     return LV_OK;
 }
 

@@ -6,14 +6,17 @@
 // decrements the counts of its lower-priority neighbours.  The result equals
 // greedy colouring in decreasing priority order, whatever the timing, because
 // a vertex's colour depends only on its higher-priority neighbours' colours.
-// On power-law graphs the priority DAG is deep (hundreds to thousands of
-// rounds), so all rounds run inside one cooperative launch separated by a
-// bounded grid barrier; a ready vertex of high degree is handled by a whole
-// CTA, the others by one warp each.
+// On power-law graphs the priority DAG is deep (1,600 to 3,800 rounds on the
+// R-MAT and Chung-Lu inputs), so all rounds run inside one cooperative launch
+// separated by a bounded grid barrier.  Ready vertices are handled by size:
+// small (< 256 arcs) one warp each; big (< 4,096 arcs) one block each; huge
+// ones are split over all blocks, which mark a shared global colour bitmap,
+// and get their colour after a second barrier.
 //
 // Vertex order: a stable radix sort of (colour, degree bin) keys, so each
 // colour class is split into the group / warp / CTA / hub bins of the sweep,
-// ascending vertex id inside each bucket.
+// ascending vertex id inside each bucket.  Bins: groups of 1..32 lanes per
+// vertex (about lane_arcs arcs per lane), CTA, hub (several CTAs).
 #include "lv_ops.cuh"
 
 namespace lv {
@@ -21,134 +24,124 @@ namespace {
 
 constexpr int kJpBlock = 1024;       // threads per block of the persistent kernel
 constexpr int kJpWarps = kJpBlock / 32;
-constexpr int kJpBigDegree = 512;    // vertices with at least this many arcs use a whole CTA
+constexpr int kJpBig = 256;          // arcs: from here a vertex uses a whole block
+constexpr int kJpHuge = 4096;        // arcs: from here a vertex is split over blocks
 constexpr int kMexWindow = 1024;     // colours examined per pass of the mex search
 
+// device state; the ring of list lengths has 3 slots of {small, big, huge}
 struct JpState {
-    int32_t *cnt;          // higher-priority neighbours not yet coloured
+    int32_t *cnt;          // higher-priority neighbours not yet processed
     int32_t *color;
-    int32_t *small_list[2];
-    int32_t *big_list[2];
-    int32_t *counts;       // ring of 3 x {small, big} list lengths
+    int32_t *list[3][2];   // [kind][round parity]
+    int32_t *counts;       // [3 ring slots][3 kinds]
     int32_t *max_color;
+    unsigned *huge_bm;     // 32-word first-window bitmap per slot of the huge list
     GridBarrier *bar;
     int *err;
+    int32_t *rounds;
+    TraceBuf tb;
 };
 
 __device__ __forceinline__ int degree_of(const DGraph &g, int u) { return g.off[u + 1] - g.off[u]; }
 
-// append u to the next round's small or big list; warp-aggregated
+// append u to the next round's list of its kind; warp-aggregated
 __device__ __forceinline__ void push_ready(const DGraph &g, const JpState &st, int32_t *cnt_next,
                                            int nxt_list, bool ready, int u) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const bool big = ready && degree_of(g, u) >= kJpBigDegree;
-    const unsigned bs = __ballot_sync(0xffffffffu, ready && !big);
-    const unsigned bb = __ballot_sync(0xffffffffu, big);
-    int ps = 0, pb = 0;
-    if (lane == 0) {
-        if (bs) ps = atomicAdd(&cnt_next[0], __popc(bs));
-        if (bb) pb = atomicAdd(&cnt_next[1], __popc(bb));
+    int kind = 0;
+    if (ready) {
+        const int d = degree_of(g, u);
+        kind = d >= kJpHuge ? 2 : (d >= kJpBig ? 1 : 0);
     }
-    ps = __shfl_sync(0xffffffffu, ps, 0);
-    pb = __shfl_sync(0xffffffffu, pb, 0);
-    if (ready && !big) st.small_list[nxt_list][ps + __popc(bs & lt)] = u;
-    if (big) st.big_list[nxt_list][pb + __popc(bb & lt)] = u;
-}
-
-// mark the colours of v's higher-priority neighbours that fall in
-// [base, base + kMexWindow); arcs e = first, first + step, ...
-__device__ __forceinline__ void mark_window(const DGraph &g, unsigned long long seed, int v,
-                                            unsigned long long hv, const int32_t *color, int beg,
-                                            int end, int first, int step, int base, unsigned *bm) {
-    for (int e = beg + first; e < end; e += step) {
-        const int u = g.arcs[e].x;
-        if (u != v && prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v)) {
-            const int c = __ldcg(&color[u]) - base;
-            if (c >= 0 && c < kMexWindow) atomicOr(&bm[c >> 5], 1u << (c & 31));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool mine = ready && kind == k;
+        const unsigned bm = __ballot_sync(0xffffffffu, mine);
+        if (bm) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(&cnt_next[k], __popc(bm));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (mine) st.list[k][nxt_list][pos + __popc(bm & lt)] = u;
         }
     }
 }
 
-// one warp colours v and releases its lower-priority neighbours
-__device__ void jp_small(const DGraph &g, unsigned long long seed, const JpState &st, int v,
-                         int32_t *cnt_next, int nxt_list, unsigned *bm) {
+// One pass over arcs [e0, e1) of v by `nw` warps (this warp has rank
+// `wrank`): the colour of every higher-priority neighbour is marked in the
+// first window [0, kMexWindow) of bm (shared or global memory), and every
+// lower-priority neighbour's count is decremented (and the neighbour queued
+// for the next round when it reaches zero).  The two kinds of arcs are
+// disjoint, so one pass serves both.
+__device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState &st, int v,
+                        unsigned long long hv, int e0, int e1, int wrank, int nw, unsigned *bm,
+                        int32_t *cnt_next, int nxt_list) {
+    constexpr int kU = 4;  // chunks of 32 arcs in flight per warp
     const int lane = threadIdx.x & 31;
-    const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+    const int stride = nw * 32;
+    for (int b0 = e0 + wrank * 32; b0 < e1; b0 += kU * stride) {
+        int uu[kU];
+        bool higher[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = b0 + u * stride + lane;
+            uu[u] = e < e1 ? g.arcs[e].x : v;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            higher[u] = uu[u] != v &&
+                        prio_greater(prio_hash((unsigned long long)uu[u] ^ seed), uu[u], hv, v);
+        int res[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (uu[u] == v) res[u] = 0;
+            else if (higher[u]) res[u] = __ldcg(&st.color[uu[u]]);
+            else res[u] = atomicSub(&st.cnt[uu[u]], 1);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (uu[u] != v && higher[u] && res[u] < kMexWindow)
+                atomicOr(&bm[res[u] >> 5], 1u << (res[u] & 31));
+            push_ready(g, st, cnt_next, nxt_list, uu[u] != v && !higher[u] && res[u] == 1, uu[u]);
+        }
+    }
+}
+
+// Smallest colour of v not in the window bitmap whose word l is held by lane
+// l; windows above the first are searched by mark-only passes of this warp
+// over v's whole row (needs >= kMexWindow colours among v's higher-priority
+// neighbours).
+__device__ int warp_mex(const DGraph &g, unsigned long long seed, const JpState &st, int v,
+                        unsigned long long hv, unsigned word0, unsigned *scratch32) {
+    const int lane = threadIdx.x & 31;
+    unsigned word = word0;
     const int beg = g.off[v], end = g.off[v + 1];
-    int mex = -1;
-    for (int base = 0; mex < 0; base += kMexWindow) {
-        bm[lane] = 0u;
-        __syncwarp();
-        mark_window(g, seed, v, hv, st.color, beg, end, lane, 32, base, bm);
-        __syncwarp();
-        const unsigned word = bm[lane];
+    for (int base = 0;; base += kMexWindow) {
         const unsigned notfull = __ballot_sync(0xffffffffu, word != 0xffffffffu);
         if (notfull) {
             const int f = __ffs(notfull) - 1;
             const unsigned wf = __shfl_sync(0xffffffffu, word, f);
-            mex = base + 32 * f + __ffs(~wf) - 1;
+            return base + 32 * f + __ffs(~wf) - 1;
+        }
+        const int nb = base + kMexWindow;
+        scratch32[lane] = 0u;
+        __syncwarp();
+        for (int e = beg + lane; e < end; e += 32) {
+            const int u = g.arcs[e].x;
+            if (u != v && prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v)) {
+                const int c = __ldcg(&st.color[u]) - nb;
+                if (c >= 0 && c < kMexWindow) atomicOr(&scratch32[c >> 5], 1u << (c & 31));
+            }
         }
         __syncwarp();
-    }
-    if (lane == 0) {
-        __stcg(&st.color[v], mex);
-        atomicMax(st.max_color, mex);
-    }
-    for (int b0 = beg; b0 < end; b0 += 32) {
-        const int e = b0 + lane;
-        bool ready = false;
-        int u = 0;
-        if (e < end) {
-            u = g.arcs[e].x;
-            if (u != v && prio_greater(hv, v, prio_hash((unsigned long long)u ^ seed), u))
-                ready = (atomicSub(&st.cnt[u], 1) == 1);
-        }
-        push_ready(g, st, cnt_next, nxt_list, ready, u);
+        word = scratch32[lane];
+        __syncwarp();
     }
 }
 
-// one CTA colours a high-degree v
-__device__ void jp_big(const DGraph &g, unsigned long long seed, const JpState &st, int v,
-                       int32_t *cnt_next, int nxt_list, unsigned *bm, int *s_mex) {
-    const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
-    const int beg = g.off[v], end = g.off[v + 1];
-    for (int base = 0;; base += kMexWindow) {
-        if (threadIdx.x < 32) bm[threadIdx.x] = 0u;
-        __syncthreads();
-        mark_window(g, seed, v, hv, st.color, beg, end, threadIdx.x, kJpBlock, base, bm);
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            const unsigned word = bm[threadIdx.x];
-            const unsigned notfull = __ballot_sync(0xffffffffu, word != 0xffffffffu);
-            if (threadIdx.x == 0) {
-                if (notfull) {
-                    const int f = __ffs(notfull) - 1;
-                    *s_mex = base + 32 * f + __ffs(~bm[f]) - 1;
-                } else {
-                    *s_mex = -1;
-                }
-            }
-        }
-        __syncthreads();
-        if (*s_mex >= 0) break;
-    }
-    if (threadIdx.x == 0) {
-        __stcg(&st.color[v], *s_mex);
-        atomicMax(st.max_color, *s_mex);
-    }
-    for (int b0 = beg; b0 < end; b0 += kJpBlock) {
-        const int e = b0 + (int)threadIdx.x;
-        bool ready = false;
-        int u = 0;
-        if (e < end) {
-            u = g.arcs[e].x;
-            if (u != v && prio_greater(hv, v, prio_hash((unsigned long long)u ^ seed), u))
-                ready = (atomicSub(&st.cnt[u], 1) == 1);
-        }
-        push_ready(g, st, cnt_next, nxt_list, ready, u);
-    }
-    __syncthreads();
+__device__ __forceinline__ void set_color(const JpState &st, int v, int mex) {
+    __stcg(&st.color[v], mex);
+    atomicMax(st.max_color, mex);
 }
 
 __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long long seed, JpState st) {
@@ -168,35 +161,100 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
             st.cnt[v] = c;
             st.color[v] = -1;
         }
-        // round 0 lists (ring slot 0)
-        push_ready(g, st, st.counts, 0, lane == 0 && c == 0, v);
+        push_ready(g, st, st.counts, 0, lane == 0 && c == 0, v);  // round 0, ring slot 0
     }
 }
 
-// All rounds of Jones-Plassmann in one cooperative launch; rounds are
-// separated by a bounded grid barrier.
+// All rounds of Jones-Plassmann in one cooperative launch.  Round r:
+//   stage 1  huge ready vertices: split over P = grid / n_huge blocks each,
+//            which mark a global bitmap and release lower-priority
+//            neighbours; big ones: one block each (mark, release, colour);
+//            small ones: one warp each
+//   barrier
+//   stage 2  one warp per huge vertex turns its bitmap into its colour and
+//            clears the bitmap                             [barrier]
+// The vertices released in round r are coloured in round r + 1, after the
+// colours they depend on have been written.
 __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsigned long long seed,
                                                                  JpState st) {
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
-    __shared__ int s_mex;
-    const int wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kJpWarps + wib;
     const int nwarps = gridDim.x * kJpWarps;
     for (int r = 0;; ++r) {
         const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
-        if (blockIdx.x == 0 && threadIdx.x < 2) st.counts[2 * clr + threadIdx.x] = 0;
-        const int n_small = __ldcg(&st.counts[2 * cur]);
-        const int n_big = __ldcg(&st.counts[2 * cur + 1]);
+        if (blockIdx.x == 0 && threadIdx.x < 3) st.counts[3 * clr + threadIdx.x] = 0;
+        const int n_small = __ldcg(&st.counts[3 * cur]);
+        const int n_big = __ldcg(&st.counts[3 * cur + 1]);
+        const int n_huge = __ldcg(&st.counts[3 * cur + 2]);
         const int in_list = r & 1, out_list = (r + 1) & 1;
-        int32_t *cnt_next = st.counts + 2 * nxt;
-        for (int t = blockIdx.x; t < n_big; t += gridDim.x)
-            jp_big(g, seed, st, __ldcg(&st.big_list[in_list][t]), cnt_next, out_list, bm_cta, &s_mex);
-        for (int t = gw; t < n_small; t += nwarps)
-            jp_small(g, seed, st, __ldcg(&st.small_list[in_list][t]), cnt_next, out_list,
-                     bm_warp[wib]);
+        int32_t *cnt_next = st.counts + 3 * nxt;
+        const unsigned long long tr0 = LV_TRACE_ON ? gtimer() : 0;
+        if (n_huge > 0) {
+            const int P = max(1, (int)gridDim.x / n_huge);
+            for (int item = blockIdx.x; item < n_huge * P; item += gridDim.x) {
+                const int t = item % n_huge, part = item / n_huge;
+                const int v = __ldcg(&st.list[2][in_list][t]);
+                const int beg = g.off[v], end = g.off[v + 1];
+                const int L = (end - beg + P - 1) / P;
+                const int e0 = beg + part * L, e1 = min(end, e0 + L);
+                jp_pass(g, seed, st, v, prio_hash((unsigned long long)v ^ seed), e0, e1, wib, kJpWarps,
+                        st.huge_bm + (size_t)t * 32, cnt_next, out_list);
+            }
+        }
+        for (int t = blockIdx.x; t < n_big; t += gridDim.x) {
+            const int v = __ldcg(&st.list[1][in_list][t]);
+            const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+            if (threadIdx.x < 32) bm_cta[threadIdx.x] = 0u;
+            __syncthreads();
+            jp_pass(g, seed, st, v, hv, g.off[v], g.off[v + 1], wib, kJpWarps, bm_cta, cnt_next,
+                    out_list);
+            __syncthreads();
+            if (wib == 0) {
+                const int mex = warp_mex(g, seed, st, v, hv, bm_cta[lane], bm_warp[0]);
+                if (lane == 0) set_color(st, v, mex);
+            }
+            __syncthreads();
+        }
+        for (int t = gw; t < n_small; t += nwarps) {
+            const int v = __ldcg(&st.list[0][in_list][t]);
+            const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+            unsigned *bm = bm_warp[wib];
+            bm[lane] = 0u;
+            __syncwarp();
+            jp_pass(g, seed, st, v, hv, g.off[v], g.off[v + 1], 0, 1, bm, cnt_next, out_list);
+            __syncwarp();
+            const unsigned w0 = bm[lane];
+            __syncwarp();
+            const int mex = warp_mex(g, seed, st, v, hv, w0, bm);
+            if (lane == 0) set_color(st, v, mex);
+            __syncwarp();
+        }
+        const unsigned long long tr1 = LV_TRACE_ON ? gtimer() : 0;
+        if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 8)
+            trace4(st.tb, 0x100000000ull | (unsigned)r, (unsigned long long)blockIdx.x, tr0, tr1);
         if (!grid_sync(st.bar, st.err)) return;
-        if (__ldcg(&cnt_next[0]) + __ldcg(&cnt_next[1]) == 0) return;
+        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
+            trace4(st.tb, 0x200000000ull | (unsigned)r,
+                   ((unsigned long long)n_small << 32) | (unsigned)(n_big + n_huge), gtimer(), 0);
+        if (n_huge > 0) {
+            for (int t = gw; t < n_huge; t += nwarps) {
+                const int v = __ldcg(&st.list[2][in_list][t]);
+                unsigned *gbm = st.huge_bm + (size_t)t * 32;
+                const unsigned w0 = __ldcg(&gbm[lane]);
+                __stcg(&gbm[lane], 0u);
+                const int mex = warp_mex(g, seed, st, v, prio_hash((unsigned long long)v ^ seed), w0,
+                                         bm_warp[wib]);
+                if (lane == 0) set_color(st, v, mex);
+                __syncwarp();
+            }
+            if (!grid_sync(st.bar, st.err)) return;
+        }
+        if (__ldcg(&cnt_next[0]) + __ldcg(&cnt_next[1]) + __ldcg(&cnt_next[2]) == 0) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *st.rounds = r + 1;
+            return;
+        }
         if (r > g.n) {  // every round colours at least one vertex
             if (threadIdx.x == 0) atomicExch(st.err, 2);
             return;
@@ -211,10 +269,11 @@ __global__ void bucket_key_kernel(DGraph g, const int32_t *__restrict__ color, B
         const int deg = g.off[v + 1] - g.off[v];
         int bin;
         if (deg == 0) bin = kBinSkip;
-        else if (deg <= lim.small_max) bin = 0;
-        else if (deg <= lim.warp_max) bin = 1;
-        else if (deg <= lim.cta_max) bin = 2;
-        else bin = 3;
+        else if (deg <= lim.warp_max) {
+            bin = 0;  // smallest group of G = 2^bin lanes with deg <= G * lane_arcs
+            while (bin < kGroupBins - 1 && deg > (1 << bin) * lim.lane_arcs) ++bin;
+        } else if (deg <= lim.cta_max) bin = kBinCta;
+        else bin = kBinHub;
         const int cls = color ? color[v] : 0;
         keys[v] = (uint32_t)(cls * (kBins + 1) + bin);
         vals[v] = (uint32_t)v;
@@ -264,22 +323,26 @@ __global__ void gather_at_kernel(const int32_t *__restrict__ vals, const int32_t
 }  // namespace
 
 lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_colors,
-                   int *pinned, cudaStream_t s) {
+                   int32_t *rounds, int *pinned, cudaStream_t s) {
     const int n = g.n;
     JpState st;
     st.color = color;
+    st.tb = trace_buffer();
     LV_TRY(dalloc_n(&st.cnt, (size_t)n, s));
-    LV_TRY(dalloc_n(&st.small_list[0], (size_t)n, s));
-    LV_TRY(dalloc_n(&st.small_list[1], (size_t)n, s));
-    LV_TRY(dalloc_n(&st.big_list[0], (size_t)n, s));
-    LV_TRY(dalloc_n(&st.big_list[1], (size_t)n, s));
-    int32_t *small_state = nullptr;  // counts[6], max_color, err, barrier
+    for (int k = 0; k < 3; ++k)
+        for (int p = 0; p < 2; ++p) LV_TRY(dalloc_n(&st.list[k][p], (size_t)n, s));
+    const size_t max_huge = (size_t)g.A / kJpHuge + 1;  // each has >= kJpHuge arcs
+    LV_TRY(dalloc_n(&st.huge_bm, 32 * max_huge, s));
+    LV_CUDA(cudaMemsetAsync(st.huge_bm, 0, sizeof(unsigned) * 32 * max_huge, s));
+    // counts[9], max_color, err, barrier (2 words), rounds
+    int32_t *small_state = nullptr;
     LV_TRY(dalloc_n(&small_state, 16, s));
     LV_CUDA(cudaMemsetAsync(small_state, 0, 16 * sizeof(int32_t), s));
     st.counts = small_state;
-    st.max_color = small_state + 6;
-    st.err = small_state + 7;
-    st.bar = reinterpret_cast<GridBarrier *>(small_state + 8);
+    st.max_color = small_state + 9;
+    st.err = small_state + 10;
+    st.bar = reinterpret_cast<GridBarrier *>(small_state + 11);
+    st.rounds = small_state + 13;
     jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, st);
     LV_LAUNCH_CHECK();
     static int blocks_per_sm = 0;
@@ -294,16 +357,16 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms * blocks_per_sm),
                                         dim3(kJpBlock), args, 0, s));
     LV_LAUNCH_CHECK();
-    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 6, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 9, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
     if (pinned[1] == 1) return LV_ERR_TIMEOUT;
     if (pinned[1] != 0) return LV_ERR_STATE;
     *num_colors = pinned[0] + 1;
+    *rounds = pinned[4];
     dfree(st.cnt, s);
-    dfree(st.small_list[0], s);
-    dfree(st.small_list[1], s);
-    dfree(st.big_list[0], s);
-    dfree(st.big_list[1], s);
+    for (int k = 0; k < 3; ++k)
+        for (int p = 0; p < 2; ++p) dfree(st.list[k][p], s);
+    dfree(st.huge_bm, s);
     dfree(small_state, s);
     return LV_OK;
 }
@@ -332,10 +395,10 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     LV_CUDA(cudaMemcpyAsync(b->host_off, b->bucket_off, sizeof(int32_t) * ((size_t)nb + 1),
                             cudaMemcpyDeviceToHost, s));
     // hub tables: slots, occupied lists, arc chunks
-    int32_t *chunk_at = nullptr;
     LV_TRY(dalloc_n(&b->hub_off, (size_t)n + 1, s));
     LV_TRY(dalloc_n(&b->hub_chunk_off, (size_t)n + 1, s));
-    LV_TRY(dalloc_n(&chunk_at, (size_t)nb + 1, s));
+    LV_TRY(dalloc_n(&b->hub_chunk_at, (size_t)nb + 1, s));
+    int32_t *chunk_at = b->hub_chunk_at;
     hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_off, b->hub_chunk_off);
     LV_LAUNCH_CHECK();
     LV_TRY(scan_excl_i32(b->hub_off, b->hub_off, n, s));
@@ -348,13 +411,15 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
                             cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaMemcpyAsync(pinned, b->hub_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
-    dfree(chunk_at, s);
     b->hub_slots = pinned[0];
     if (b->hub_slots > 0) {
         LV_TRY(dalloc_n(&b->hub_table, (size_t)b->hub_slots, s));
         LV_TRY(dalloc_n(&b->hub_occ, (size_t)b->hub_slots, s));
         LV_TRY(dalloc_n(&b->hub_cnt, (size_t)n, s));
         LV_CUDA(cudaMemsetAsync(b->hub_cnt, 0, sizeof(int32_t) * (size_t)n, s));
+        LV_TRY(dalloc_n(&b->hub_done, (size_t)n, s));
+        LV_CUDA(cudaMemsetAsync(b->hub_done, 0, sizeof(int32_t) * (size_t)n, s));
+        LV_TRY(dalloc(&b->hub_part, hub_part_bytes() * (b->host_chunk[nb] + 1), s));
         fill_empty_kernel<<<grid_for(b->hub_slots, 256, g_num_sms * 8), 256, 0, s>>>(b->hub_table,
                                                                                    b->hub_slots);
         LV_LAUNCH_CHECK();
@@ -373,6 +438,9 @@ void free_buckets(Buckets &b, cudaStream_t s) {
     dfree(b.hub_occ, s);
     dfree(b.hub_cnt, s);
     dfree(b.hub_chunk_off, s);
+    dfree(b.hub_chunk_at, s);
+    dfree(b.hub_part, s);
+    dfree(b.hub_done, s);
     delete[] b.host_off;
     delete[] b.host_chunk;
     b = Buckets();

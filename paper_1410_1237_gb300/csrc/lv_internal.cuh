@@ -22,13 +22,17 @@
 namespace lv {
 
 constexpr int kEmpty = -1;           // empty hash slot (labels are >= 0)
-constexpr int kBins = 4;             // sweep bins: group / warp / CTA / hub
+// Sweep bins: 0..5 = groups of G = 1, 2, 4, 8, 16, 32 lanes per vertex,
+// 6 = one CTA per vertex, 7 = hubs (several CTAs per vertex).
+constexpr int kGroupBins = 6;
+constexpr int kBins = 8;
 constexpr int kBinSkip = kBins;      // isolated vertices (no arcs)
-constexpr int kSmallMaxLimit = 32;   // group-bin table holds 2x this
-constexpr int kWarpMaxLimit = 256;   // warp-bin table holds 2x this
+constexpr int kBinCta = 6;
+constexpr int kBinHub = 7;
+constexpr int kLaneArcsLimit = 8;    // a group of G lanes takes <= G * lane_arcs arcs
+constexpr int kWarpMaxLimit = 256;   // warp table holds 2x this
 constexpr int kCtaMaxLimit = 4096;   // CTA-bin table holds 2x this (64 KB)
-constexpr int kGroupLanes = 8;       // lanes per vertex in the group bin
-constexpr int kGroupSlots = 2 * kSmallMaxLimit;
+constexpr int kGroupTableInts = 512;  // per warp: every group's table slots
 constexpr int kWarpSlots = 2 * kWarpMaxLimit;
 constexpr int kCtaSlots = 2 * kCtaMaxLimit;
 
@@ -136,7 +140,7 @@ struct GridBarrier {
     unsigned int count;
     unsigned int gen;
 };
-constexpr unsigned long long kBarrierSpinLimit = 1ull << 26;  // x ~50-100 ns sleeps
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 27;  // x ~20-100 ns sleeps
 
 __device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
     __shared__ int s_ok;
@@ -159,7 +163,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
                     atomicExch(err, 1);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(20);
             }
         }
         __threadfence();
@@ -167,6 +171,46 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// ----------------------------------------------------------------- tracing
+// Builds with -DLV_TRACE record %globaltimer stamps at the stage boundaries
+// of the persistent kernels into a device buffer (read back by a profiling
+// driver); in normal builds the buffer pointer is null and the calls vanish.
+struct TraceBuf {
+    unsigned long long *buf = nullptr;
+    unsigned int *n = nullptr;
+};
+#ifdef LV_TRACE
+#define LV_TRACE_ON 1
+#else
+#define LV_TRACE_ON 0
+#endif
+TraceBuf trace_buffer();  // the process-wide buffer (null unless LV_TRACE)
+constexpr unsigned kTraceCap = 1u << 20;
+__device__ __forceinline__ unsigned long long gtimer() {
+#ifdef LV_TRACE
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+#else
+    return 0;
+#endif
+}
+__device__ __forceinline__ void trace4(const TraceBuf &tb, unsigned long long a,
+                                       unsigned long long b, unsigned long long c,
+                                       unsigned long long d) {
+#ifdef LV_TRACE
+    const unsigned i = atomicAdd(tb.n, 4u);
+    if (i + 4 <= kTraceCap) {
+        tb.buf[i] = a;
+        tb.buf[i + 1] = b;
+        tb.buf[i + 2] = c;
+        tb.buf[i + 3] = d;
+    }
+#else
+    (void)tb; (void)a; (void)b; (void)c; (void)d;
+#endif
 }
 
 // ------------------------------------------------------------- primitives

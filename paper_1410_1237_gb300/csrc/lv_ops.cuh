@@ -22,7 +22,7 @@ void free_graph(DGraph &g, cudaStream_t s);
 // lv_color.cu ------------------------------------------------------------
 // Jones-Plassmann distance-1 colouring with priority (h(v ^ seed), v).
 lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_colors,
-                   int *scratch_pinned, cudaStream_t s);
+                   int32_t *rounds, int *scratch_pinned, cudaStream_t s);
 
 // Vertex order of a phase: vertices grouped by (colour class, degree bin),
 // ascending id inside a group.  order[n], bucket_off[(classes*(kBins+1))+1]
@@ -37,12 +37,15 @@ struct Buckets {
     int32_t *hub_occ = nullptr;      // device, occupied-slot list per hub (same offsets)
     int32_t *hub_cnt = nullptr;      // device, n: occupied count per position
     int32_t *hub_chunk_off = nullptr;  // device, n+1: first arc chunk of each position
+    int32_t *hub_chunk_at = nullptr;   // device: hub_chunk_off at every bucket boundary
+    void *hub_part = nullptr;          // device: partial best per hub chunk
+    int32_t *hub_done = nullptr;       // device, n: finished decide chunks per position
     int32_t *host_off = nullptr;     // host copy of bucket_off
     int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
 };
-constexpr int kHubChunk = 4096;      // arcs per block of the hub accumulate kernel
+constexpr int kHubChunk = 1024;      // arcs (and occupied slots) per block item of a hub
 struct BinLimits {
-    int small_max = 16, warp_max = 128, cta_max = 4096;
+    int lane_arcs = 4, warp_max = 128, cta_max = 4096;
 };
 lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes,
                           const BinLimits &lim, Buckets *b, int *scratch_pinned, cudaStream_t s);
@@ -54,26 +57,41 @@ struct IterStats {
     unsigned long long delta_ein;  // sum over movers of 2 (e_{i->new} - e_{i->old})
     unsigned long long sum_a2;     // sum over communities of a_C^2
     int moved;
-    int err;
+    int err;                       // a hash probe bound was exceeded
+    GridBarrier bar;               // barrier state of the persistent sweep (reset with the stats)
+    int bar_err;                   // a grid barrier wait expired
+    int pad;
 };
 struct PhaseState {
     DGraph g;
     const int32_t *k = nullptr;
     const int32_t *loop = nullptr;
     int32_t *C = nullptr;
-    unsigned long long *comm = nullptr;
-    int2 *moves = nullptr;
-    int32_t *move_count = nullptr;  // one slot per colour class
+    unsigned long long *comm[2] = {nullptr, nullptr};  // {a_C, |C|}; two buffers when coloured
+    int4 *moves[2] = {nullptr, nullptr};               // {i, old, new, k_i}
+    int32_t *move_count = nullptr;  // one slot per active class + a carry slot
+    int32_t *act = nullptr;         // device: active classes (those with arcs)
+    int n_act = 0;
+    bool coloured = false;
+    long long g_total = 0;          // classes swept so far in the phase (buffer parity)
     IterStats *stats = nullptr;
+    GridBarrier *bar = nullptr;   // &stats->bar
+    int *bar_err = nullptr;       // &stats->bar_err
     long long two_m = 0;
 };
-// C = identity, comm = (k, 1); stats->sum_ein = sum of loops, stats->sum_a2 = sum k^2
+// C = identity, comm = (k, 1) (both buffers when coloured); stats->sum_ein =
+// sum of loops, stats->sum_a2 = sum of k^2; move counters cleared
 lv_status init_phase(PhaseState &ps, cudaStream_t s);
-// sweep every bin of class `cls`; appends moves to ps.moves / move_count[cls]
-lv_status sweep_class(PhaseState &ps, const Buckets &b, int cls, const BinLimits &lim,
-                      int64_t *launches, cudaStream_t s);
-lv_status apply_moves(PhaseState &ps, int cls, cudaStream_t s);
-lv_status sum_a2(PhaseState &ps, cudaStream_t s);
+// One cooperative launch sweeping all active classes.  Coloured phases apply
+// each class's moves before the next class (double-buffered community state);
+// uncoloured phases leave the moves in ps.moves[0] / move_count[0].  Adds
+// sum_ein, delta_ein, moved and the sum of a_C^2 (after the sweep) to stats.
+lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s);
+// uncoloured phases: apply the listed moves
+lv_status apply_moves(PhaseState &ps, cudaStream_t s);
+// the community-state buffer holding the current state
+unsigned long long *current_comm(const PhaseState &ps);
+size_t hub_part_bytes();
 
 // lv_rebuild.cu ----------------------------------------------------------
 // newid[c] = rank of c among non-empty communities (n+1 entries, newid[n] = count)

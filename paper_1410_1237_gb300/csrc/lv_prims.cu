@@ -8,6 +8,17 @@
 namespace lv {
 
 int g_num_sms = 0;
+static TraceBuf g_trace;
+TraceBuf trace_buffer() {
+#ifdef LV_TRACE
+    if (!g_trace.buf) {
+        cudaMalloc(&g_trace.buf, sizeof(unsigned long long) * kTraceCap);
+        cudaMalloc(&g_trace.n, sizeof(unsigned int));
+        cudaMemset(g_trace.n, 0, sizeof(unsigned int));
+    }
+#endif
+    return g_trace;
+}
 unsigned long long g_kernel_launches = 0;
 
 // --------------------------------------------------------------- errors
@@ -295,3 +306,22 @@ lv_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uin
 }  // namespace lv
 
 extern "C" const char *lv_last_error(void) { return lv::t_last_error; }
+
+#ifdef LV_TRACE
+// profiling builds only: read and reset the stage timestamps
+extern "C" int lv_trace_read(unsigned long long *out, int max) {
+    lv::TraceBuf tb = lv::trace_buffer();
+    unsigned int n = 0;
+    cudaDeviceSynchronize();
+    cudaMemcpy(&n, tb.n, sizeof n, cudaMemcpyDeviceToHost);
+    if (n > lv::kTraceCap) n = lv::kTraceCap;
+    if ((int)n > max) n = (unsigned)max;
+    cudaMemcpy(out, tb.buf, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    return (int)n;
+}
+extern "C" void lv_trace_reset(void) {
+    lv::TraceBuf tb = lv::trace_buffer();
+    cudaDeviceSynchronize();
+    cudaMemset(tb.n, 0, sizeof(unsigned int));
+}
+#endif

@@ -1,26 +1,40 @@
 // lv_sweep.cu -- the vertex sweep of one iteration (Algorithm 1, Sec. 4.1).
 //
-// For every vertex i of the current colour class (or of the whole graph):
+// For every vertex i of a colour class (or of the whole graph):
 //   e[c]   = sum of w(i,j) over neighbours j != i with C(j) = c     (Eq. 1)
 //   s(c)   = 2m e[c] - k_i a_c                                        (Eq. 4 x (2m)^2/2)
 //   s_old  = 2m e[C(i)] - k_i (a_{C(i)} - k_i)
 //   best   = argmax over c != C(i) of s(c), ties to the smaller label (Eq. 5)
 //   move   iff s(best) - s_old > 0 and not (|C(i)| = |best| = 1 and best > C(i))
 // All products are below 2^62 (2m < 2^31), so int64 holds them exactly and
-// every decision is exact.  The sweep reads a snapshot: moves are appended
-// to a list and applied by a second kernel after the sweep, so all vertices
-// of a class decide from the state at the start of the class.
+// every decision is exact.  All vertices of a class decide from the state at
+// the start of the class.
 //
-// Vertices are binned by degree:
-//   bin 0  8 lanes per vertex, hash table of <= 64 slots in shared memory
-//   bin 1  one warp per vertex, <= 512 slots in shared memory
-//   bin 2  one CTA per vertex, <= 8192 slots (64 KB) in shared memory
-//   bin 3  hubs: a table in global memory, filled by several CTAs per
-//          vertex (chunks of kHubChunk arcs) and evaluated by one CTA
-// Tables are open-addressing (linear probing) keyed by community label and
-// sized to the next power of two >= 2 * degree, so the load factor is <= 1/2
-// and every probe sequence ends; a probe count above the table size is an
-// internal error (LV_ERR_HASH), never a hang.
+// One cooperative launch sweeps every class of an iteration.  Per class:
+//   stage A  block items: hub arc chunks (global tables) and CTA-bin vertices
+//            (shared-memory table); warp items: 32/G vertices of G lanes each,
+//            G = 1..32 chosen per vertex so each lane holds a few arcs
+//   [barrier, stage B: per hub, blocks evaluate chunks of its occupied
+//    slots; the last one to finish combines them and decides]
+//   barrier
+// Coloured phases keep the community state {a_C, |C|} in two buffers.  Class
+// g reads X[g % 2] and writes X[(g + 1) % 2], which before class g holds the
+// state of class g - 1's start: class g replays class g - 1's moves into it
+// and its own movers add their deltas there directly.  Labels are updated in
+// place (a class is an independent set, so no vertex of the class reads the
+// label of another).  One barrier per class suffices (two with hubs).
+// Uncoloured phases sweep the whole graph from X[0] and leave the moves in a
+// list for the host (the stopping test decides whether they are applied).
+//
+// Labels and community state change between classes, so they are read with
+// L2-only loads (L1 is not coherent across SMs); the graph is read normally.
+// Every loop keeps up to 4 independent loads in flight per thread.
+//
+// Hash tables are open-addressing (linear probing) keyed by community label
+// and sized to the next power of two >= 2 * degree, so the load factor is
+// <= 1/2 and every probe sequence ends; a probe count above the table size is
+// an internal error (LV_ERR_HASH), never a hang.  Grid barriers wait a bounded
+// time and report LV_ERR_TIMEOUT.
 #include <climits>
 
 #include "lv_ops.cuh"
@@ -28,25 +42,66 @@
 namespace lv {
 namespace {
 
-struct SweepArgs {
+constexpr int kSwBlock = 512;
+constexpr int kSwWarps = kSwBlock / 32;
+constexpr int kWarpRegion = 2 * kWarpSlots;            // ints per warp (keys + vals)
+constexpr int kSwSmemInts = kSwWarps * kWarpRegion;    // == 2 * kCtaSlots
+constexpr int kU = 4;                                  // loads in flight per thread
+static_assert(kSwSmemInts >= 2 * kCtaSlots, "CTA table must fit the block's region");
+static_assert(2 * kGroupTableInts <= kWarpRegion, "group tables must fit the warp region");
+static_assert(2 * kWarpMaxLimit * 2 <= 2 * kGroupTableInts, "warp table must fit");
+
+struct HubPart {
+    long long s;
+    int c, z, e, eo;
+};
+
+struct Sweep {
     const int32_t *__restrict__ off;
     const int2 *__restrict__ arcs;
     const int32_t *__restrict__ k;
     const int32_t *__restrict__ loop;
-    const int32_t *__restrict__ C;
-    const unsigned long long *__restrict__ comm;
-    long long two_m;
-    int2 *moves;
-    int32_t *move_count;
+    int32_t *C;
+    unsigned long long *comm0, *comm1;
+    int4 *moves0, *moves1;
+    int32_t *move_count;  // per active class, plus a carry slot at [n_act]
     IterStats *stats;
-    const int32_t *__restrict__ verts;  // vertices of this (class, bin)
-    int nverts;
+    const int32_t *__restrict__ order;
+    const int32_t *__restrict__ bucket_off;
+    const int32_t *__restrict__ chunk_at;
     int2 *hub_table;
-    const int32_t *__restrict__ hub_off;  // table offset per position of `verts`
-    int32_t *hub_occ;                     // occupied-slot lists (same offsets)
-    int32_t *hub_cnt;                     // occupied count per position of `verts`
-    const int32_t *__restrict__ hub_chunk_off;  // first arc chunk per position of `verts`
+    const int32_t *__restrict__ hub_off;
+    int32_t *hub_occ;
+    int32_t *hub_cnt;
+    const int32_t *__restrict__ hub_chunk_off;
+    HubPart *hub_part;
+    int32_t *hub_done;
+    const int32_t *__restrict__ act;  // active classes (colour indexes)
+    int n_act;
+    long long g0;  // classes swept in this phase before this launch
+    int coloured;
+    int n;
+    long long two_m;
+    GridBarrier *bar;
+    int *err;
+    TraceBuf tb;
 };
+
+// per-class view: read buffer, write buffer, move list and its counter
+struct Cls {
+    const unsigned long long *xr;
+    unsigned long long *xw;
+    int4 *mw;
+    int32_t *cnt;
+    int coloured;
+};
+
+struct Acc {
+    long long ein = 0, dein = 0;
+    int moved = 0, err = 0;
+};
+
+__device__ __forceinline__ int ldC(const Sweep &s, int j) { return __ldcg(&s.C[j]); }
 
 __device__ __forceinline__ int pow2_at_least(int x) {
     int p = 1;
@@ -54,19 +109,22 @@ __device__ __forceinline__ int pow2_at_least(int x) {
     return p;
 }
 
-// insert (c, w) into a shared-memory table of `mask + 1` slots
+// insert (c, w) into a shared-memory table of `mask + 1` slots whose slot h
+// lives at key[h * ST] / val[h * ST] (ST = 32 interleaves one table per lane
+// so that the lanes of a warp never collide on a bank)
+template <int ST>
 __device__ __forceinline__ bool smem_insert(int *key, int *val, unsigned mask, int c, int w) {
     unsigned h = hash32(c) & mask;
     for (unsigned probe = 0; probe <= mask; ++probe) {
-        const int cur = ((volatile int *)key)[h];
+        const int cur = ((volatile int *)key)[h * ST];
         if (cur == c) {
-            atomicAdd(&val[h], w);
+            atomicAdd(&val[h * ST], w);
             return true;
         }
         if (cur == kEmpty) {
-            const int prev = atomicCAS(&key[h], kEmpty, c);
+            const int prev = atomicCAS(&key[h * ST], kEmpty, c);
             if (prev == kEmpty || prev == c) {
-                atomicAdd(&val[h], w);
+                atomicAdd(&val[h * ST], w);
                 return true;
             }
         }
@@ -75,26 +133,25 @@ __device__ __forceinline__ bool smem_insert(int *key, int *val, unsigned mask, i
     return false;
 }
 
-// the same in a global-memory table of int2 {key, val}
-__device__ __forceinline__ bool gmem_insert(int2 *tab, unsigned mask, int c, int w) {
-    unsigned h = hash32(c) & mask;
-    for (unsigned probe = 0; probe <= mask; ++probe) {
-        int *kp = &tab[h].x;
-        const int cur = *((volatile int *)kp);
-        if (cur == c) {
-            atomicAdd(&tab[h].y, w);
-            return true;
+// insert the arcs e = first, first + step, ... < end of vertex i into a
+// shared-memory table, kU arcs (and their label gathers) at a time
+template <int ST>
+__device__ __forceinline__ void insert_arcs(const Sweep &s, int i, int first, int end, int step,
+                                            int *key, int *val, unsigned mask, Acc &acc) {
+    for (int e0 = first; e0 < end; e0 += kU * step) {
+        int2 a[kU];
+        int c[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * step;
+            a[u] = e < end ? s.arcs[e] : make_int2(i, 0);
         }
-        if (cur == kEmpty) {
-            const int prev = atomicCAS(kp, kEmpty, c);
-            if (prev == kEmpty || prev == c) {
-                atomicAdd(&tab[h].y, w);
-                return true;
-            }
-        }
-        h = (h + 1) & mask;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c[u] = a[u].x != i ? ldC(s, a[u].x) : kEmpty;
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (c[u] != kEmpty && !smem_insert<ST>(key, val, mask, c[u], a[u].y)) acc.err = 1;
     }
-    return false;
 }
 
 // best candidate so far: maximum s, then minimum label
@@ -126,355 +183,466 @@ __device__ __forceinline__ void best_shfl_xor(Best &b, int o) {
     best_take(b, s, c, z, e);
 }
 
-// evaluate one table slot
-__device__ __forceinline__ void eval_slot(const SweepArgs &a, int c, int e, int ci, int ki, Best &b,
-                                          int &e_old) {
-    if (c == kEmpty) return;
-    if (c == ci) {
-        e_old = e;
-        return;
+// evaluate table slots sl = first, first + step, ... <= mask, kU at a time
+template <int ST>
+__device__ __forceinline__ void eval_slots(const Sweep &s, const Cls &cc, const int *key,
+                                           const int *val, int first, unsigned mask, int step,
+                                           int ci, int ki, Best &b, int &e_old) {
+    for (int s0 = first; s0 <= (int)mask; s0 += kU * step) {
+        int kk[kU], vv[kU];
+        unsigned long long cm[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int sl = s0 + u * step;
+            kk[u] = sl <= (int)mask ? key[sl * ST] : kEmpty;
+            vv[u] = sl <= (int)mask ? val[sl * ST] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            cm[u] = (kk[u] != kEmpty && kk[u] != ci) ? __ldcg(&cc.xr[kk[u]]) : 0ull;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kk[u] == kEmpty) continue;
+            if (kk[u] == ci) {
+                e_old = vv[u];
+                continue;
+            }
+            best_take(b, s.two_m * (long long)vv[u] - (long long)ki * comm_a(cm[u]), kk[u],
+                      comm_size(cm[u]), vv[u]);
+        }
     }
-    const unsigned long long cm = a.comm[c];
-    best_take(b, a.two_m * (long long)e - (long long)ki * comm_a(cm), c, comm_size(cm), e);
 }
 
-// decision for vertex i given the reduced candidate; returns true on a move
-__device__ __forceinline__ bool decide(const SweepArgs &a, int i, int ci, int ki, const Best &b,
-                                       int e_old, long long &ein, long long &dein) {
-    const unsigned long long cmi = a.comm[ci];
-    const long long s_old = a.two_m * (long long)e_old - (long long)ki * (comm_a(cmi) - ki);
-    ein += (long long)e_old + a.loop[i];
+// decision for vertex i given the reduced candidate; true on a move
+__device__ __forceinline__ bool decide(const Sweep &s, const Cls &cc, int i, int ci, int ki,
+                                       const Best &b, int e_old, Acc &acc) {
+    const unsigned long long cmi = __ldcg(&cc.xr[ci]);
+    const long long s_old = s.two_m * (long long)e_old - (long long)ki * (comm_a(cmi) - ki);
+    acc.ein += (long long)e_old + s.loop[i];
     if (b.c == INT_MAX) return false;
-    const long long gain = b.s - s_old;
-    if (gain <= 0) return false;
+    if (b.s - s_old <= 0) return false;
     if (comm_size(cmi) == 1 && b.size == 1 && b.c > ci) return false;  // singlet rule
-    dein += 2ll * ((long long)b.e - e_old);
+    acc.dein += 2ll * ((long long)b.e - e_old);
     return true;
 }
 
-__device__ __forceinline__ void flush_stats(const SweepArgs &a, long long ein, long long dein,
-                                            int moved, int err) {
-    __shared__ long long red[8];
-    __shared__ int redi[8];
-    const long long t1 = block_sum_256(ein, red);
-    const long long t2 = block_sum_256(dein, red);
-    const int t3 = block_sum_256(moved, redi);
-    const int t4 = block_sum_256(err, redi);
-    if (threadIdx.x == 0) {
-        if (t1) atomicAdd(&a.stats->sum_ein, (unsigned long long)t1);
-        if (t2) atomicAdd(&a.stats->delta_ein, (unsigned long long)t2);
-        if (t3) atomicAdd(&a.stats->moved, t3);
-        if (t4) atomicOr(&a.stats->err, 1);
+// record a decided move at list position pos; coloured phases apply it now
+// (label in place, community deltas into the write buffer)
+__device__ __forceinline__ void commit(const Sweep &s, const Cls &cc, int pos, int i, int ci,
+                                       int nc, int ki) {
+    cc.mw[pos] = make_int4(i, ci, nc, ki);
+    if (cc.coloured) {
+        __stcg(&s.C[i], nc);
+        atomicAdd(&cc.xw[ci], comm_leave(ki));
+        atomicAdd(&cc.xw[nc], comm_join(ki));
     }
 }
 
-// ---------------------------------------------------------------- bins 0/1
-// G lanes per vertex, up to SLOTS table slots per group.  The loop over
-// vertices advances a whole warp at a time, so shuffles see full warps.
-template <int G, int SLOTS>
-__global__ void __launch_bounds__(256) sweep_group_kernel(SweepArgs a) {
-    constexpr int GPB = 256 / G;  // groups per block
-    constexpr int GPW = 32 / G;   // groups per warp
-    __shared__ int skey[GPB * SLOTS];
-    __shared__ int sval[GPB * SLOTS];
-    const int lane = threadIdx.x & 31;
-    const int gl = threadIdx.x & (G - 1);
-    const int gib = threadIdx.x / G;
-    int *key = skey + gib * SLOTS;
-    int *val = sval + gib * SLOTS;
-    const unsigned lt = (1u << lane) - 1u;
-    long long ein = 0, dein = 0;
-    int moved = 0, err = 0;
-    const int wid = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * 8;
-    for (int base = wid * GPW; base < a.nverts; base += nwarps * GPW) {
-        const int vi = base + lane / G;
-        const bool valid = vi < a.nverts;
-        int i = 0, beg = 0, end = 0, ci = 0, ki = 0;
-        unsigned mask = 0;
-        if (valid) {
-            i = a.verts[vi];
-            beg = a.off[i];
-            end = a.off[i + 1];
-            ci = a.C[i];
-            ki = a.k[i];
-            const int h = pow2_at_least(2 * (end - beg));
-            mask = (unsigned)((h < 8 ? 8 : h) - 1);
-        }
-        for (int sl = gl; sl <= (int)mask; sl += G) {
-            key[sl] = kEmpty;
-            val[sl] = 0;
-        }
-        __syncwarp();
-        for (int e = beg + gl; e < end; e += G) {
-            const int2 arc = a.arcs[e];
-            if (arc.x != i && !smem_insert(key, val, mask, a.C[arc.x], arc.y)) err = 1;
-        }
-        __syncwarp();
-        Best b;
-        best_init(b);
-        int e_old = 0;
-        if (valid)
-            for (int sl = gl; sl <= (int)mask; sl += G) eval_slot(a, key[sl], val[sl], ci, ki, b, e_old);
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
-            best_shfl_xor(b, o);
-        }
-        bool mv = false;
-        if (valid && gl == 0) mv = decide(a, i, ci, ki, b, e_old, ein, dein);
-        const unsigned bm = __ballot_sync(0xffffffffu, mv);
-        if (bm) {
-            int pos = 0;
-            if (lane == 0) pos = atomicAdd(a.move_count, __popc(bm));
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (mv) a.moves[pos + __popc(bm & lt)] = make_int2(i, b.c);
-            moved += mv ? 1 : 0;
-        }
-        __syncwarp();
-    }
-    flush_stats(a, ein, dein, moved, err);
-}
-
-// ---------------------------------------------------------------- bins 2/3
-// One 256-thread CTA per vertex.  GLOBAL = false: table in dynamic shared
-// memory; GLOBAL = true: table in a per-vertex slice of global memory.
-template <bool GLOBAL>
-__global__ void __launch_bounds__(256) sweep_cta_kernel(SweepArgs a) {
-    extern __shared__ int dyn[];
-    __shared__ long long rs[8];
-    __shared__ int rc[8], rz[8], re[8], reo[8];
-    __shared__ int s_mv;
+// block-wide reduction of (Best, e_old) over kSwWarps warps; result in thread 0
+struct BlockRed {
+    long long s[kSwWarps];
+    int c[kSwWarps], z[kSwWarps], e[kSwWarps], eo[kSwWarps];
+};
+__device__ __forceinline__ void block_best(Best &b, int &e_old, BlockRed &r) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    long long ein = 0, dein = 0;
-    int moved = 0, err = 0;
-    for (int vi = blockIdx.x; vi < a.nverts; vi += gridDim.x) {
-        const int i = a.verts[vi];
-        const int beg = a.off[i], end = a.off[i + 1];
-        const int ci = a.C[i], ki = a.k[i];
-        const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
-        int *key = dyn;
-        int *val = dyn + kCtaSlots;
-        int2 *tab = GLOBAL ? a.hub_table + a.hub_off[vi] : nullptr;
-        for (int sl = threadIdx.x; sl <= (int)mask; sl += 256) {
-            if (GLOBAL) tab[sl] = make_int2(kEmpty, 0);
-            else {
-                key[sl] = kEmpty;
-                val[sl] = 0;
-            }
-        }
-        __syncthreads();
-        for (int e = beg + threadIdx.x; e < end; e += 256) {
-            const int2 arc = a.arcs[e];
-            if (arc.x == i) continue;
-            const int c = a.C[arc.x];
-            const bool ok = GLOBAL ? gmem_insert(tab, mask, c, arc.y)
-                                   : smem_insert(key, val, mask, c, arc.y);
-            if (!ok) err = 1;
-        }
-        __syncthreads();
-        Best b;
-        best_init(b);
-        int e_old = 0;
-        for (int sl = threadIdx.x; sl <= (int)mask; sl += 256) {
-            if (GLOBAL) {
-                const int2 kv = tab[sl];
-                eval_slot(a, kv.x, kv.y, ci, ki, b, e_old);
-            } else {
-                eval_slot(a, key[sl], val[sl], ci, ki, b, e_old);
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
-            best_shfl_xor(b, o);
-        }
-        if (lane == 0) {
-            rs[w] = b.s;
-            rc[w] = b.c;
-            rz[w] = b.size;
-            re[w] = b.e;
-            reo[w] = e_old;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            Best t;
-            best_init(t);
-            int eo = 0;
-            for (int q = 0; q < 8; ++q) {
-                best_take(t, rs[q], rc[q], rz[q], re[q]);
-                eo += reo[q];
-            }
-            const bool mv = decide(a, i, ci, ki, t, eo, ein, dein);
-            if (mv) {
-                const int pos = atomicAdd(a.move_count, 1);
-                a.moves[pos] = make_int2(i, t.c);
-                ++moved;
-            }
-        }
-        __syncthreads();
-    }
-    (void)s_mv;
-    flush_stats(a, ein, dein, moved, err);
-}
-
-// ------------------------------------------------------------------ hubs
-// Hub vertices (degree above the CTA bin) are split into chunks of kHubChunk
-// arcs.  hub_accum: one block per chunk inserts its arcs into the hub's
-// global table, after merging equal labels within each warp; a thread that
-// claims an empty slot appends the slot to the hub's occupied list.
-// hub_decide: one block per hub evaluates only the occupied slots, resets
-// them to empty (so the table is clean for the next use) and decides.
-__global__ void __launch_bounds__(256) hub_accum_kernel(SweepArgs a) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int chunk = a.hub_chunk_off[0] + (int)blockIdx.x;
-    // position p of the hub owning this chunk: last p with hub_chunk_off[p] <= chunk
-    int lo = 0, hi = a.nverts;  // hub_chunk_off[nverts] > chunk
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (a.hub_chunk_off[mid] <= chunk) lo = mid; else hi = mid;
-    }
-    const int p = lo;
-    const int i = a.verts[p];
-    const int beg = a.off[i], end = a.off[i + 1];
-    const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
-    int2 *tab = a.hub_table + a.hub_off[p];
-    int32_t *occ = a.hub_occ + a.hub_off[p];
-    int32_t *occ_cnt = a.hub_cnt + p;
-    const int start = beg + (chunk - a.hub_chunk_off[p]) * kHubChunk;
-    const int stop = min(end, start + kHubChunk);
-    int err = 0;
-    for (int base = start + w * 32; base < stop; base += 256) {
-        const int e = base + lane;
-        bool valid = e < stop;
-        int c = 0, wt = 0;
-        if (valid) {
-            const int2 arc = a.arcs[e];
-            valid = arc.x != i;
-            if (valid) {
-                c = a.C[arc.x];
-                wt = arc.y;
-            }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : -1 - lane);
-        const int sum = __reduce_add_sync(peers, wt);
-        if (valid && lane == __ffs(peers) - 1) {
-            unsigned h = hash32(c) & mask;
-            bool done = false;
-            for (unsigned probe = 0; probe <= mask; ++probe) {
-                int *kp = &tab[h].x;
-                const int cur = *((volatile int *)kp);
-                if (cur == c) {
-                    atomicAdd(&tab[h].y, sum);
-                    done = true;
-                    break;
-                }
-                if (cur == kEmpty) {
-                    const int prev = atomicCAS(kp, kEmpty, c);
-                    if (prev == kEmpty) occ[atomicAdd(occ_cnt, 1)] = (int)h;
-                    if (prev == kEmpty || prev == c) {
-                        atomicAdd(&tab[h].y, sum);
-                        done = true;
-                        break;
-                    }
-                }
-                h = (h + 1) & mask;
-            }
-            if (!done) err = 1;
-        }
-    }
-    if (err) atomicOr(&a.stats->err, 1);
-}
-
-__global__ void __launch_bounds__(1024) hub_decide_kernel(SweepArgs a) {
-    __shared__ long long rs[32];
-    __shared__ int rc[32], rz[32], re[32], reo[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int p = blockIdx.x;
-    const int i = a.verts[p];
-    const int ci = a.C[i], ki = a.k[i];
-    int2 *tab = a.hub_table + a.hub_off[p];
-    const int32_t *occ = a.hub_occ + a.hub_off[p];
-    const int cnt = a.hub_cnt[p];
-    Best b;
-    best_init(b);
-    int e_old = 0;
-    for (int t = threadIdx.x; t < cnt; t += 1024) {
-        const int h = occ[t];
-        const int2 kv = tab[h];
-        tab[h] = make_int2(kEmpty, 0);
-        eval_slot(a, kv.x, kv.y, ci, ki, b, e_old);
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
         best_shfl_xor(b, o);
     }
     if (lane == 0) {
-        rs[w] = b.s;
-        rc[w] = b.c;
-        rz[w] = b.size;
-        re[w] = b.e;
-        reo[w] = e_old;
+        r.s[w] = b.s;
+        r.c[w] = b.c;
+        r.z[w] = b.size;
+        r.e[w] = b.e;
+        r.eo[w] = e_old;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        best_init(b);
+        e_old = 0;
+        for (int q = 0; q < kSwWarps; ++q) {
+            best_take(b, r.s[q], r.c[q], r.z[q], r.e[q]);
+            e_old += r.eo[q];
+        }
+    }
+}
+
+// ------------------------------------------------ group items (1..32 lanes)
+// One warp sweeps 32/G vertices verts[base + lane/G] with G lanes each.  The
+// NG = 32/G tables of a warp are interleaved (slot s of group q at s*NG + q),
+// so the lanes of a warp clear and probe distinct banks.
+template <int G>
+__device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *verts, int nverts,
+                                 int base, int *region, Acc &acc) {
+    constexpr int NG = 32 / G;
+    constexpr int ST = NG;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    int *key = region + lane / G;
+    int *val = region + kGroupTableInts + lane / G;
+    const unsigned lt = (1u << lane) - 1u;
+    const int vi = base + lane / G;
+    const bool valid = vi < nverts;
+    int i = 0, beg = 0, end = 0, ci = 0, ki = 0;
+    unsigned mask = 0;
+    if (valid) {
+        i = verts[vi];
+        beg = s.off[i];
+        end = s.off[i + 1];
+        ci = ldC(s, i);
+        ki = s.k[i];
+        const int h = pow2_at_least(2 * (end - beg));
+        mask = (unsigned)((h < 4 ? 4 : h) - 1);
+    }
+    for (int sl = gl; sl <= (int)mask; sl += G) {
+        key[sl * ST] = kEmpty;
+        val[sl * ST] = 0;
+    }
+    __syncwarp();
+    insert_arcs<ST>(s, i, beg + gl, end, G, key, val, mask, acc);
+    __syncwarp();
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    if (valid) eval_slots<ST>(s, cc, key, val, gl, mask, G, ci, ki, b, e_old);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
+        best_shfl_xor(b, o);
+    }
+    bool mv = false;
+    if (valid && gl == 0) mv = decide(s, cc, i, ci, ki, b, e_old, acc);
+    const unsigned bm = __ballot_sync(0xffffffffu, mv);
+    if (bm) {
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(cc.cnt, __popc(bm));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (mv) {
+            commit(s, cc, pos + __popc(bm & lt), i, ci, b.c, ki);
+            acc.moved += 1;
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------ block items
+// CTA-bin vertex: the whole block, table in shared memory.
+__device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dyn, BlockRed &red,
+                                   Acc &acc) {
+    const int beg = s.off[i], end = s.off[i + 1];
+    const int ci = ldC(s, i), ki = s.k[i];
+    const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+    int *key = dyn;
+    int *val = dyn + kCtaSlots;
+    for (int sl = threadIdx.x; sl <= (int)mask; sl += kSwBlock) {
+        key[sl] = kEmpty;
+        val[sl] = 0;
+    }
+    __syncthreads();
+    insert_arcs<1>(s, i, beg + threadIdx.x, end, kSwBlock, key, val, mask, acc);
+    __syncthreads();
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    eval_slots<1>(s, cc, key, val, threadIdx.x, mask, kSwBlock, ci, ki, b, e_old);
+    block_best(b, e_old, red);
+    if (threadIdx.x == 0 && decide(s, cc, i, ci, ki, b, e_old, acc)) {
+        commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+        acc.moved += 1;
+    }
+    __syncthreads();
+}
+
+// position of the hub owning arc chunk `chunk` in bucket [lo, lo + cnt)
+__device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int chunk) {
+    const int32_t *co = s.hub_chunk_off + lo;  // co[cnt] > chunk >= co[0]
+    int a = 0, b = cnt;
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (co[mid] <= chunk) a = mid; else b = mid;
+    }
+    return a;
+}
+
+// Hub arc chunk: inserts kHubChunk arcs of one hub into its global table,
+// merging equal labels within each warp first; a claimed slot is appended to
+// the hub's occupied list.
+__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int a = hub_of_chunk(s, lo, cnt, chunk);
+    const int p = lo + a;
+    const int i = s.order[p];
+    const int beg = s.off[i], end = s.off[i + 1];
+    const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+    int2 *tab = s.hub_table + s.hub_off[p];
+    int32_t *occ = s.hub_occ + s.hub_off[p];
+    int32_t *occ_cnt = s.hub_cnt + p;
+    const int start = beg + (chunk - s.hub_chunk_off[p]) * kHubChunk;
+    const int stop = min(end, start + kHubChunk);
+    for (int b0 = start + w * 32; b0 < stop; b0 += kU * kSwBlock) {
+        int2 ar[kU];
+        int cl[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int e = b0 + u * kSwBlock + lane;
+            ar[u] = e < stop ? s.arcs[e] : make_int2(i, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) cl[u] = ar[u].x != i ? ldC(s, ar[u].x) : kEmpty;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const bool valid = cl[u] != kEmpty;
+            const int c = cl[u];
+            const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : -1 - lane);
+            const int sum = __reduce_add_sync(peers, valid ? ar[u].y : 0);
+            if (valid && lane == __ffs(peers) - 1) {
+                unsigned h = hash32(c) & mask;
+                bool done = false;
+                for (unsigned probe = 0; probe <= mask && !done; ++probe) {
+                    int *kp = &tab[h].x;
+                    const int cur = *((volatile int *)kp);
+                    if (cur == c) {
+                        atomicAdd(&tab[h].y, sum);
+                        done = true;
+                    } else if (cur == kEmpty) {
+                        const int prev = atomicCAS(kp, kEmpty, c);
+                        if (prev == kEmpty) occ[atomicAdd(occ_cnt, 1)] = (int)h;
+                        if (prev == kEmpty || prev == c) {
+                            atomicAdd(&tab[h].y, sum);
+                            done = true;
+                        }
+                    }
+                    h = (h + 1) & mask;
+                }
+                if (!done) acc.err = 1;
+            }
+        }
+    }
+}
+
+// Hub decision, one block per chunk of the occupied list: evaluates its
+// slots (resetting them to empty) and stores a partial best; the last block
+// of the hub to finish (counted with a fenced atomic, no waiting) combines
+// the partials and decides.
+__device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk,
+                                 BlockRed &red, Acc &acc) {
+    __shared__ int s_last;
+    const int a = hub_of_chunk(s, lo, cnt, chunk);
+    const int p = lo + a;
+    const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
+    const int i = s.order[p];
+    const int ci = ldC(s, i), ki = s.k[i];
+    int2 *tab = s.hub_table + s.hub_off[p];
+    const int32_t *occ = s.hub_occ + s.hub_off[p];
+    const int n_occ = __ldcg(&s.hub_cnt[p]);
+    const int t0 = (chunk - first) * kHubChunk, t1 = min(n_occ, t0 + kHubChunk);
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    for (int q0 = t0 + threadIdx.x; q0 < t1; q0 += kU * kSwBlock) {
+        int hh[kU];
+        int2 kv[kU];
+        unsigned long long cm[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = q0 + u * kSwBlock;
+            hh[u] = q < t1 ? __ldcg(&occ[q]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) kv[u] = hh[u] >= 0 ? __ldcg(&tab[hh[u]]) : make_int2(kEmpty, 0);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (hh[u] >= 0) __stcg(&tab[hh[u]], make_int2(kEmpty, 0));
+            cm[u] = (kv[u].x != kEmpty && kv[u].x != ci) ? __ldcg(&cc.xr[kv[u].x]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kv[u].x == kEmpty) continue;
+            if (kv[u].x == ci) {
+                e_old = kv[u].y;
+                continue;
+            }
+            best_take(b, s.two_m * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
+                      comm_size(cm[u]), kv[u].y);
+        }
+    }
+    block_best(b, e_old, red);
+    if (threadIdx.x == 0) {
+        HubPart hp;
+        hp.s = b.s;
+        hp.c = b.c;
+        hp.z = b.size;
+        hp.e = b.e;
+        hp.eo = e_old;
+        s.hub_part[chunk] = hp;
+        __threadfence();
+        s_last = (atomicAdd(&s.hub_done[p], 1) == nch - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
         Best t;
         best_init(t);
         int eo = 0;
-        for (int q = 0; q < 32; ++q) {
-            best_take(t, rs[q], rc[q], rz[q], re[q]);
-            eo += reo[q];
+        for (int q = first; q < first + nch; ++q) {
+            const HubPart *hq = &s.hub_part[q];
+            best_take(t, __ldcg(&hq->s), __ldcg(&hq->c), __ldcg(&hq->z), __ldcg(&hq->e));
+            eo += __ldcg(&hq->eo);
         }
-        a.hub_cnt[p] = 0;
-        long long ein = 0, dein = 0;
-        if (decide(a, i, ci, ki, t, eo, ein, dein)) {
-            const int pos = atomicAdd(a.move_count, 1);
-            a.moves[pos] = make_int2(i, t.c);
-            atomicAdd(&a.stats->moved, 1);
+        __stcg(&s.hub_cnt[p], 0);
+        __stcg(&s.hub_done[p], 0);
+        if (decide(s, cc, i, ci, ki, t, eo, acc)) {
+            commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
+            acc.moved += 1;
         }
-        if (ein) atomicAdd(&a.stats->sum_ein, (unsigned long long)ein);
-        if (dein) atomicAdd(&a.stats->delta_ein, (unsigned long long)dein);
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum_sw(T v, T *sm) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    T r = 0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < kSwWarps; ++q) r += sm[q];
+    return r;
+}
+
+// ------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) {
+    extern __shared__ int dyn[];
+    __shared__ BlockRed red;
+    __shared__ long long sml[kSwWarps];
+    Acc acc;
+    const int wib = threadIdx.x >> 5;
+    int *region = dyn + wib * kWarpRegion;
+    const int gwarp = blockIdx.x * kSwWarps + wib;
+    const int nwarps = gridDim.x * kSwWarps;
+    const int gthread = blockIdx.x * kSwBlock + threadIdx.x;
+    const int nthreads = gridDim.x * kSwBlock;
+    for (int q = 0; q < s.n_act; ++q) {
+        const int c = s.act[q];
+        const long long g = s.g0 + q;
+        Cls cc;
+        cc.coloured = s.coloured;
+        cc.xr = s.coloured && (g & 1) ? s.comm1 : s.comm0;
+        cc.xw = s.coloured && (g & 1) ? s.comm0 : s.comm1;
+        cc.mw = s.coloured && (g & 1) ? s.moves1 : s.moves0;
+        cc.cnt = s.move_count + q;
+        if (s.coloured) {
+            // bring the write buffer up to date with the previous class's moves
+            const int4 *mp = (g & 1) ? s.moves0 : s.moves1;
+            const int np = __ldcg(&s.move_count[q == 0 ? s.n_act : q - 1]);
+            for (int t = gthread; t < np; t += nthreads) {
+                const int4 m = __ldcg(&mp[t]);
+                atomicAdd(&cc.xw[m.y], comm_leave(m.w));
+                atomicAdd(&cc.xw[m.z], comm_join(m.w));
+            }
+        }
+        const int32_t *bo = s.bucket_off + c * (kBins + 1);
+        const int b_cta = bo[kBinCta], b_hub = bo[kBinHub], b_end = bo[kBins];
+        const int32_t *ca = s.chunk_at + c * (kBins + 1);
+        const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
+        const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
+        for (int it = blockIdx.x; it < nchunks + n_cta; it += gridDim.x) {
+            if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, acc);
+            else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
+        }
+        __syncthreads();
+        // warp items: 32/G vertices of group bin log2(G), largest groups first
+        int item_end[kGroupBins];
+        {
+            int acc_items = 0;
+            for (int gb = kGroupBins - 1; gb >= 0; --gb) {
+                acc_items += (bo[gb + 1] - bo[gb] + (32 >> gb) - 1) >> (5 - gb);
+                item_end[gb] = acc_items;
+            }
+        }
+        for (int it = gwarp; it < item_end[0]; it += nwarps) {
+            int gb = kGroupBins - 1;
+            while (it >= item_end[gb]) --gb;
+            const int first = gb == kGroupBins - 1 ? 0 : item_end[gb + 1];
+            const int lo = bo[gb], cnt = bo[gb + 1] - bo[gb];
+            const int base = (it - first) << (5 - gb);
+            switch (gb) {
+            case 5: warp_group_sweep<32>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            case 4: warp_group_sweep<16>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            case 3: warp_group_sweep<8>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            case 2: warp_group_sweep<4>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            case 1: warp_group_sweep<2>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            default: warp_group_sweep<1>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            }
+        }
+        if (n_hub > 0) {
+            if (!grid_sync(s.bar, s.err)) return;
+            for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
+                hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
+            if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 4)
+                trace4(s.tb, 0x400000000ull | (unsigned)q, (unsigned long long)blockIdx.x, 0, gtimer());
+        }
+        if (s.coloured || q + 1 < s.n_act)
+            if (!grid_sync(s.bar, s.err)) return;
+        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
+            trace4(s.tb, 0x500000000ull | (unsigned)q, ((unsigned long long)n_cta << 32) | (unsigned)n_hub,
+                   ((unsigned long long)(bo[kGroupBins] - bo[kGroupBins - 1]) << 32) |
+                       (unsigned)(bo[kGroupBins - 1] - bo[0]),
+                   gtimer());
+    }
+    if (s.coloured && blockIdx.x == 0 && threadIdx.x == 0 && s.n_act > 0)
+        s.move_count[s.n_act] = __ldcg(&s.move_count[s.n_act - 1]);  // carry for the next launch
+    // sum of a_C^2 over all communities of the state the sweep leaves
+    const unsigned long long *xf =
+        s.coloured && ((s.g0 + s.n_act) & 1) ? s.comm1 : s.comm0;
+    long long a2 = 0;
+    for (int c = gthread; c < s.n; c += nthreads) {
+        const long long x = comm_a(__ldcg(&xf[c]));
+        a2 += x * x;
+    }
+    const long long t_ein = block_sum_sw(acc.ein, sml);
+    const long long t_dein = block_sum_sw(acc.dein, sml);
+    const long long t_a2 = block_sum_sw(a2, sml);
+    const long long t_mv = block_sum_sw((long long)acc.moved, sml);
+    const long long t_err = block_sum_sw((long long)acc.err, sml);
+    if (threadIdx.x == 0) {
+        if (t_ein) atomicAdd(&s.stats->sum_ein, (unsigned long long)t_ein);
+        if (t_dein) atomicAdd(&s.stats->delta_ein, (unsigned long long)t_dein);
+        if (t_a2) atomicAdd(&s.stats->sum_a2, (unsigned long long)t_a2);
+        if (t_mv) atomicAdd(&s.stats->moved, (int)t_mv);
+        if (t_err) atomicOr(&s.stats->err, 1);
     }
 }
 
-// ------------------------------------------------------------ apply, a^2
+// ------------------------------------------------------------ apply, init
+// uncoloured phases: apply the listed moves (after the stopping test)
 __global__ void apply_moves_kernel(int32_t *C, unsigned long long *comm,
-                                   const int32_t *__restrict__ k, const int2 *__restrict__ moves,
+                                   const int4 *__restrict__ moves,
                                    const int32_t *__restrict__ count) {
     const int cnt = *count;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
-        const int2 mv = moves[t];
-        const int old = C[mv.x];
-        const int ki = k[mv.x];
-        C[mv.x] = mv.y;
-        atomicAdd(&comm[old], comm_leave(ki));
-        atomicAdd(&comm[mv.y], comm_join(ki));
+        const int4 m = moves[t];
+        C[m.x] = m.z;
+        atomicAdd(&comm[m.y], comm_leave(m.w));
+        atomicAdd(&comm[m.z], comm_join(m.w));
     }
-}
-
-__global__ void __launch_bounds__(256) sum_a2_kernel(const unsigned long long *__restrict__ comm,
-                                                     int n, unsigned long long *out) {
-    __shared__ long long red[8];
-    long long acc = 0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const long long x = comm_a(comm[c]);
-        acc += x * x;
-    }
-    acc = block_sum_256(acc, red);
-    if (threadIdx.x == 0 && acc) atomicAdd(out, (unsigned long long)acc);
 }
 
 __global__ void __launch_bounds__(256) init_phase_kernel(int n, const int32_t *__restrict__ k,
                                                          const int32_t *__restrict__ loop,
-                                                         int32_t *C, unsigned long long *comm,
+                                                         int32_t *C, unsigned long long *comm0,
+                                                         unsigned long long *comm1,
                                                          IterStats *stats) {
     __shared__ long long red[8];
     long long sl = 0, sk = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int ki = k[i];
         C[i] = i;
-        comm[i] = comm_pack(ki, 1);
+        comm0[i] = comm_pack(ki, 1);
+        if (comm1) comm1[i] = comm_pack(ki, 1);
         sl += loop[i];
         sk += (long long)ki * ki;
     }
@@ -486,86 +654,80 @@ __global__ void __launch_bounds__(256) init_phase_kernel(int n, const int32_t *_
     }
 }
 
+int g_sweep_blocks_per_sm = 0;
+
 }  // namespace
+
+lv_status sweep_setup() {
+    const int smem = kSwSmemInts * (int)sizeof(int);
+    LV_CUDA(cudaFuncSetAttribute(sweep_persistent_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_sweep_blocks_per_sm,
+                                                          sweep_persistent_kernel, kSwBlock, smem));
+    if (g_sweep_blocks_per_sm < 1) return LV_ERR_CUDA;
+    return LV_OK;
+}
+
+size_t hub_part_bytes() { return sizeof(HubPart); }
 
 lv_status init_phase(PhaseState &ps, cudaStream_t s) {
     LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
+    LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * ((size_t)ps.n_act + 1), s));
+    ps.g_total = 0;
     init_phase_kernel<<<grid_for(ps.g.n, 256, g_num_sms * 8), 256, 0, s>>>(
-        ps.g.n, ps.k, ps.loop, ps.C, ps.comm, ps.stats);
+        ps.g.n, ps.k, ps.loop, ps.C, ps.comm[0], ps.coloured ? ps.comm[1] : nullptr, ps.stats);
     LV_LAUNCH_CHECK();
     return LV_OK;
 }
 
-lv_status sweep_class(PhaseState &ps, const Buckets &b, int cls, const BinLimits &lim,
-                      int64_t *launches, cudaStream_t s) {
-    (void)lim;
-    SweepArgs a;
+lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
+    Sweep a;
     a.off = ps.g.off;
     a.arcs = ps.g.arcs;
     a.k = ps.k;
     a.loop = ps.loop;
     a.C = ps.C;
-    a.comm = ps.comm;
-    a.two_m = ps.two_m;
-    a.moves = ps.moves;
-    a.move_count = ps.move_count + cls;
+    a.comm0 = ps.comm[0];
+    a.comm1 = ps.comm[1];
+    a.moves0 = ps.moves[0];
+    a.moves1 = ps.moves[1];
+    a.move_count = ps.move_count;
     a.stats = ps.stats;
+    a.order = b.order;
+    a.bucket_off = b.bucket_off;
+    a.chunk_at = b.hub_chunk_at;
     a.hub_table = b.hub_table;
+    a.hub_off = b.hub_off;
     a.hub_occ = b.hub_occ;
-    for (int bin = 0; bin < kBins; ++bin) {
-        const int lo = b.host_off[cls * (kBins + 1) + bin];
-        const int hi = b.host_off[cls * (kBins + 1) + bin + 1];
-        const int cnt = hi - lo;
-        if (cnt <= 0) continue;
-        a.verts = b.order + lo;
-        a.nverts = cnt;
-        a.hub_off = b.hub_off + lo;
-        switch (bin) {
-        case 0:
-            sweep_group_kernel<kGroupLanes, kGroupSlots>
-                <<<grid_for(cnt, 256 / kGroupLanes, g_num_sms * 8), 256, 0, s>>>(a);
-            break;
-        case 1:
-            sweep_group_kernel<32, kWarpSlots><<<grid_for(cnt, 8, g_num_sms * 8), 256, 0, s>>>(a);
-            break;
-        case 2:
-            sweep_cta_kernel<false>
-                <<<grid_for(cnt, 1, g_num_sms * 3), 256, 2 * kCtaSlots * sizeof(int), s>>>(a);
-            break;
-        default: {
-            const int bq = cls * (kBins + 1) + bin;
-            const int nchunks = b.host_chunk[bq + 1] - b.host_chunk[bq];
-            a.hub_chunk_off = b.hub_chunk_off + lo;
-            a.hub_cnt = b.hub_cnt + lo;
-            hub_accum_kernel<<<nchunks, 256, 0, s>>>(a);
-            LV_LAUNCH_CHECK();
-            hub_decide_kernel<<<cnt, 1024, 0, s>>>(a);
-            break;
-        }
-        }
-        LV_LAUNCH_CHECK();
-        ++*launches;
-    }
-    return LV_OK;
-}
-
-lv_status apply_moves(PhaseState &ps, int cls, cudaStream_t s) {
-    apply_moves_kernel<<<g_num_sms * 4, 256, 0, s>>>(ps.C, ps.comm, ps.k, ps.moves,
-                                                    ps.move_count + cls);
+    a.hub_cnt = b.hub_cnt;
+    a.hub_chunk_off = b.hub_chunk_off;
+    a.hub_part = reinterpret_cast<HubPart *>(b.hub_part);
+    a.hub_done = b.hub_done;
+    a.act = ps.act;
+    a.n_act = ps.n_act;
+    a.g0 = ps.g_total;
+    a.coloured = ps.coloured ? 1 : 0;
+    a.n = ps.g.n;
+    a.two_m = ps.two_m;
+    a.bar = ps.bar;
+    a.err = ps.bar_err;
+    a.tb = trace_buffer();
+    void *args[] = {&a};
+    LV_CUDA(cudaLaunchCooperativeKernel((void *)sweep_persistent_kernel,
+                                        dim3(g_num_sms * g_sweep_blocks_per_sm), dim3(kSwBlock), args,
+                                        kSwSmemInts * sizeof(int), s));
     LV_LAUNCH_CHECK();
+    if (ps.coloured) ps.g_total += ps.n_act;
     return LV_OK;
 }
 
-lv_status sum_a2(PhaseState &ps, cudaStream_t s) {
-    sum_a2_kernel<<<grid_for(ps.g.n, 256, g_num_sms * 4), 256, 0, s>>>(ps.comm, ps.g.n,
-                                                                      &ps.stats->sum_a2);
+unsigned long long *current_comm(const PhaseState &ps) {
+    return ps.coloured ? ps.comm[ps.g_total & 1] : ps.comm[0];
+}
+
+lv_status apply_moves(PhaseState &ps, cudaStream_t s) {
+    apply_moves_kernel<<<g_num_sms * 4, 256, 0, s>>>(ps.C, ps.comm[0], ps.moves[0], ps.move_count);
     LV_LAUNCH_CHECK();
-    return LV_OK;
-}
-
-lv_status sweep_setup() {
-    LV_CUDA(cudaFuncSetAttribute(sweep_cta_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * kCtaSlots * (int)sizeof(int)));
     return LV_OK;
 }
 

@@ -39,7 +39,7 @@ class lv_params(ctypes.Structure):
                 ("color_cutoff", ctypes.c_int64), ("max_iters", ctypes.c_int32),
                 ("max_phases", ctypes.c_int32), ("color_seed", ctypes.c_uint64),
                 ("collect_timing", ctypes.c_int32), ("keep_graphs", ctypes.c_int32),
-                ("bin_small_max", ctypes.c_int32), ("bin_warp_max", ctypes.c_int32),
+                ("bin_lane_arcs", ctypes.c_int32), ("bin_warp_max", ctypes.c_int32),
                 ("bin_cta_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
@@ -48,7 +48,7 @@ class lv_phase_info(ctypes.Structure):
                 ("two_m", ctypes.c_int64), ("N_start", ctypes.c_int64), ("N_end", ctypes.c_int64),
                 ("q", ctypes.c_double), ("theta", ctypes.c_double), ("colored", ctypes.c_int32),
                 ("num_colors", ctypes.c_int32), ("iterations", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("ms_color", ctypes.c_double),
+                ("color_rounds", ctypes.c_int32), ("ms_color", ctypes.c_double),
                 ("ms_iterate", ctypes.c_double), ("ms_rebuild", ctypes.c_double)]
 
 

@@ -88,16 +88,15 @@ def test_random_small(lv, seed):
         compare(lv, g, **v)
 
 
-@pytest.mark.parametrize("bins", [(1, 2, 3), (2, 4, 8), (4, 32, 64), (16, 128, 4096),
-                                  (32, 256, 4096)])
+@pytest.mark.parametrize("bins", [(1, 1, 2), (1, 2, 3), (2, 8, 16), (1, 32, 64), (4, 128, 4096),
+                                  (8, 256, 4096), (3, 100, 1000)])
 def test_every_bin_path(lv, bins):
-    # tiny bin limits push ordinary vertices through the CTA and hub kernels
+    # small bin limits push ordinary vertices through the CTA and hub kernels
     g = gg.chunglu(4000, 2.1, 0.7, 16000, 300.0, seed=7)
-    s, w_, c = bins
-    compare(lv, g, vertex_following=1, coloring=1, color_cutoff=0,
-            bin_small_max=s, bin_warp_max=w_, bin_cta_max=c)
-    compare(lv, g, graphs=False, vertex_following=0, coloring=0,
-            bin_small_max=s, bin_warp_max=w_, bin_cta_max=c)
+    la, w_, c = bins
+    kw = dict(bin_lane_arcs=la, bin_warp_max=w_, bin_cta_max=c)
+    compare(lv, g, vertex_following=1, coloring=1, color_cutoff=0, **kw)
+    compare(lv, g, graphs=False, vertex_following=0, coloring=0, **kw)
 
 
 def test_hub_vertex(lv):
@@ -132,7 +131,7 @@ def test_rmat20_full(lv):
 def test_determinism(lv):
     g, prm = gg.workload("rmat16")
     a = lv.run(g.rowptr, g.col, g.w, **prm)
-    b = lv.run(g.rowptr, g.col, g.w, bin_small_max=4, bin_warp_max=64, bin_cta_max=512, **prm)
+    b = lv.run(g.rowptr, g.col, g.w, bin_lane_arcs=2, bin_warp_max=64, bin_cta_max=512, **prm)
     for x, y in zip(a.phases, b.phases):
         assert np.array_equal(x.labels, y.labels) and x.N_end == y.N_end
 
