@@ -90,6 +90,9 @@ SIGNATURES = {
     "lv_get_phase_graph": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _vp, _vp, _vp, ctypes.c_int]),
     "lv_get_phase_colors": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int]),
+    "lv_modularity_noalloc": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, _vp,
+                                             _P(ctypes.c_int64), _P(ctypes.c_uint64),
+                                             _P(ctypes.c_int64), _vp]),
     "lv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lv_last_error": (ctypes.c_char_p, []),
     "lv_graph_destroy": (None, [_vp]),
@@ -234,6 +237,19 @@ def lv_get_phase_colors(h: int, phase: int, n: int) -> np.ndarray:
     out = np.empty(n, dtype=np.int32)
     _check(load().lv_get_phase_colors(h, phase, out.ctypes.data, 0), "lv_get_phase_colors")
     return out
+
+
+def lv_modularity_noalloc(n: int, rowptr, col, w, labels, stream: int = 0) -> tuple[int, int]:
+    """(N, den) of a labelling, with device-resident CSR and labels (CUDA
+    tensors), using only the library's fixed scratch array (no allocation)."""
+    ptrs = [_ptr(x) for x in (rowptr, col, w, labels)]
+    if not all(d for _, d in ptrs):
+        raise ValueError("lv_modularity_noalloc takes device arrays only")
+    hi, lo, den = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+    _check(load().lv_modularity_noalloc(int(n), *[p for p, _ in ptrs], ctypes.byref(hi),
+                                        ctypes.byref(lo), ctypes.byref(den), stream or None),
+           "lv_modularity_noalloc")
+    return (hi.value << 64) | lo.value, den.value
 
 
 def lv_status_string(code: int) -> str:
