@@ -247,6 +247,7 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
     int64_t n_p = 0;
     int64_t moved_prev = 0;
     int ev_prev0 = -1, ev_prev1 = -1;
+    ps.hub_fast = false;
     auto record = [&](int t, int64_t moved, int64_t N, int e0, int e1) {
         IterRecord r;
         r.st.phase = phase;
@@ -262,13 +263,14 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
     };
     for (int step = 1;; ++step) {
         LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t), s));
+        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s));
         const int e0 = h->timer.mark();
         LV_TRY(sweep_iteration(ps, b, s));
         ++h->stats.sweep_launches;
         const int e1 = h->timer.mark();
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
+        ps.hub_fast = hs.max_occ <= kHubFastOcc;  // scheduling only: results do not depend on it
         const int64_t N_prev = ps.two_m * (int64_t)hs.sum_ein - (int64_t)hs.sum_a2;  // N(C^{step-1})
         const int64_t moved = hs.moved;
         if (step == 1) {
@@ -310,15 +312,17 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
     bool have_np = false;
     int64_t n_p = 0;
     int64_t sum_ein = sum_loops;
+    ps.hub_fast = false;
     for (int t = 1;; ++t) {
         LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * (size_t)ps.n_act, s));
+        LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t) * (size_t)ps.n_act, s));
         const int e0 = h->timer.mark();
         LV_TRY(sweep_iteration(ps, b, s));
         ++h->stats.sweep_launches;
         const int e1 = h->timer.mark();
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
+        ps.hub_fast = hs.max_occ <= kHubFastOcc;  // scheduling only: results do not depend on it
         sum_ein += (int64_t)hs.delta_ein;
         const int64_t N = ps.two_m * sum_ein - (int64_t)hs.sum_a2;
         IterRecord r;
@@ -471,7 +475,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
             LV_CUDA(cudaMemcpyAsync(ps.act, act.data(), sizeof(int32_t) * act.size(),
                                     cudaMemcpyHostToDevice, s));
         }
-        LV_TRY(dalloc_n(&ps.move_count, (size_t)ps.n_act + 1, s));
+        LV_TRY(dalloc_n(&ps.move_count, 3 * (size_t)ps.n_act + 1, s));
         const int ev_i0 = h->timer.mark();
         LV_TRY(init_phase(ps, s));
         IterStats hs0;

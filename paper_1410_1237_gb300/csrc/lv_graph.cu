@@ -89,6 +89,13 @@ __device__ __forceinline__ void check_mirror(const DGraph &g, int i, int2 a, int
 
 constexpr int kBigRow = 1024;
 
+// rows of at least kBigRow arcs (optionally only kept ones), appended to list
+__global__ void big_rows_kernel(DGraph g, const int32_t *__restrict__ keep, int32_t *list,
+                                int32_t *count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
+        if (g.off[i + 1] - g.off[i] >= kBigRow && (!keep || keep[i])) list[atomicAdd(count, 1)] = i;
+}
+
 // one warp per row of fewer than kBigRow arcs
 __global__ void __launch_bounds__(256) symmetry_kernel(DGraph g, int *sev) {
     const int lane = threadIdx.x & 31;
@@ -100,12 +107,15 @@ __global__ void __launch_bounds__(256) symmetry_kernel(DGraph g, int *sev) {
     }
 }
 
-// one 1024-thread block per row of at least kBigRow arcs
-__global__ void __launch_bounds__(1024) symmetry_big_kernel(DGraph g, int *sev) {
-    for (int64_t i = blockIdx.x; i < g.n; i += gridDim.x) {
+// one 1024-thread block per row of at least kBigRow arcs (from a list)
+__global__ void __launch_bounds__(1024) symmetry_big_kernel(DGraph g, const int32_t *__restrict__ list,
+                                                            const int32_t *__restrict__ count,
+                                                            int *sev) {
+    const int nb = *count;
+    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
+        const int i = list[t];
         const int beg = g.off[i], end = g.off[i + 1];
-        if (end - beg < kBigRow) continue;
-        for (int e = beg + threadIdx.x; e < end; e += 1024) check_mirror(g, (int)i, g.arcs[e], sev);
+        for (int e = beg + threadIdx.x; e < end; e += 1024) check_mirror(g, i, g.arcs[e], sev);
     }
 }
 
@@ -183,7 +193,7 @@ __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *_
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t ii = blockIdx.x * 8 + (threadIdx.x >> 5); ii < g.n; ii += nw) {
         const int i = (int)ii;
-        if (!keep[i]) continue;  // warp-uniform
+        if (!keep[i] || g.off[i + 1] - g.off[i] >= kBigRow) continue;  // warp-uniform
         const int ni = newid[i];
         const int ex = extra[i];
         bool pending = (loop[i] == 0 && ex > 0);  // self-loop to insert
@@ -214,6 +224,69 @@ __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *_
             run += __popc(bk);
         }
         if (pending && lane == 0) arcs2[run + sh] = make_int2(ni, ex);
+    }
+}
+
+// the same for kept rows of at least kBigRow arcs, one 1024-thread block each:
+// positions come from a block-wide prefix over the kept flags of each chunk
+__global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32_t *__restrict__ keep,
+                                                           const int32_t *__restrict__ list,
+                                                           const int32_t *__restrict__ count,
+                                                           const int32_t *__restrict__ newid,
+                                                           const int32_t *__restrict__ loop,
+                                                           const int32_t *__restrict__ extra,
+                                                           const int32_t *__restrict__ off2,
+                                                           int2 *arcs2) {
+    __shared__ int s_wcnt[32], s_wpre[32], s_tot, s_first;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nbig = *count;
+    for (int t = blockIdx.x; t < nbig; t += gridDim.x) {
+        const int i = list[t];
+        const int beg = g.off[i], end = g.off[i + 1];
+        const int ni = newid[i];
+        const int ex = extra[i];
+        bool pending = (loop[i] == 0 && ex > 0);
+        int run = off2[ni];
+        int sh = 0;
+        for (int base = beg; base < end; base += 1024) {
+            const int e = base + (int)threadIdx.x;
+            const bool valid = e < end;
+            const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
+            const bool kp = valid && (a.x == i || keep[a.x]);
+            const unsigned wb = __ballot_sync(0xffffffffu, kp);
+            if (lane == 0) s_wcnt[w] = __popc(wb);
+            if (threadIdx.x == 0) s_first = 1 << 30;
+            __syncthreads();
+            if (w == 0) {
+                int x = s_wcnt[lane], incl = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                s_wpre[lane] = incl - x;
+                if (lane == 31) s_tot = incl;
+            }
+            if (pending && kp && a.x > i) atomicMin(&s_first, (int)threadIdx.x);
+            __syncthreads();
+            const int rank = s_wpre[w] + __popc(wb & lt);
+            int lsh = sh;
+            if (pending && s_first < (1 << 30)) {
+                if ((int)threadIdx.x == s_first) arcs2[run + rank] = make_int2(ni, ex);
+                if ((int)threadIdx.x >= s_first) lsh = 1;
+            }
+            if (kp) arcs2[run + rank + lsh] =
+                (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
+            if (pending && s_first < (1 << 30)) {
+                pending = false;
+                sh = 1;
+            }
+            run += s_tot;
+            __syncthreads();
+        }
+        if (pending && threadIdx.x == 0) arcs2[run + sh] = make_int2(ni, ex);
+        __syncthreads();
     }
 }
 
@@ -286,8 +359,14 @@ lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *co
     if (scratch_pinned[0] < kSevSym && n > 0) {
         symmetry_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev);
         LV_LAUNCH_CHECK();
-        symmetry_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, dsev);
+        int32_t *big = nullptr;
+        LV_TRY(dalloc_n(&big, (size_t)n / kBigRow + (size_t)g.A / kBigRow + 2, s));
+        LV_CUDA(cudaMemsetAsync(big, 0, sizeof(int32_t), s));
+        big_rows_kernel<<<grid_items(n), 256, 0, s>>>(g, nullptr, big + 1, big);
         LV_LAUNCH_CHECK();
+        symmetry_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, big + 1, big, dsev);
+        LV_LAUNCH_CHECK();
+        dfree(big, s);
     }
     unsigned long long tm = 0;
     LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -363,6 +442,15 @@ lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, in
     LV_TRY(dalloc_n(&h.arcs, (size_t)h.A, s));
     vf_fill_kernel<<<grid_rows(n), 256, 0, s>>>(g, keep, newid, loop, extra, h.off, h.arcs);
     LV_LAUNCH_CHECK();
+    int32_t *big = nullptr;
+    LV_TRY(dalloc_n(&big, (size_t)g.A / kBigRow + 2, s));
+    LV_CUDA(cudaMemsetAsync(big, 0, sizeof(int32_t), s));
+    big_rows_kernel<<<grid_items(n), 256, 0, s>>>(g, keep, big + 1, big);
+    LV_LAUNCH_CHECK();
+    vf_fill_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, keep, big + 1, big, newid, loop, extra,
+                                                      h.off, h.arcs);
+    LV_LAUNCH_CHECK();
+    dfree(big, s);
     vf_map_kernel<<<grid_items(n), 256, 0, s>>>(n, keep, newid, target, map);
     LV_LAUNCH_CHECK();
     dfree(d1, s);

@@ -133,12 +133,15 @@ __device__ __forceinline__ bool prio_greater(unsigned long long hu, int u, unsig
 }
 
 // ------------------------------------------------------------ grid barrier
-// Barrier across all blocks of a cooperative (co-resident) launch.  The wait
-// is bounded: a block that waits longer than the limit sets *err and gets
-// false, and callers then return, so a fault can never hang the device.
+// Barrier across all blocks of a cooperative (co-resident) launch, on a
+// monotonic ticket counter: the k-th barrier of a launch completes when the
+// counter reaches k * gridDim.x, so arriving is one atomic and nobody resets
+// anything.  The counter starts at 0 for every launch (callers clear it).
+// The wait is bounded: a block that waits longer than the limit sets *err
+// and gets false, and callers then return, so a fault cannot hang the device.
 struct GridBarrier {
     unsigned int count;
-    unsigned int gen;
+    unsigned int unused;
 };
 constexpr unsigned long long kBarrierSpinLimit = 1ull << 27;  // x ~20-100 ns sleeps
 
@@ -147,24 +150,18 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned int *vgen = &gb->gen;
-        const unsigned int g = *vgen;
         __threadfence();
-        const unsigned int arrived = atomicAdd(&gb->count, 1u);
-        if (arrived == gridDim.x - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*vgen == g) {
-                if (++spins > kBarrierSpinLimit) {
-                    ok = 0;
-                    atomicExch(err, 1);
-                    break;
-                }
-                __nanosleep(20);
+        const unsigned int ticket = atomicAdd(&gb->count, 1u);
+        const unsigned int target = (ticket / gridDim.x + 1u) * gridDim.x;
+        volatile unsigned int *vc = &gb->count;
+        unsigned long long spins = 0;
+        while ((int)(*vc - target) < 0) {
+            if (++spins > kBarrierSpinLimit) {
+                ok = 0;
+                atomicExch(err, 1);
+                break;
             }
+            __nanosleep(20);
         }
         __threadfence();
         s_ok = ok && (*(volatile int *)err == 0);

@@ -43,7 +43,14 @@ struct Buckets {
     int32_t *host_off = nullptr;     // host copy of bucket_off
     int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
 };
-constexpr int kHubChunk = 1024;      // arcs (and occupied slots) per block item of a hub
+#ifndef LV_HUB_CHUNK
+#define LV_HUB_CHUNK 512
+#endif
+#ifndef LV_HUB_FAST_OCC
+#define LV_HUB_FAST_OCC 4096
+#endif
+constexpr int kHubChunk = LV_HUB_CHUNK;        // arcs (and occupied slots) per block item of a hub
+constexpr int kHubFastOcc = LV_HUB_FAST_OCC;   // hub decided by its last chunk below this many labels
 struct BinLimits {
     int lane_arcs = 4, warp_max = 128, cta_max = 4096;
 };
@@ -60,7 +67,7 @@ struct IterStats {
     int err;                       // a hash probe bound was exceeded
     GridBarrier bar;               // barrier state of the persistent sweep (reset with the stats)
     int bar_err;                   // a grid barrier wait expired
-    int pad;
+    int max_occ;                   // largest distinct-label count of a hub this sweep
 };
 struct PhaseState {
     DGraph g;
@@ -69,11 +76,12 @@ struct PhaseState {
     int32_t *C = nullptr;
     unsigned long long *comm[2] = {nullptr, nullptr};  // {a_C, |C|}; two buffers when coloured
     int4 *moves[2] = {nullptr, nullptr};               // {i, old, new, k_i}
-    int32_t *move_count = nullptr;  // one slot per active class + a carry slot
+    int32_t *move_count = nullptr;  // per active class: moves, block / warp work counters; + carry
     int32_t *act = nullptr;         // device: active classes (those with arcs)
     int n_act = 0;
     bool coloured = false;
     long long g_total = 0;          // classes swept so far in the phase (buffer parity)
+    bool hub_fast = false;          // hubs decided by their last arc chunk (no extra barrier)
     IterStats *stats = nullptr;
     GridBarrier *bar = nullptr;   // &stats->bar
     int *bar_err = nullptr;       // &stats->bar_err

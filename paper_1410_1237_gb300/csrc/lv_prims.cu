@@ -323,5 +323,11 @@ extern "C" void lv_trace_reset(void) {
     lv::TraceBuf tb = lv::trace_buffer();
     cudaDeviceSynchronize();
     cudaMemset(tb.n, 0, sizeof(unsigned int));
+    cudaMemset(tb.buf, 0, sizeof(unsigned long long) * lv::kTraceCap);
+}
+extern "C" void lv_trace_read_region(unsigned long long *out, int offset, int count) {
+    lv::TraceBuf tb = lv::trace_buffer();
+    cudaDeviceSynchronize();
+    cudaMemcpy(out, tb.buf + offset, count * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
 }
 #endif

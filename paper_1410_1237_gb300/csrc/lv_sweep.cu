@@ -15,7 +15,9 @@
 //            (shared-memory table); warp items: 32/G vertices of G lanes each,
 //            G = 1..32 chosen per vertex so each lane holds a few arcs
 //   [barrier, stage B: per hub, blocks evaluate chunks of its occupied
-//    slots; the last one to finish combines them and decides]
+//    slots; the last one to finish combines them and decides -- or, when the
+//    hubs' distinct-label counts were small in the previous iteration, the
+//    last arc chunk of each hub decides it in stage A without a barrier]
 //   barrier
 // Coloured phases keep the community state {a_C, |C|} in two buffers.  Class
 // g reads X[g % 2] and writes X[(g + 1) % 2], which before class g holds the
@@ -64,7 +66,10 @@ struct Sweep {
     int32_t *C;
     unsigned long long *comm0, *comm1;
     int4 *moves0, *moves1;
-    int32_t *move_count;  // per active class, plus a carry slot at [n_act]
+    // [0, n_act): moves per class; [n_act, 2 n_act): block-item counters;
+    // [2 n_act, 3 n_act): warp-item counters; [3 n_act]: moves of the last
+    // class of the previous launch
+    int32_t *move_count;
     IterStats *stats;
     const int32_t *__restrict__ order;
     const int32_t *__restrict__ bucket_off;
@@ -80,6 +85,7 @@ struct Sweep {
     int n_act;
     long long g0;  // classes swept in this phase before this launch
     int coloured;
+    int hub_fast;  // 1: the last arc chunk of a hub decides it (no hub barrier)
     int n;
     long long two_m;
     GridBarrier *bar;
@@ -365,10 +371,64 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
     return a;
 }
 
+// Hub decision by one block over the hub's whole occupied list (slots reset
+// to empty; counters cleared for the next use).
+__device__ void hub_decide_all(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc) {
+    const int i = s.order[p];
+    const int ci = ldC(s, i), ki = s.k[i];
+    int2 *tab = s.hub_table + s.hub_off[p];
+    const int32_t *occ = s.hub_occ + s.hub_off[p];
+    const int n_occ = __ldcg(&s.hub_cnt[p]);
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    for (int q0 = threadIdx.x; q0 < n_occ; q0 += kU * kSwBlock) {
+        int hh[kU];
+        int2 kv[kU];
+        unsigned long long cm[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int q = q0 + u * kSwBlock;
+            hh[u] = q < n_occ ? __ldcg(&occ[q]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) kv[u] = hh[u] >= 0 ? __ldcg(&tab[hh[u]]) : make_int2(kEmpty, 0);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (hh[u] >= 0) __stcg(&tab[hh[u]], make_int2(kEmpty, 0));
+            cm[u] = (kv[u].x != kEmpty && kv[u].x != ci) ? __ldcg(&cc.xr[kv[u].x]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kv[u].x == kEmpty) continue;
+            if (kv[u].x == ci) {
+                e_old = kv[u].y;
+                continue;
+            }
+            best_take(b, s.two_m * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
+                      comm_size(cm[u]), kv[u].y);
+        }
+    }
+    block_best(b, e_old, red);
+    if (threadIdx.x == 0) {
+        __stcg(&s.hub_cnt[p], 0);
+        __stcg(&s.hub_done[p], 0);
+        atomicMax(&s.stats->max_occ, n_occ);
+        if (decide(s, cc, i, ci, ki, b, e_old, acc)) {
+            commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+            acc.moved += 1;
+        }
+    }
+    __syncthreads();
+}
+
 // Hub arc chunk: inserts kHubChunk arcs of one hub into its global table,
 // merging equal labels within each warp first; a claimed slot is appended to
-// the hub's occupied list.
-__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) {
+// the hub's occupied list.  With hub_fast, the last chunk of the hub to
+// finish (fenced atomic count, no waiting) decides the hub itself.
+__device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, BlockRed &red,
+                          Acc &acc) {
+    __shared__ int s_last_acc;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
     const int p = lo + a;
@@ -407,7 +467,7 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) 
                         done = true;
                     } else if (cur == kEmpty) {
                         const int prev = atomicCAS(kp, kEmpty, c);
-                        if (prev == kEmpty) occ[atomicAdd(occ_cnt, 1)] = (int)h;
+                        if (prev == kEmpty) __stcg(&occ[atomicAdd(occ_cnt, 1)], (int)h);
                         if (prev == kEmpty || prev == c) {
                             atomicAdd(&tab[h].y, sum);
                             done = true;
@@ -417,6 +477,19 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) 
                 }
                 if (!done) acc.err = 1;
             }
+        }
+    }
+    if (s.hub_fast) {
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nch = s.hub_chunk_off[p + 1] - s.hub_chunk_off[p];
+            s_last_acc = (atomicAdd(&s.hub_done[p], 1) == nch - 1);
+        }
+        __syncthreads();
+        if (s_last_acc) {
+            __threadfence();
+            hub_decide_all(s, cc, p, red, acc);
         }
     }
 }
@@ -492,6 +565,7 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
         }
         __stcg(&s.hub_cnt[p], 0);
         __stcg(&s.hub_done[p], 0);
+        atomicMax(&s.stats->max_occ, n_occ);
         if (decide(s, cc, i, ci, ki, t, eo, acc)) {
             commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
             acc.moved += 1;
@@ -518,11 +592,10 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
     extern __shared__ int dyn[];
     __shared__ BlockRed red;
     __shared__ long long sml[kSwWarps];
+    __shared__ int s_item;
     Acc acc;
-    const int wib = threadIdx.x >> 5;
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int *region = dyn + wib * kWarpRegion;
-    const int gwarp = blockIdx.x * kSwWarps + wib;
-    const int nwarps = gridDim.x * kSwWarps;
     const int gthread = blockIdx.x * kSwBlock + threadIdx.x;
     const int nthreads = gridDim.x * kSwBlock;
     for (int q = 0; q < s.n_act; ++q) {
@@ -537,21 +610,49 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         if (s.coloured) {
             // bring the write buffer up to date with the previous class's moves
             const int4 *mp = (g & 1) ? s.moves0 : s.moves1;
-            const int np = __ldcg(&s.move_count[q == 0 ? s.n_act : q - 1]);
+            const int np = __ldcg(&s.move_count[q == 0 ? 3 * s.n_act : q - 1]);
             for (int t = gthread; t < np; t += nthreads) {
                 const int4 m = __ldcg(&mp[t]);
                 atomicAdd(&cc.xw[m.y], comm_leave(m.w));
                 atomicAdd(&cc.xw[m.z], comm_join(m.w));
             }
         }
+        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
+            trace4(s.tb, 0x600000000ull | (unsigned)q, (unsigned long long)g, gtimer(), 0);
         const int32_t *bo = s.bucket_off + c * (kBins + 1);
         const int b_cta = bo[kBinCta], b_hub = bo[kBinHub], b_end = bo[kBins];
         const int32_t *ca = s.chunk_at + c * (kBins + 1);
         const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
         const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
-        for (int it = blockIdx.x; it < nchunks + n_cta; it += gridDim.x) {
-            if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, acc);
-            else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
+        // block items, handed out by a class counter (the next index is
+        // fetched while the current item runs)
+        const int n_bitems = nchunks + n_cta;
+        if (n_bitems > 0) {
+            int32_t *bctr = s.move_count + s.n_act + q;
+            if (threadIdx.x == 0) s_item = atomicAdd(bctr, 1);
+            __syncthreads();
+            int it = s_item;
+            while (it < n_bitems) {
+                int nxt = 0;
+                if (threadIdx.x == 0) nxt = atomicAdd(bctr, 1);
+#ifdef LV_TRACE
+                const unsigned long long ti0 = gtimer();
+#endif
+                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
+                else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
+                __syncthreads();
+#ifdef LV_TRACE
+                if (threadIdx.x == 0 && blockIdx.x < 64) {
+                    const int vv = it < nchunks ? -1 : s.order[b_cta + it - nchunks];
+                    const int dd = vv < 0 ? kHubChunk : s.off[vv + 1] - s.off[vv];
+                    trace4(s.tb, 0x700000000ull | (unsigned)(it < nchunks ? 0 : 1),
+                           (unsigned long long)g, (unsigned long long)dd, gtimer() - ti0);
+                }
+#endif
+                if (threadIdx.x == 0) s_item = nxt;
+                __syncthreads();
+                it = s_item;
+            }
         }
         __syncthreads();
         // warp items: 32/G vertices of group bin log2(G), largest groups first
@@ -563,12 +664,25 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
                 item_end[gb] = acc_items;
             }
         }
-        for (int it = gwarp; it < item_end[0]; it += nwarps) {
+        int32_t *wctr = s.move_count + 2 * s.n_act + q;
+        int it = 0;
+        if (item_end[0] > 0) {
+            if (lane == 0) it = atomicAdd(wctr, 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+        } else {
+            it = 0;
+        }
+        while (it < item_end[0]) {
+            int nxt = 0;
+            if (lane == 0) nxt = atomicAdd(wctr, 1);
             int gb = kGroupBins - 1;
             while (it >= item_end[gb]) --gb;
             const int first = gb == kGroupBins - 1 ? 0 : item_end[gb + 1];
             const int lo = bo[gb], cnt = bo[gb + 1] - bo[gb];
             const int base = (it - first) << (5 - gb);
+#ifdef LV_TRACE
+            const unsigned long long tw0 = gtimer();
+#endif
             switch (gb) {
             case 5: warp_group_sweep<32>(s, cc, s.order + lo, cnt, base, region, acc); break;
             case 4: warp_group_sweep<16>(s, cc, s.order + lo, cnt, base, region, acc); break;
@@ -577,24 +691,34 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             case 1: warp_group_sweep<2>(s, cc, s.order + lo, cnt, base, region, acc); break;
             default: warp_group_sweep<1>(s, cc, s.order + lo, cnt, base, region, acc); break;
             }
+#ifdef LV_TRACE
+            if (lane == 0 && blockIdx.x < 16)
+                trace4(s.tb, 0x800000000ull | (unsigned)gb, (unsigned long long)g, 0, gtimer() - tw0);
+#endif
+            it = __shfl_sync(0xffffffffu, nxt, 0);
         }
-        if (n_hub > 0) {
+#ifdef LV_TRACE
+        __syncthreads();
+        if (threadIdx.x == 0 && g < (long long)(kTraceCap / 4))
+            atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g], gtimer());
+#endif
+        if (n_hub > 0 && !s.hub_fast) {
             if (!grid_sync(s.bar, s.err)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
                 hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
-            if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 4)
-                trace4(s.tb, 0x400000000ull | (unsigned)q, (unsigned long long)blockIdx.x, 0, gtimer());
+#ifdef LV_TRACE
+            __syncthreads();
+#endif
         }
+#ifdef LV_TRACE
+        if (threadIdx.x == 0 && g < (long long)(kTraceCap / 4))
+            atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g + 1], gtimer());
+#endif
         if (s.coloured || q + 1 < s.n_act)
             if (!grid_sync(s.bar, s.err)) return;
-        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
-            trace4(s.tb, 0x500000000ull | (unsigned)q, ((unsigned long long)n_cta << 32) | (unsigned)n_hub,
-                   ((unsigned long long)(bo[kGroupBins] - bo[kGroupBins - 1]) << 32) |
-                       (unsigned)(bo[kGroupBins - 1] - bo[0]),
-                   gtimer());
     }
     if (s.coloured && blockIdx.x == 0 && threadIdx.x == 0 && s.n_act > 0)
-        s.move_count[s.n_act] = __ldcg(&s.move_count[s.n_act - 1]);  // carry for the next launch
+        s.move_count[3 * s.n_act] = __ldcg(&s.move_count[s.n_act - 1]);  // carry for the next launch
     // sum of a_C^2 over all communities of the state the sweep leaves
     const unsigned long long *xf =
         s.coloured && ((s.g0 + s.n_act) & 1) ? s.comm1 : s.comm0;
@@ -672,7 +796,7 @@ size_t hub_part_bytes() { return sizeof(HubPart); }
 
 lv_status init_phase(PhaseState &ps, cudaStream_t s) {
     LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-    LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * ((size_t)ps.n_act + 1), s));
+    LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * (3 * (size_t)ps.n_act + 1), s));
     ps.g_total = 0;
     init_phase_kernel<<<grid_for(ps.g.n, 256, g_num_sms * 8), 256, 0, s>>>(
         ps.g.n, ps.k, ps.loop, ps.C, ps.comm[0], ps.coloured ? ps.comm[1] : nullptr, ps.stats);
@@ -707,6 +831,7 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.n_act = ps.n_act;
     a.g0 = ps.g_total;
     a.coloured = ps.coloured ? 1 : 0;
+    a.hub_fast = ps.hub_fast ? 1 : 0;
     a.n = ps.g.n;
     a.two_m = ps.two_m;
     a.bar = ps.bar;
