@@ -192,3 +192,79 @@ def workload(name: str):
     g = wl["gen"]()
     g.name = name
     return g, dict(wl["params"])
+
+
+# ----------------------------------------------------------------------------
+# Batches of graphs: a disjoint union stored as one CSR plus vertex offsets.
+# ----------------------------------------------------------------------------
+@dataclass
+class Batch:
+    """``num_graphs`` graphs; graph g owns vertices [gptr[g], gptr[g+1]) of the
+    union CSR (rowptr, col, w), and its arcs stay inside that range."""
+
+    gptr: np.ndarray
+    rowptr: np.ndarray
+    col: np.ndarray
+    w: np.ndarray
+    name: str = ""
+
+    @property
+    def num_graphs(self) -> int:
+        return len(self.gptr) - 1
+
+    @property
+    def n(self) -> int:
+        return int(self.gptr[-1])
+
+    @property
+    def arcs(self) -> int:
+        return int(self.rowptr[-1])
+
+    def graph(self, g: int) -> Graph:
+        """Graph g alone, with local vertex ids."""
+        lo, hi = int(self.gptr[g]), int(self.gptr[g + 1])
+        a0, a1 = int(self.rowptr[lo]), int(self.rowptr[hi])
+        return Graph(hi - lo, self.rowptr[lo:hi + 1] - a0, self.col[a0:a1] - lo,
+                     self.w[a0:a1].copy(), f"{self.name}[{g}]")
+
+
+def concat(graphs: list, name: str = "") -> Batch:
+    """Disjoint union of graphs (vertex ids shifted by the preceding sizes)."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    gptr = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(ns, out=gptr[1:])
+    arcs = np.array([g.arcs for g in graphs], dtype=np.int64)
+    aoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(arcs, out=aoff[1:])
+    rowptr = np.empty(int(gptr[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(aoff[-1]), dtype=np.int32)
+    w = np.empty(int(aoff[-1]), dtype=np.int32)
+    for i, g in enumerate(graphs):
+        lo, hi = int(gptr[i]), int(gptr[i + 1])
+        rowptr[lo:hi] = g.rowptr[:-1] + aoff[i]
+        col[aoff[i]:aoff[i + 1]] = g.col + lo
+        w[aoff[i]:aoff[i + 1]] = g.w
+    rowptr[-1] = aoff[-1]
+    return Batch(gptr, rowptr, col, w, name)
+
+
+def planted_batch(num_graphs: int = 4096, nmin: int = 100, nmax: int = 50_000, bmin: int = 2,
+                  bmax: int = 200, intra_deg: float = 12.0, inter_deg: float = 2.0, wmax: int = 8,
+                  seed: int = 4) -> Batch:
+    """Batch of planted-partition graphs: n log-uniform in [nmin, nmax], B
+    uniform in [bmin, bmax] clipped so blocks have >= 3 vertices, p_in so the
+    mean intra-block degree is intra_deg, p_out so the mean inter-block degree
+    is inter_deg, weights uniform in [1, wmax].  Graph g uses seed
+    (seed << 20) + g."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(nmin), np.log(nmax), size=num_graphs)).astype(np.int64)
+    bs = rng.integers(bmin, bmax + 1, size=num_graphs)
+    graphs = []
+    for g in range(num_graphs):
+        n = int(ns[g])
+        b = int(min(bs[g], max(1, n // 3)))
+        sz = n / b
+        p_in = min(1.0, intra_deg / max(sz - 1.0, 1.0))
+        p_out = min(1.0, inter_deg / max(n - sz, 1.0)) if b > 1 else 0.0
+        graphs.append(planted(n, b, p_in, p_out, 1, wmax, seed=(seed << 20) + g))
+    return concat(graphs, f"planted_batch({num_graphs},seed={seed})")

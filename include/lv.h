@@ -221,6 +221,79 @@ const char *lv_last_error(void);
 /* Release the handle and all its device memory (NULL is a no-op). */
 void lv_graph_destroy(lv_graph *g);
 
+/* ---------------------------------------------------------------- batches
+ * A batch holds many independent graphs and runs the method on all of them
+ * at once: each sweep is one persistent launch over the vertices of every
+ * graph still iterating, and each rebuild one pass over all graphs.  Every
+ * graph follows exactly the phase and iteration control of lv_run (its own
+ * 2m, thresholds and stopping tests), so its labels, numerators and
+ * iteration counts are those lv_run gives for it alone.  Graphs that finish
+ * early are skipped by later sweeps.  Colouring is not batched: lv_batch_run
+ * returns LV_ERR_ARG when colouring is on and a graph has at least
+ * color_cutoff vertices after vertex following (run such graphs alone). */
+typedef struct lv_batch lv_batch; /* opaque, owned by the library */
+
+/* Per-graph record of a batched run. */
+typedef struct {
+    int64_t n;          /* vertices of the graph */
+    int64_t arcs;       /* stored arcs */
+    int64_t two_m;      /* 2m of the graph */
+    int64_t n_final;    /* communities after its last phase */
+    int64_t N_final;    /* modularity numerator after its last phase */
+    double q;           /* N_final / (2m)^2 */
+    int32_t num_phases; /* phases it ran */
+    int32_t iterations; /* iterations over all its phases */
+} lv_batch_graph_info;
+
+/* Create a batch: the disjoint union of n_graphs graphs as ONE CSR whose
+ * vertices are numbered graph after graph.
+ *   n_graphs  >= 1
+ *   gptr      int64[n_graphs+1]: graph g owns vertices [gptr[g], gptr[g+1]);
+ *             gptr[0] = 0, strictly increasing (every graph has a vertex),
+ *             gptr[n_graphs] = n < 2^31 - 1
+ *   rowptr, col, w  the union CSR under the lv_graph_create contract, with
+ *             union vertex ids; every arc must stay inside its graph
+ *   ptrs_on_device  applies to gptr, rowptr, col and w alike
+ * Each graph needs 2m_g < 2^31 (LV_ERR_OVERFLOW) and m_g > 0 (LV_ERR_EMPTY);
+ * the union needs fewer than 2^31 stored arcs.  An arc between two graphs
+ * or a malformed gptr gives LV_ERR_ARG.  Other errors as lv_graph_create. */
+lv_status lv_batch_create(lv_batch **out, int32_t n_graphs, const int64_t *gptr,
+                          const int64_t *rowptr, const int32_t *col, const int32_t *w,
+                          int ptrs_on_device, void *cuda_stream);
+
+/* Run every graph of the batch with parameters *p (NULL = defaults); the
+ * bin limits apply to all graphs.  Replaces the results of an earlier run. */
+lv_status lv_batch_run(lv_batch *b, const lv_params *p);
+
+/* Number of graphs in the batch. */
+lv_status lv_batch_num_graphs(const lv_batch *b, int32_t *out);
+
+/* Labels after phase `phase` of the last run, numbered per graph from 0 as
+ * lv_get_labels numbers them for the graph alone.
+ *   graph >= 0: int32[n_g] of that graph; phase -1 = its last phase, else a
+ *               phase it ran (LV_ERR_STATE otherwise)
+ *   graph = -1: int32[n] of all graphs in union order; phase -1 = each
+ *               graph's last phase, else phase p of the graphs that ran it
+ *               and the final labels of those that had stopped before p
+ *               (p < the largest phase count)
+ * `out` is host memory, or device memory when ptr_on_device = 1. */
+lv_status lv_batch_get_labels(const lv_batch *b, int32_t graph, int32_t phase, int32_t *out,
+                              int ptr_on_device);
+
+/* Per-graph summary, and per-graph phase record (phase -1 = its last). */
+lv_status lv_batch_get_graph_info(const lv_batch *b, int32_t graph, lv_batch_graph_info *out);
+lv_status lv_batch_get_phase_info(const lv_batch *b, int32_t graph, int32_t phase,
+                                  lv_phase_info *out);
+
+/* Whole-batch totals: num_phases = largest phase count; total_iterations
+ * and edge_visits = the sums over graphs of what lv_run reports for each;
+ * vf_n = vertices of the union after vertex following; sweep_launches =
+ * batched sweeps; times (collect_timing) and kernel launches of the run. */
+lv_status lv_batch_get_stats(const lv_batch *b, lv_stats *out);
+
+/* Release the batch and its device memory (NULL is a no-op). */
+void lv_batch_destroy(lv_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

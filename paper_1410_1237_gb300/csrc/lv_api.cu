@@ -38,40 +38,12 @@ struct PhaseRec {
     int32_t *colors = nullptr;  // kept copy (keep_graphs, coloured phases)
 };
 
-struct Timer {
-    bool on = false;
-    cudaStream_t s = nullptr;
-    std::vector<cudaEvent_t> ev;
-    int mark() {  // returns an index, or -1 when timing is off
-        if (!on) return -1;
-        cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return -1;
-        cudaEventRecord(e, s);
-        ev.push_back(e);
-        return (int)ev.size() - 1;
-    }
-    double ms(int a, int b) const {
-        if (a < 0 || b < 0) return -1.0;
-        float t = 0.f;
-        if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) return -1.0;
-        return (double)t;
-    }
-    void clear() {
-        for (auto e : ev) cudaEventDestroy(e);
-        ev.clear();
-    }
-};
-
-bool gain_below(int64_t Nc, int64_t Np, double theta) {
-    const int64_t d = Nc - Np;
-    const int64_t b = Np < 0 ? -Np : Np;
-    return (double)d < theta * (double)b;
-}
-
 std::once_flag g_setup_once;
 lv_status g_setup_status = LV_OK;
 
-lv_status ensure_setup(cudaStream_t s) {
+}  // namespace
+
+lv_status lv::ensure_setup(cudaStream_t s) {
     std::call_once(g_setup_once, [&] {
         void *p = nullptr;
         g_setup_status = dalloc(&p, 16, s);  // creates the pool, reads the SM count
@@ -82,8 +54,6 @@ lv_status ensure_setup(cudaStream_t s) {
     });
     return g_setup_status;
 }
-
-}  // namespace
 
 struct lv_graph {
     int device = 0;
@@ -247,7 +217,6 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
     int64_t n_p = 0;
     int64_t moved_prev = 0;
     int ev_prev0 = -1, ev_prev1 = -1;
-    ps.hub_fast = false;
     auto record = [&](int t, int64_t moved, int64_t N, int e0, int e1) {
         IterRecord r;
         r.st.phase = phase;
@@ -270,7 +239,6 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
         const int e1 = h->timer.mark();
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
-        ps.hub_fast = hs.max_occ <= kHubFastOcc;  // scheduling only: results do not depend on it
         const int64_t N_prev = ps.two_m * (int64_t)hs.sum_ein - (int64_t)hs.sum_a2;  // N(C^{step-1})
         const int64_t moved = hs.moved;
         if (step == 1) {
@@ -312,7 +280,6 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
     bool have_np = false;
     int64_t n_p = 0;
     int64_t sum_ein = sum_loops;
-    ps.hub_fast = false;
     for (int t = 1;; ++t) {
         LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
         LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t) * (size_t)ps.n_act, s));
@@ -322,7 +289,6 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
         const int e1 = h->timer.mark();
         IterStats hs;
         LV_TRY(read_stats(h, ps, &hs));
-        ps.hub_fast = hs.max_occ <= kHubFastOcc;  // scheduling only: results do not depend on it
         sum_ein += (int64_t)hs.delta_ein;
         const int64_t N = ps.two_m * sum_ein - (int64_t)hs.sum_a2;
         IterRecord r;

@@ -309,7 +309,8 @@ static int grid_items(int64_t items) { return grid_for(items, 256, g_num_sms * 1
 
 lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *col,
                              const int32_t *w, DGraph *out, int32_t **k_out, int32_t **loop_out,
-                             int64_t *two_m_out, int *scratch_pinned, cudaStream_t s) {
+                             int64_t *two_m_out, int *scratch_pinned, cudaStream_t s,
+                             bool limit_two_m) {
     *out = DGraph();
     *k_out = nullptr;
     *loop_out = nullptr;
@@ -374,7 +375,7 @@ lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *co
     LV_CUDA(cudaStreamSynchronize(s));
     st = severity_to_status(scratch_pinned[0]);
     if (st == LV_OK) {
-        if (tm >= (1ull << 31)) st = LV_ERR_OVERFLOW;
+        if (limit_two_m && tm >= (1ull << 31)) st = LV_ERR_OVERFLOW;
         else if (tm == 0) st = LV_ERR_EMPTY;
     }
     dfree(dsev, s);

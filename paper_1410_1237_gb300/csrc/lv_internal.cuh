@@ -120,6 +120,24 @@ __device__ __forceinline__ T block_sum_256(T v, T *smem8) {
     return r;
 }
 
+// Warp-wide segmented add: lane l holds (key, v); equal keys occupy
+// contiguous lanes.  Each run's sum of v is added to out[key] by one atomic.
+// Lanes with valid == false take no part.
+__device__ __forceinline__ void warp_run_add(int key, unsigned long long v, bool valid,
+                                             unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int k = valid ? key : -1 - lane;
+    if (!valid) v = 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long vu = __shfl_up_sync(0xffffffffu, v, o);
+        const int ku = __shfl_up_sync(0xffffffffu, k, o);
+        if (lane >= o && ku == k) v += vu;
+    }
+    const int kn = __shfl_down_sync(0xffffffffu, k, 1);
+    if (valid && v && (lane == 31 || kn != k)) atomicAdd(&out[key], v);
+}
+
 // splitmix64 output function (Steele, Lea, Flood 2014): colouring priority
 __device__ __forceinline__ unsigned long long prio_hash(unsigned long long x) {
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;

@@ -1,6 +1,8 @@
 // lv_ops.cuh -- host-side entry points of the kernel translation units.
 #pragma once
 
+#include <vector>
+
 #include "lv_internal.cuh"
 
 namespace lv {
@@ -8,10 +10,12 @@ namespace lv {
 // lv_graph.cu ------------------------------------------------------------
 lv_status severity_to_status(int sev);
 // Validate a device-resident CSR (Sec. 2 contract) and build the internal
-// graph plus k (weighted degree) and loop (self-loop weight).
+// graph plus k (weighted degree) and loop (self-loop weight).  limit_two_m =
+// false skips the 2m < 2^31 test (a batch checks each of its graphs instead).
 lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *col,
                              const int32_t *w, DGraph *out, int32_t **k, int32_t **loop,
-                             int64_t *two_m, int *scratch_pinned, cudaStream_t s);
+                             int64_t *two_m, int *scratch_pinned, cudaStream_t s,
+                             bool limit_two_m = true);
 lv_status compute_degrees(const DGraph &g, int32_t *k, int32_t *loop, cudaStream_t s);
 lv_status iota(int32_t n, int32_t *out, cudaStream_t s);
 // Vertex following (Sec. 4.3); allocates *out; map[v] = vertex of v in *out.
@@ -44,13 +48,9 @@ struct Buckets {
     int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
 };
 #ifndef LV_HUB_CHUNK
-#define LV_HUB_CHUNK 512
+#define LV_HUB_CHUNK 1024
 #endif
-#ifndef LV_HUB_FAST_OCC
-#define LV_HUB_FAST_OCC 4096
-#endif
-constexpr int kHubChunk = LV_HUB_CHUNK;        // arcs (and occupied slots) per block item of a hub
-constexpr int kHubFastOcc = LV_HUB_FAST_OCC;   // hub decided by its last chunk below this many labels
+constexpr int kHubChunk = LV_HUB_CHUNK;  // arcs (and occupied slots) per block item of a hub
 struct BinLimits {
     int lane_arcs = 4, warp_max = 128, cta_max = 4096;
 };
@@ -81,11 +81,19 @@ struct PhaseState {
     int n_act = 0;
     bool coloured = false;
     long long g_total = 0;          // classes swept so far in the phase (buffer parity)
-    bool hub_fast = false;          // hubs decided by their last arc chunk (no extra barrier)
     IterStats *stats = nullptr;
     GridBarrier *bar = nullptr;   // &stats->bar
     int *bar_err = nullptr;       // &stats->bar_err
     long long two_m = 0;
+    // batched runs over a disjoint union of graphs (all null otherwise): the
+    // sweep skips graphs whose active flag is 0 and sums the modularity terms
+    // and moves per graph instead of into stats
+    const int32_t *gid = nullptr;          // graph of each vertex
+    const long long *two_m_g = nullptr;    // 2m of each graph
+    const uint8_t *active_g = nullptr;     // graphs still iterating in this phase
+    unsigned long long *g_ein = nullptr;   // per graph: sum of e_{i->C(i)} incl. loops
+    unsigned long long *g_a2 = nullptr;    // per graph: sum of a_C^2 after the sweep
+    unsigned long long *g_moved = nullptr; // per graph: moves proposed
 };
 // C = identity, comm = (k, 1) (both buffers when coloured); stats->sum_ein =
 // sum of loops, stats->sum_a2 = sum of k^2; move counters cleared
@@ -115,4 +123,39 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
 
 namespace lv {
 lv_status sweep_setup();  // one-time kernel attributes (large dynamic shared memory)
+// process-wide setup (memory pool, SM count, kernel attributes), run once
+lv_status ensure_setup(cudaStream_t s);
+
+// Signed relative stopping test of Sec. 4.1 on exact numerators:
+// (N_C - N_P) < theta |N_P|, converted to double once.
+inline bool gain_below(int64_t Nc, int64_t Np, double theta) {
+    const int64_t d = Nc - Np;
+    const int64_t b = Np < 0 ? -Np : Np;
+    return (double)d < theta * (double)b;
+}
+
+// CUDA events on one stream, recorded on demand (timing switched on per run).
+struct Timer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<cudaEvent_t> ev;
+    int mark() {  // returns an index, or -1 when timing is off
+        if (!on) return -1;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        return (int)ev.size() - 1;
+    }
+    double ms(int a, int b) const {
+        if (a < 0 || b < 0) return -1.0;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) return -1.0;
+        return (double)t;
+    }
+    void clear() {
+        for (auto e : ev) cudaEventDestroy(e);
+        ev.clear();
+    }
+};
 }  // namespace lv

@@ -15,9 +15,7 @@
 //            (shared-memory table); warp items: 32/G vertices of G lanes each,
 //            G = 1..32 chosen per vertex so each lane holds a few arcs
 //   [barrier, stage B: per hub, blocks evaluate chunks of its occupied
-//    slots; the last one to finish combines them and decides -- or, when the
-//    hubs' distinct-label counts were small in the previous iteration, the
-//    last arc chunk of each hub decides it in stage A without a barrier]
+//    slots; the last one to finish combines them and decides]
 //   barrier
 // Coloured phases keep the community state {a_C, |C|} in two buffers.  Class
 // g reads X[g % 2] and writes X[(g + 1) % 2], which before class g holds the
@@ -85,13 +83,30 @@ struct Sweep {
     int n_act;
     long long g0;  // classes swept in this phase before this launch
     int coloured;
-    int hub_fast;  // 1: the last arc chunk of a hub decides it (no hub barrier)
     int n;
     long long two_m;
     GridBarrier *bar;
     int *err;
     TraceBuf tb;
+    // batched runs (disjoint union of graphs); gid == nullptr otherwise
+    const int32_t *__restrict__ gid;       // graph of each vertex
+    const long long *__restrict__ two_m_g; // 2m of each graph
+    const uint8_t *__restrict__ active_g;  // graphs still iterating
+    unsigned long long *g_ein;             // per graph: sum of e_{i->C(i)} incl. loops
+    unsigned long long *g_a2;              // per graph: sum of a_C^2
+    unsigned long long *g_moved;           // per graph: moves
 };
+
+// 2m of the graph holding vertex i
+__device__ __forceinline__ long long tm_of(const Sweep &s, int i) {
+    return s.gid ? s.two_m_g[s.gid[i]] : s.two_m;
+}
+// false for vertices of batched graphs that stopped iterating
+__device__ __forceinline__ bool live(const Sweep &s, int i) {
+    return !s.gid || s.active_g[s.gid[i]];
+}
+// modularity terms of one decided vertex, for block items
+__device__ __forceinline__ void add_terms(const Sweep &s, struct Acc &acc, int i, int ein, bool mv);
 
 // per-class view: read buffer, write buffer, move list and its counter
 struct Cls {
@@ -106,6 +121,17 @@ struct Acc {
     long long ein = 0, dein = 0;
     int moved = 0, err = 0;
 };
+
+__device__ __forceinline__ void add_terms(const Sweep &s, Acc &acc, int i, int ein, bool mv) {
+    if (s.gid) {
+        const int g = s.gid[i];
+        if (ein) atomicAdd(&s.g_ein[g], (unsigned long long)ein);
+        if (mv) atomicAdd(&s.g_moved[g], 1ull);
+    } else {
+        acc.ein += ein;
+        acc.moved += mv ? 1 : 0;
+    }
+}
 
 __device__ __forceinline__ int ldC(const Sweep &s, int j) { return __ldcg(&s.C[j]); }
 
@@ -193,7 +219,7 @@ __device__ __forceinline__ void best_shfl_xor(Best &b, int o) {
 template <int ST>
 __device__ __forceinline__ void eval_slots(const Sweep &s, const Cls &cc, const int *key,
                                            const int *val, int first, unsigned mask, int step,
-                                           int ci, int ki, Best &b, int &e_old) {
+                                           int ci, int ki, long long tm, Best &b, int &e_old) {
     for (int s0 = first; s0 <= (int)mask; s0 += kU * step) {
         int kk[kU], vv[kU];
         unsigned long long cm[kU];
@@ -213,18 +239,19 @@ __device__ __forceinline__ void eval_slots(const Sweep &s, const Cls &cc, const 
                 e_old = vv[u];
                 continue;
             }
-            best_take(b, s.two_m * (long long)vv[u] - (long long)ki * comm_a(cm[u]), kk[u],
+            best_take(b, tm * (long long)vv[u] - (long long)ki * comm_a(cm[u]), kk[u],
                       comm_size(cm[u]), vv[u]);
         }
     }
 }
 
-// decision for vertex i given the reduced candidate; true on a move
+// decision for vertex i given the reduced candidate; true on a move.  ein
+// receives e_{i->C(i)} including the self-loop (the vertex's modularity term).
 __device__ __forceinline__ bool decide(const Sweep &s, const Cls &cc, int i, int ci, int ki,
-                                       const Best &b, int e_old, Acc &acc) {
+                                       long long tm, const Best &b, int e_old, Acc &acc, int &ein) {
     const unsigned long long cmi = __ldcg(&cc.xr[ci]);
-    const long long s_old = s.two_m * (long long)e_old - (long long)ki * (comm_a(cmi) - ki);
-    acc.ein += (long long)e_old + s.loop[i];
+    const long long s_old = tm * (long long)e_old - (long long)ki * (comm_a(cmi) - ki);
+    ein = e_old + s.loop[i];
     if (b.c == INT_MAX) return false;
     if (b.s - s_old <= 0) return false;
     if (comm_size(cmi) == 1 && b.size == 1 && b.c > ci) return false;  // singlet rule
@@ -289,11 +316,16 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
     int *val = region + kGroupTableInts + lane / G;
     const unsigned lt = (1u << lane) - 1u;
     const int vi = base + lane / G;
-    const bool valid = vi < nverts;
+    bool valid = vi < nverts;
     int i = 0, beg = 0, end = 0, ci = 0, ki = 0;
+    long long tm = 0;
     unsigned mask = 0;
     if (valid) {
         i = verts[vi];
+        valid = live(s, i);
+    }
+    if (valid) {
+        tm = tm_of(s, i);
         beg = s.off[i];
         end = s.off[i + 1];
         ci = ldC(s, i);
@@ -311,23 +343,37 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
     Best b;
     best_init(b);
     int e_old = 0;
-    if (valid) eval_slots<ST>(s, cc, key, val, gl, mask, G, ci, ki, b, e_old);
+    if (valid) eval_slots<ST>(s, cc, key, val, gl, mask, G, ci, ki, tm, b, e_old);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
         best_shfl_xor(b, o);
     }
     bool mv = false;
-    if (valid && gl == 0) mv = decide(s, cc, i, ci, ki, b, e_old, acc);
+    int ein = 0;
+    const bool leader = valid && gl == 0;
+    if (leader) mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
     const unsigned bm = __ballot_sync(0xffffffffu, mv);
     if (bm) {
         int pos = 0;
         if (lane == 0) pos = atomicAdd(cc.cnt, __popc(bm));
         pos = __shfl_sync(0xffffffffu, pos, 0);
-        if (mv) {
-            commit(s, cc, pos + __popc(bm & lt), i, ci, b.c, ki);
-            acc.moved += 1;
+        if (mv) commit(s, cc, pos + __popc(bm & lt), i, ci, b.c, ki);
+    }
+    if (s.gid) {
+        // per-graph terms, merged over the warp's leaders of one graph; their
+        // ein sum is at most that graph's 2m < 2^31, so it fits 32 bits
+        const int g = leader ? s.gid[i] : -1 - lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, g);
+        const unsigned se = __reduce_add_sync(peers, (unsigned)ein);
+        const int nm = __popc(peers & bm);
+        if (leader && lane == __ffs(peers) - 1) {
+            if (se) atomicAdd(&s.g_ein[g], (unsigned long long)se);
+            if (nm) atomicAdd(&s.g_moved[g], (unsigned long long)nm);
         }
+    } else if (leader) {
+        acc.ein += ein;
+        acc.moved += mv ? 1 : 0;
     }
     __syncwarp();
 }
@@ -336,6 +382,8 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
 // CTA-bin vertex: the whole block, table in shared memory.
 __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dyn, BlockRed &red,
                                    Acc &acc) {
+    if (!live(s, i)) return;  // block-uniform
+    const long long tm = tm_of(s, i);
     const int beg = s.off[i], end = s.off[i + 1];
     const int ci = ldC(s, i), ki = s.k[i];
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
@@ -351,11 +399,13 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
     Best b;
     best_init(b);
     int e_old = 0;
-    eval_slots<1>(s, cc, key, val, threadIdx.x, mask, kSwBlock, ci, ki, b, e_old);
+    eval_slots<1>(s, cc, key, val, threadIdx.x, mask, kSwBlock, ci, ki, tm, b, e_old);
     block_best(b, e_old, red);
-    if (threadIdx.x == 0 && decide(s, cc, i, ci, ki, b, e_old, acc)) {
-        commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
-        acc.moved += 1;
+    if (threadIdx.x == 0) {
+        int ein = 0;
+        const bool mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
+        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+        add_terms(s, acc, i, ein, mv);
     }
     __syncthreads();
 }
@@ -371,68 +421,15 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
     return a;
 }
 
-// Hub decision by one block over the hub's whole occupied list (slots reset
-// to empty; counters cleared for the next use).
-__device__ void hub_decide_all(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc) {
-    const int i = s.order[p];
-    const int ci = ldC(s, i), ki = s.k[i];
-    int2 *tab = s.hub_table + s.hub_off[p];
-    const int32_t *occ = s.hub_occ + s.hub_off[p];
-    const int n_occ = __ldcg(&s.hub_cnt[p]);
-    Best b;
-    best_init(b);
-    int e_old = 0;
-    for (int q0 = threadIdx.x; q0 < n_occ; q0 += kU * kSwBlock) {
-        int hh[kU];
-        int2 kv[kU];
-        unsigned long long cm[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int q = q0 + u * kSwBlock;
-            hh[u] = q < n_occ ? __ldcg(&occ[q]) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) kv[u] = hh[u] >= 0 ? __ldcg(&tab[hh[u]]) : make_int2(kEmpty, 0);
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (hh[u] >= 0) __stcg(&tab[hh[u]], make_int2(kEmpty, 0));
-            cm[u] = (kv[u].x != kEmpty && kv[u].x != ci) ? __ldcg(&cc.xr[kv[u].x]) : 0ull;
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (kv[u].x == kEmpty) continue;
-            if (kv[u].x == ci) {
-                e_old = kv[u].y;
-                continue;
-            }
-            best_take(b, s.two_m * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
-                      comm_size(cm[u]), kv[u].y);
-        }
-    }
-    block_best(b, e_old, red);
-    if (threadIdx.x == 0) {
-        __stcg(&s.hub_cnt[p], 0);
-        __stcg(&s.hub_done[p], 0);
-        atomicMax(&s.stats->max_occ, n_occ);
-        if (decide(s, cc, i, ci, ki, b, e_old, acc)) {
-            commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
-            acc.moved += 1;
-        }
-    }
-    __syncthreads();
-}
-
 // Hub arc chunk: inserts kHubChunk arcs of one hub into its global table,
 // merging equal labels within each warp first; a claimed slot is appended to
-// the hub's occupied list.  With hub_fast, the last chunk of the hub to
-// finish (fenced atomic count, no waiting) decides the hub itself.
-__device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, BlockRed &red,
-                          Acc &acc) {
-    __shared__ int s_last_acc;
+// the hub's occupied list.
+__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
     const int p = lo + a;
     const int i = s.order[p];
+    if (!live(s, i)) return;  // block-uniform
     const int beg = s.off[i], end = s.off[i + 1];
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
     int2 *tab = s.hub_table + s.hub_off[p];
@@ -479,19 +476,6 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
             }
         }
     }
-    if (s.hub_fast) {
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int nch = s.hub_chunk_off[p + 1] - s.hub_chunk_off[p];
-            s_last_acc = (atomicAdd(&s.hub_done[p], 1) == nch - 1);
-        }
-        __syncthreads();
-        if (s_last_acc) {
-            __threadfence();
-            hub_decide_all(s, cc, p, red, acc);
-        }
-    }
 }
 
 // Hub decision, one block per chunk of the occupied list: evaluates its
@@ -505,6 +489,8 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
     const int p = lo + a;
     const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
     const int i = s.order[p];
+    if (!live(s, i)) return;  // block-uniform; its chunks inserted nothing
+    const long long tm = tm_of(s, i);
     const int ci = ldC(s, i), ki = s.k[i];
     int2 *tab = s.hub_table + s.hub_off[p];
     const int32_t *occ = s.hub_occ + s.hub_off[p];
@@ -536,7 +522,7 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
                 e_old = kv[u].y;
                 continue;
             }
-            best_take(b, s.two_m * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
+            best_take(b, tm * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
                       comm_size(cm[u]), kv[u].y);
         }
     }
@@ -566,10 +552,10 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
         __stcg(&s.hub_cnt[p], 0);
         __stcg(&s.hub_done[p], 0);
         atomicMax(&s.stats->max_occ, n_occ);
-        if (decide(s, cc, i, ci, ki, t, eo, acc)) {
-            commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
-            acc.moved += 1;
-        }
+        int ein = 0;
+        const bool mv = decide(s, cc, i, ci, ki, tm, t, eo, acc, ein);
+        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
+        add_terms(s, acc, i, ein, mv);
     }
     __syncthreads();
 }
@@ -638,7 +624,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
 #ifdef LV_TRACE
                 const unsigned long long ti0 = gtimer();
 #endif
-                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
+                if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, acc);
                 else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
                 __syncthreads();
 #ifdef LV_TRACE
@@ -702,7 +688,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         if (threadIdx.x == 0 && g < (long long)(kTraceCap / 4))
             atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g], gtimer());
 #endif
-        if (n_hub > 0 && !s.hub_fast) {
+        if (n_hub > 0) {
             if (!grid_sync(s.bar, s.err)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
                 hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
@@ -723,9 +709,20 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
     const unsigned long long *xf =
         s.coloured && ((s.g0 + s.n_act) & 1) ? s.comm1 : s.comm0;
     long long a2 = 0;
-    for (int c = gthread; c < s.n; c += nthreads) {
-        const long long x = comm_a(__ldcg(&xf[c]));
-        a2 += x * x;
+    if (s.gid) {  // per graph: communities of a graph are consecutive ids
+        const int nr = (s.n + 31) & ~31;  // whole warps take part in the runs
+        for (int c = gthread; c < nr; c += nthreads) {
+            const bool in = c < s.n;
+            const int g = in ? s.gid[c] : 0;
+            const bool v = in && s.active_g[g];
+            const long long x = v ? comm_a(__ldcg(&xf[c])) : 0;
+            warp_run_add(g, (unsigned long long)(x * x), v, s.g_a2);
+        }
+    } else {
+        for (int c = gthread; c < s.n; c += nthreads) {
+            const long long x = comm_a(__ldcg(&xf[c]));
+            a2 += x * x;
+        }
     }
     const long long t_ein = block_sum_sw(acc.ein, sml);
     const long long t_dein = block_sum_sw(acc.dein, sml);
@@ -831,12 +828,17 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.n_act = ps.n_act;
     a.g0 = ps.g_total;
     a.coloured = ps.coloured ? 1 : 0;
-    a.hub_fast = ps.hub_fast ? 1 : 0;
     a.n = ps.g.n;
     a.two_m = ps.two_m;
     a.bar = ps.bar;
     a.err = ps.bar_err;
     a.tb = trace_buffer();
+    a.gid = ps.gid;
+    a.two_m_g = ps.two_m_g;
+    a.active_g = ps.active_g;
+    a.g_ein = ps.g_ein;
+    a.g_a2 = ps.g_a2;
+    a.g_moved = ps.g_moved;
     void *args[] = {&a};
     LV_CUDA(cudaLaunchCooperativeKernel((void *)sweep_persistent_kernel,
                                         dim3(g_num_sms * g_sweep_blocks_per_sm), dim3(kSwBlock), args,

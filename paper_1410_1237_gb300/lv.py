@@ -68,6 +68,12 @@ class lv_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64)]
 
 
+class lv_batch_graph_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("arcs", ctypes.c_int64), ("two_m", ctypes.c_int64),
+                ("n_final", ctypes.c_int64), ("N_final", ctypes.c_int64), ("q", ctypes.c_double),
+                ("num_phases", ctypes.c_int32), ("iterations", ctypes.c_int32)]
+
+
 _lib = None
 
 # every function declared in include/lv.h, with its ctypes signature
@@ -96,6 +102,16 @@ SIGNATURES = {
     "lv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lv_last_error": (ctypes.c_char_p, []),
     "lv_graph_destroy": (None, [_vp]),
+    "lv_batch_create": (ctypes.c_int, [_P(_vp), ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                       _vp]),
+    "lv_batch_run": (ctypes.c_int, [_vp, _P(lv_params)]),
+    "lv_batch_num_graphs": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
+    "lv_batch_get_labels": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int]),
+    "lv_batch_get_graph_info": (ctypes.c_int, [_vp, ctypes.c_int32, _P(lv_batch_graph_info)]),
+    "lv_batch_get_phase_info": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32,
+                                               _P(lv_phase_info)]),
+    "lv_batch_get_stats": (ctypes.c_int, [_vp, _P(lv_stats)]),
+    "lv_batch_destroy": (None, [_vp]),
 }
 
 
@@ -259,6 +275,63 @@ def lv_status_string(code: int) -> str:
 def lv_graph_destroy(h: int) -> None:
     if h:
         load().lv_graph_destroy(h)
+
+
+def _arr(x, dtype):
+    return np.ascontiguousarray(x, dtype=dtype) if isinstance(x, np.ndarray) else x
+
+
+def lv_batch_create(n_graphs: int, gptr, rowptr, col, w, stream: int = 0) -> int:
+    """Handle of a batch: the disjoint union CSR (union vertex ids) and the
+    int64 graph starts ``gptr``; numpy (host) or CUDA tensors, all alike."""
+    ptrs = [_ptr(_arr(gptr, np.int64)), _ptr(_arr(rowptr, np.int64)), _ptr(_arr(col, np.int32)),
+            _ptr(_arr(w, np.int32))]
+    if len({d for _, d in ptrs}) != 1:
+        raise ValueError("gptr, rowptr, col and w must all be host or all be device arrays")
+    h = ctypes.c_void_p()
+    _check(load().lv_batch_create(ctypes.byref(h), int(n_graphs), *[p for p, _ in ptrs],
+                                  int(ptrs[0][1]), stream or None), "lv_batch_create")
+    return h.value
+
+
+def lv_batch_run(h: int, params: lv_params | None = None):
+    _check(load().lv_batch_run(h, ctypes.byref(params) if params is not None else None),
+           "lv_batch_run")
+
+
+def lv_batch_num_graphs(h: int) -> int:
+    out = ctypes.c_int32()
+    _check(load().lv_batch_num_graphs(h, ctypes.byref(out)), "lv_batch_num_graphs")
+    return out.value
+
+
+def lv_batch_get_labels(h: int, graph: int, phase: int, out) -> None:
+    p, dev = _ptr(out)
+    _check(load().lv_batch_get_labels(h, graph, phase, p, int(dev)), "lv_batch_get_labels")
+
+
+def lv_batch_get_graph_info(h: int, graph: int) -> lv_batch_graph_info:
+    out = lv_batch_graph_info()
+    _check(load().lv_batch_get_graph_info(h, graph, ctypes.byref(out)), "lv_batch_get_graph_info")
+    return out
+
+
+def lv_batch_get_phase_info(h: int, graph: int, phase: int) -> lv_phase_info:
+    out = lv_phase_info()
+    _check(load().lv_batch_get_phase_info(h, graph, phase, ctypes.byref(out)),
+           "lv_batch_get_phase_info")
+    return out
+
+
+def lv_batch_get_stats(h: int) -> lv_stats:
+    out = lv_stats()
+    _check(load().lv_batch_get_stats(h, ctypes.byref(out)), "lv_batch_get_stats")
+    return out
+
+
+def lv_batch_destroy(h: int) -> None:
+    if h:
+        load().lv_batch_destroy(h)
 
 
 # ------------------------------------------------------- convenience layer
