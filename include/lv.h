@@ -245,6 +245,19 @@ typedef struct {
     int32_t iterations; /* iterations over all its phases */
 } lv_batch_graph_info;
 
+/* Record of one batched sweep (one persistent launch over the graphs still
+ * iterating in the phase). */
+typedef struct {
+    int32_t phase;
+    int32_t sweep;      /* 1-based within the phase */
+    int32_t graphs;     /* graphs swept */
+    int32_t reserved;
+    int64_t vertices;   /* vertices of the swept graphs */
+    int64_t arcs;       /* arcs of the swept graphs */
+    int64_t moved;      /* moves proposed */
+    double ms;          /* CUDA-event time of the sweep (collect_timing), else -1 */
+} lv_batch_sweep;
+
 /* Create a batch: the disjoint union of n_graphs graphs as ONE CSR whose
  * vertices are numbered graph after graph.
  *   n_graphs  >= 1
@@ -290,6 +303,10 @@ lv_status lv_batch_get_phase_info(const lv_batch *b, int32_t graph, int32_t phas
  * vf_n = vertices of the union after vertex following; sweep_launches =
  * batched sweeps; times (collect_timing) and kernel launches of the run. */
 lv_status lv_batch_get_stats(const lv_batch *b, lv_stats *out);
+
+/* Batched sweep records of the last run: count, then copy up to `count`. */
+lv_status lv_batch_get_num_sweeps(const lv_batch *b, int64_t *count);
+lv_status lv_batch_get_sweeps(const lv_batch *b, lv_batch_sweep *out, int64_t count);
 
 /* Release the batch and its device memory (NULL is a no-op). */
 void lv_batch_destroy(lv_batch *b);

@@ -128,6 +128,34 @@ __global__ void localize_kernel(int32_t n, const int32_t *__restrict__ gid,
         labels[v] -= gstart[gid[v]];
 }
 
+// Compaction of the group bins (degree bins 0..5, positions [lo, hi) of
+// the bucketed order): vertices of graphs that stopped iterating are dropped,
+// so later sweeps of a phase hand out items over live vertices only.  The
+// kept vertices are packed at the END of [lo, hi) (CTA-bin and hub positions
+// after hi keep their places and their per-position hub arrays).
+__global__ void keep_flags_kernel(const int32_t *__restrict__ order, int lo, int hi,
+                                  const int32_t *__restrict__ gid,
+                                  const uint8_t *__restrict__ active, int32_t *flag) {
+    for (int p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x)
+        flag[p - lo] = active[gid[order[p]]] ? 1 : 0;
+}
+
+__global__ void compact_kernel(const int32_t *__restrict__ order, int lo, int hi,
+                               const int32_t *__restrict__ pos, int32_t *out) {
+    const int base = hi - pos[hi - lo];
+    for (int p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x)
+        if (pos[p - lo + 1] != pos[p - lo]) out[base + pos[p - lo]] = order[p];
+}
+
+// bucket offsets of the compacted list (class 0): group-bin starts move,
+// the rest is copied
+__global__ void compact_offsets_kernel(const int32_t *__restrict__ bo, const int32_t *__restrict__ pos,
+                                       int32_t *bo_c) {
+    const int t = threadIdx.x;
+    const int lo = bo[0], hi = bo[kBinCta];
+    if (t <= kBins) bo_c[t] = t <= kBinCta ? hi - pos[hi - lo] + pos[bo[t] - lo] : bo[t];
+}
+
 int grid_n(int64_t items) { return grid_for(items, 256, g_num_sms * 16); }
 
 }  // namespace
@@ -156,6 +184,7 @@ struct lv_batch {
     bool have_run = false;
     std::vector<int32_t *> labels;   // per batch phase: device int32[n], local ids
     std::vector<std::vector<lv_phase_info>> info;  // per graph, per phase
+    std::vector<lv_batch_sweep> sweeps;
     lv_stats stats;
     Timer timer;
 
@@ -163,6 +192,7 @@ struct lv_batch {
         for (auto p : labels) dfree(p, stream);
         labels.clear();
         info.clear();
+        sweeps.clear();
         std::memset(&stats, 0, sizeof stats);
         timer.clear();
         have_run = false;
@@ -367,7 +397,11 @@ struct RunBufs {
     PhaseState ps;
     Buckets b;
     bool have_b = false;
+    int32_t *order_c = nullptr, *bo_c = nullptr, *pos = nullptr;  // compacted vertex list
     ~RunBufs() {
+        dfree(order_c, s);
+        dfree(bo_c, s);
+        dfree(pos, s);
         if (own_g) free_graph(g, s);
         dfree(k, s);
         dfree(loop, s);
@@ -466,6 +500,9 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
     LV_TRY(dalloc_n(&ps.moves[0], (size_t)nmax, s));
     LV_TRY(dalloc_n(&ps.stats, 1, s));
     LV_TRY(dalloc_n(&r.newid, (size_t)nmax + 1, s));
+    LV_TRY(dalloc_n(&r.order_c, (size_t)nmax, s));
+    LV_TRY(dalloc_n(&r.bo_c, (size_t)kBins + 2, s));
+    LV_TRY(dalloc_n(&r.pos, (size_t)nmax + 1, s));
     LV_TRY(dalloc_n(&ps.act, 1, s));
     LV_TRY(dalloc_n(&ps.move_count, 4, s));
     LV_CUDA(cudaMemsetAsync(ps.act, 0, sizeof(int32_t), s));
@@ -485,6 +522,7 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
     double ms_iter = 0.0, ms_rebuild = 0.0;
     const size_t gsum_bytes = sizeof(unsigned long long) * 3 * (size_t)G;
     std::vector<int> ev_iter, ev_reb;  // event index pairs per phase
+    std::vector<int> ev_sweep;         // event index pairs per sweep
 
     for (int32_t p = 0; p < P.max_phases; ++p) {
         const int32_t *gptr = r.gbuf[cur];
@@ -530,11 +568,29 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
                 gs[g].N_start = h->two_m[g] * (int64_t)h->pin_u64[g] - (int64_t)h->pin_u64[G + g];
 
         // ---- batched iterations (Alg. 1 per graph, fused modularity)
+        int32_t sweep_no = 0;
+        Buckets bl = r.b;  // the vertex list the sweeps walk (compacted as graphs stop)
+        const int glo = r.b.host_off[0], ghi = r.b.host_off[kBinCta];
+        int64_t listed = 0;  // vertices of the graphs in the list
+        for (int32_t g = 0; g < G; ++g)
+            if (gs[g].running) listed += gp[g + 1] - gp[g];
         while (n_running > 0) {
+            lv_batch_sweep rec;
+            std::memset(&rec, 0, sizeof rec);
+            rec.phase = p;
+            rec.sweep = ++sweep_no;
+            rec.graphs = n_running;
+            for (int32_t g = 0; g < G; ++g)
+                if (gs[g].running) {
+                    rec.vertices += gp[g + 1] - gp[g];
+                    rec.arcs += garcs[g];
+                }
             LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
             LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s));
             LV_CUDA(cudaMemsetAsync(r.gsum, 0, gsum_bytes, s));
-            LV_TRY(sweep_iteration(ps, r.b, s));
+            ev_sweep.push_back(h->timer.mark());
+            LV_TRY(sweep_iteration(ps, bl, s));
+            ev_sweep.push_back(h->timer.mark());
             ++h->stats.sweep_launches;
             LV_CUDA(cudaMemcpyAsync(h->pin_stats, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, s));
             LV_CUDA(cudaMemcpyAsync(h->pin_u64, r.gsum, gsum_bytes, cudaMemcpyDeviceToHost, s));
@@ -549,6 +605,7 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
                 const int64_t N_prev =
                     h->two_m[g] * (int64_t)h->pin_u64[g] - (int64_t)h->pin_u64[G + g];
                 const int64_t moved = (int64_t)h->pin_u64[2 * (size_t)G + g];
+                rec.moved += moved;
                 bool fin = false;
                 if (step == 1) {
                     if (moved == 0) {
@@ -576,12 +633,40 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
                     --n_running;
                 }
             }
+            h->sweeps.push_back(rec);
             if (n_running > 0) {
                 // graphs that go on apply their moves and are swept again
                 LV_CUDA(cudaMemcpyAsync(r.flags, h->pin_flags, (size_t)G, cudaMemcpyHostToDevice, s));
                 apply_batch_kernel<<<g_num_sms * 4, 256, 0, s>>>(ps.C, ps.comm[0], ps.moves[0],
                                                                   ps.move_count, gid, r.flags);
                 LV_LAUNCH_CHECK();
+                int64_t live_v = 0;
+                for (int32_t g = 0; g < G; ++g)
+                    if (gs[g].running) live_v += gp[g + 1] - gp[g];
+                if (ghi > glo && live_v * 4 < listed * 3) {
+                    // drop stopped graphs from the group bins (from the full list)
+                    keep_flags_kernel<<<grid_n(ghi - glo), 256, 0, s>>>(r.b.order, glo, ghi, gid,
+                                                                         r.flags, r.pos);
+                    LV_LAUNCH_CHECK();
+                    LV_TRY(scan_excl_i32(r.pos, r.pos, ghi - glo, s));
+                    compact_kernel<<<grid_n(ghi - glo), 256, 0, s>>>(r.b.order, glo, ghi, r.pos,
+                                                                     r.order_c);
+                    LV_LAUNCH_CHECK();
+                    if (bl.order != r.order_c) {  // first compaction: CTA, hub and skip bins
+                        const int tail = r.b.host_off[kBins + 1] - ghi;
+                        if (tail > 0)
+                            LV_CUDA(cudaMemcpyAsync(r.order_c + ghi, r.b.order + ghi,
+                                                    sizeof(int32_t) * (size_t)tail,
+                                                    cudaMemcpyDeviceToDevice, s));
+                        LV_CUDA(cudaMemcpyAsync(r.bo_c + kBins + 1, r.b.bucket_off + kBins + 1,
+                                                sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+                    }
+                    compact_offsets_kernel<<<1, 32, 0, s>>>(r.b.bucket_off, r.pos, r.bo_c);
+                    LV_LAUNCH_CHECK();
+                    bl.order = r.order_c;
+                    bl.bucket_off = r.bo_c;
+                    listed = live_v;
+                }
             }
         }
         const int ev_i1 = h->timer.mark();
@@ -674,6 +759,8 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
         ms_iter += h->timer.ms(ev_iter[q], ev_iter[q + 1]);
         ms_rebuild += h->timer.ms(ev_reb[q], ev_reb[q + 1]);
     }
+    for (size_t q = 0; q < h->sweeps.size(); ++q)
+        h->sweeps[q].ms = h->timer.ms(ev_sweep[2 * q], ev_sweep[2 * q + 1]);
     h->stats.ms_total = h->timer.ms(ev_run0, ev_run1);
     h->stats.ms_vf = h->timer.ms(ev_vf0, ev_vf1);
     h->stats.ms_color = h->timer.on ? 0.0 : -1.0;
@@ -753,6 +840,21 @@ lv_status lv_batch_get_phase_info(const lv_batch *b, int32_t graph, int32_t phas
     const int32_t q = phase == -1 ? (int32_t)ph.size() - 1 : phase;
     if (q < 0 || q >= (int32_t)ph.size()) return LV_ERR_STATE;
     *out = ph[q];
+    return LV_OK;
+}
+
+lv_status lv_batch_get_num_sweeps(const lv_batch *b, int64_t *count) {
+    if (!b || !count) return LV_ERR_ARG;
+    if (!b->have_run) return LV_ERR_STATE;
+    *count = (int64_t)b->sweeps.size();
+    return LV_OK;
+}
+
+lv_status lv_batch_get_sweeps(const lv_batch *b, lv_batch_sweep *out, int64_t count) {
+    if (!b || (!out && count > 0) || count < 0) return LV_ERR_ARG;
+    if (!b->have_run) return LV_ERR_STATE;
+    const size_t c = std::min((size_t)count, b->sweeps.size());
+    if (c) std::memcpy(out, b->sweeps.data(), c * sizeof(lv_batch_sweep));
     return LV_OK;
 }
 

@@ -650,17 +650,20 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
                 item_end[gb] = acc_items;
             }
         }
+        // items are claimed `claim` at a time (about 8 claims per warp), so
+        // the class counter sees few atomics even with millions of items
         int32_t *wctr = s.move_count + 2 * s.n_act + q;
+        const int claim = max(1, item_end[0] / (gridDim.x * kSwWarps * 8));
         int it = 0;
         if (item_end[0] > 0) {
-            if (lane == 0) it = atomicAdd(wctr, 1);
+            if (lane == 0) it = atomicAdd(wctr, claim);
             it = __shfl_sync(0xffffffffu, it, 0);
-        } else {
-            it = 0;
         }
         while (it < item_end[0]) {
-            int nxt = 0;
-            if (lane == 0) nxt = atomicAdd(wctr, 1);
+          int nxt = 0;
+          if (lane == 0) nxt = atomicAdd(wctr, claim);
+          const int it_stop = min(it + claim, item_end[0]);
+          for (; it < it_stop; ++it) {
             int gb = kGroupBins - 1;
             while (it >= item_end[gb]) --gb;
             const int first = gb == kGroupBins - 1 ? 0 : item_end[gb + 1];
@@ -681,7 +684,8 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             if (lane == 0 && blockIdx.x < 16)
                 trace4(s.tb, 0x800000000ull | (unsigned)gb, (unsigned long long)g, 0, gtimer() - tw0);
 #endif
-            it = __shfl_sync(0xffffffffu, nxt, 0);
+          }
+          it = __shfl_sync(0xffffffffu, nxt, 0);
         }
 #ifdef LV_TRACE
         __syncthreads();

@@ -74,6 +74,12 @@ class lv_batch_graph_info(ctypes.Structure):
                 ("num_phases", ctypes.c_int32), ("iterations", ctypes.c_int32)]
 
 
+class lv_batch_sweep(ctypes.Structure):
+    _fields_ = [("phase", ctypes.c_int32), ("sweep", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("vertices", ctypes.c_int64),
+                ("arcs", ctypes.c_int64), ("moved", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
 _lib = None
 
 # every function declared in include/lv.h, with its ctypes signature
@@ -111,6 +117,8 @@ SIGNATURES = {
     "lv_batch_get_phase_info": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32,
                                                _P(lv_phase_info)]),
     "lv_batch_get_stats": (ctypes.c_int, [_vp, _P(lv_stats)]),
+    "lv_batch_get_num_sweeps": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
+    "lv_batch_get_sweeps": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "lv_batch_destroy": (None, [_vp]),
 }
 
@@ -327,6 +335,15 @@ def lv_batch_get_stats(h: int) -> lv_stats:
     out = lv_stats()
     _check(load().lv_batch_get_stats(h, ctypes.byref(out)), "lv_batch_get_stats")
     return out
+
+
+def lv_batch_get_sweeps(h: int) -> list:
+    L = load()
+    cnt = ctypes.c_int64()
+    _check(L.lv_batch_get_num_sweeps(h, ctypes.byref(cnt)), "lv_batch_get_num_sweeps")
+    arr = (lv_batch_sweep * max(cnt.value, 1))()
+    _check(L.lv_batch_get_sweeps(h, arr, cnt.value), "lv_batch_get_sweeps")
+    return list(arr[:cnt.value])
 
 
 def lv_batch_destroy(h: int) -> None:
