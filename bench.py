@@ -228,8 +228,8 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize(dev)
     h = lv.lv_batch_create(b.num_graphs, *dt, stream=cs)
-    params = lv.make_params(**BATCH_PARAMS, collect_timing=1)
-    for _ in range(args.warmup):
+    params = lv.make_params(**BATCH_PARAMS, autotune=1, collect_timing=1)
+    for _ in range(args.warmup):  # the first run also measures the bins of each phase
         lv.lv_batch_run(h, params)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
@@ -344,6 +344,7 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
                    "params": BATCH_PARAMS, "parallelism": f"replicas x{world}",
                    "l2": "input larger than L2 and a 256 MB L2 flush before every step",
                    "phases_max": st.num_phases, "batched_sweeps": st.sweep_launches,
+                   "sweeps_from_cuda_graph": st.graph_launches,
                    "iterations_all_graphs": st.total_iterations,
                    "edge_visits_per_step": st.edge_visits,
                    "q_min": min(qs), "q_median": statistics.median(qs)},

@@ -73,6 +73,16 @@ typedef struct {
     int32_t bin_lane_arcs;    /* 1..8, default 4 */
     int32_t bin_warp_max;     /* 1..256, default 128 */
     int32_t bin_cta_max;      /* bin_warp_max+1 .. 4096, default 4096 */
+    /* 0/1: choose the bins of each uncoloured phase with >= 2^22 arcs by
+     * timing one sweep per candidate set (the sweep of an uncoloured phase
+     * changes no community state, so results do not change).  The choice is
+     * kept per phase index in the handle and reused by later runs; the bin_*
+     * fields then only seed the first candidate. */
+    int32_t autotune;
+    /* 0/1: batched runs replay each phase's sweep launch (with the clearing
+     * of its counters) from a captured CUDA graph; default 1.  Ignored on the
+     * legacy default stream (NULL), which cannot be captured. */
+    int32_t graph_capture;
     int32_t reserved;
 } lv_params;
 
@@ -119,11 +129,13 @@ typedef struct {
     double ms_color;
     double ms_iterate;
     double ms_rebuild;
-    int64_t kernel_launches; /* CUDA kernels this run launched */
+    int64_t kernel_launches; /* CUDA kernels this run launched (a graph replay counts 1) */
+    int64_t graph_launches;  /* CUDA graph replays among them */
 } lv_stats;
 
 /* Fill *p with the defaults of Sec. 5.1: VF on, colouring on, theta_low 1e-6,
- * theta_high 1e-2, cutoff 100,000 vertices, max_iters 10,000, max_phases 64. */
+ * theta_high 1e-2, cutoff 100,000 vertices, max_iters 10,000, max_phases 64;
+ * default bins, no autotuning, graph capture on. */
 void lv_params_default(lv_params *p);
 
 /* Create a handle from a symmetric CSR with integer weights (Sec. 2: an

@@ -68,6 +68,9 @@ struct lv_graph {
     lv_stats stats;
     int32_t *vf_map = nullptr;
     Timer timer;
+    // bins chosen by measurement per phase index (autotune), kept across runs
+    std::vector<BinLimits> tuned;
+    std::vector<char> tuned_ok;
 
     void clear_results() {
         for (auto &p : phases) {
@@ -96,6 +99,7 @@ void lv_params_default(lv_params *p) {
     p->max_iters = 10000;
     p->max_phases = 64;
     p->color_seed = 0x5EED;
+    p->graph_capture = 1;
 }
 
 const char *lv_status_string(lv_status s) {
@@ -413,8 +417,40 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
             LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, color, &K, &rounds, h->pinned, s));
         info.color_rounds = rounds;
         info.num_colors = colour_on ? K : 0;
+        BinLimits plim = lim;
+        if (P.autotune && !colour_on && (int64_t)G.A >= kTuneMinArcs) {
+            if ((int32_t)h->tuned.size() <= p || !h->tuned_ok[p]) {
+                // time candidate bins on the phase's initial state (a scratch
+                // phase state over the run's buffers; the phase starts afresh)
+                PhaseState tp = ps;
+                tp.g = G;
+                tp.k = k;
+                tp.loop = loop;
+                tp.coloured = false;
+                tp.n_act = 1;
+                tp.act = nullptr;
+                tp.move_count = nullptr;
+                BinLimits best = lim;
+                lv_status ts = dalloc_n(&tp.act, 1, s);
+                if (ts == LV_OK) ts = dalloc_n(&tp.move_count, 4, s);
+                if (ts == LV_OK && cudaMemsetAsync(tp.act, 0, sizeof(int32_t), s) != cudaSuccess)
+                    ts = LV_ERR_CUDA;
+                if (ts == LV_OK) ts = init_phase(tp, s);
+                if (ts == LV_OK) ts = tune_bins(tp, lim, nullptr, 0, &best, h->pinned, s);
+                dfree(tp.act, s);
+                dfree(tp.move_count, s);
+                LV_TRY(ts);
+                if ((int32_t)h->tuned.size() <= p) {
+                    h->tuned.resize(p + 1);
+                    h->tuned_ok.resize(p + 1, 0);
+                }
+                h->tuned[p] = best;
+                h->tuned_ok[p] = 1;
+            }
+            plim = h->tuned[p];
+        }
         Buckets b;
-        LV_TRY(bucket_vertices(G, colour_on ? color : nullptr, K, lim, &b, h->pinned, s));
+        LV_TRY(bucket_vertices(G, colour_on ? color : nullptr, K, plim, &b, h->pinned, s));
         const int ev_c1 = h->timer.mark();
         if (P.keep_graphs) {
             LV_TRY(copy_graph(G, &rec.graph, s));

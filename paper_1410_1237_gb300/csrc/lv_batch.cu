@@ -185,6 +185,9 @@ struct lv_batch {
     std::vector<int32_t *> labels;   // per batch phase: device int32[n], local ids
     std::vector<std::vector<lv_phase_info>> info;  // per graph, per phase
     std::vector<lv_batch_sweep> sweeps;
+    // bins chosen by measurement per phase index (autotune), kept across runs
+    std::vector<BinLimits> tuned;
+    std::vector<char> tuned_ok;
     lv_stats stats;
     Timer timer;
 
@@ -382,6 +385,24 @@ struct GState {
     int32_t iters = 0;
 };
 
+// The fixed part of a batched iteration (clearing the counters and the
+// persistent sweep launch) as an instantiated CUDA graph: captured at the
+// first sweep of a phase and again when the vertex list moves to the
+// compacted buffer, replayed by every other iteration.  If the capture is
+// refused the iterations are issued directly.
+struct SweepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const int32_t *order = nullptr, *bo = nullptr;
+    bool disabled = false;
+    int captures = 0;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        order = bo = nullptr;
+    }
+    ~SweepGraph() { reset(); }
+};
+
 // device buffers of one run, released on every exit path
 struct RunBufs {
     cudaStream_t s = nullptr;
@@ -398,7 +419,9 @@ struct RunBufs {
     Buckets b;
     bool have_b = false;
     int32_t *order_c = nullptr, *bo_c = nullptr, *pos = nullptr;  // compacted vertex list
+    SweepGraph sg;
     ~RunBufs() {
+        sg.reset();
         dfree(order_c, s);
         dfree(bo_c, s);
         dfree(pos, s);
@@ -532,8 +555,6 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
         LV_LAUNCH_CHECK();
         LV_CUDA(cudaMemcpyAsync(h->pin_i32, r.tmp, sizeof(int32_t) * ((size_t)G + 1),
                                 cudaMemcpyDeviceToHost, s));
-        r.have_b = true;
-        LV_TRY(bucket_vertices(Gp, nullptr, 1, lim, &r.b, h->pinned, s));
         LV_CUDA(cudaStreamSynchronize(s));
         for (int32_t g = 0; g < G; ++g) garcs[g] = (int64_t)h->pin_i32[g + 1] - h->pin_i32[g];
 
@@ -567,7 +588,26 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
             if (gs[g].running)
                 gs[g].N_start = h->two_m[g] * (int64_t)h->pin_u64[g] - (int64_t)h->pin_u64[G + g];
 
+        // ---- degree bins (measured once per phase index when autotuning)
+        BinLimits plim = lim;
+        if (P.autotune && Gp.A >= kTuneMinArcs) {
+            if ((int32_t)h->tuned.size() <= p || !h->tuned_ok[p]) {
+                BinLimits best = lim;
+                LV_TRY(tune_bins(ps, lim, r.gsum, gsum_bytes, &best, h->pinned, s));
+                if ((int32_t)h->tuned.size() <= p) {
+                    h->tuned.resize(p + 1);
+                    h->tuned_ok.resize(p + 1, 0);
+                }
+                h->tuned[p] = best;
+                h->tuned_ok[p] = 1;
+            }
+            plim = h->tuned[p];
+        }
+        r.have_b = true;
+        LV_TRY(bucket_vertices(Gp, nullptr, 1, plim, &r.b, h->pinned, s));
+
         // ---- batched iterations (Alg. 1 per graph, fused modularity)
+        r.sg.reset();  // new phase graph: recapture
         int32_t sweep_no = 0;
         Buckets bl = r.b;  // the vertex list the sweeps walk (compacted as graphs stop)
         const int glo = r.b.host_off[0], ghi = r.b.host_off[kBinCta];
@@ -585,11 +625,45 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
                     rec.vertices += gp[g + 1] - gp[g];
                     rec.arcs += garcs[g];
                 }
-            LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-            LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s));
-            LV_CUDA(cudaMemsetAsync(r.gsum, 0, gsum_bytes, s));
+            auto enqueue = [&]() -> lv_status {
+                LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
+                LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s));
+                LV_CUDA(cudaMemsetAsync(r.gsum, 0, gsum_bytes, s));
+                return sweep_iteration(ps, bl, s);
+            };
+            SweepGraph &sg = r.sg;
+            if (P.graph_capture && !sg.disabled &&
+                (!sg.exec || sg.order != bl.order || sg.bo != bl.bucket_off)) {
+                sg.reset();
+                const unsigned long long l0 = g_kernel_launches;
+                cudaGraph_t graph = nullptr;
+                bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+                if (ok) {
+                    const lv_status est = enqueue();
+                    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                    ok = est == LV_OK && ce == cudaSuccess && graph &&
+                         cudaGraphInstantiate(&sg.exec, graph, 0) == cudaSuccess;
+                    if (graph) cudaGraphDestroy(graph);
+                }
+                g_kernel_launches = l0;
+                if (ok) {
+                    sg.order = bl.order;
+                    sg.bo = bl.bucket_off;
+                    ++sg.captures;
+                } else {
+                    cudaGetLastError();
+                    sg.reset();
+                    sg.disabled = true;
+                }
+            }
             ev_sweep.push_back(h->timer.mark());
-            LV_TRY(sweep_iteration(ps, bl, s));
+            if (sg.exec) {
+                LV_CUDA(cudaGraphLaunch(sg.exec, s));
+                ++g_kernel_launches;
+                ++h->stats.graph_launches;
+            } else {
+                LV_TRY(enqueue());
+            }
             ev_sweep.push_back(h->timer.mark());
             ++h->stats.sweep_launches;
             LV_CUDA(cudaMemcpyAsync(h->pin_stats, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, s));

@@ -109,6 +109,15 @@ lv_status apply_moves(PhaseState &ps, cudaStream_t s);
 unsigned long long *current_comm(const PhaseState &ps);
 size_t hub_part_bytes();
 
+// lv_tune.cu -------------------------------------------------------------
+// Time one sweep of the (uncoloured) phase state per candidate bin set and
+// return the fastest in *best; `first` is tried first.  `zero` (may be null)
+// is cleared before each sweep with the statistics.  Leaves ps's community
+// state untouched; its move list and statistics hold the last candidate's.
+lv_status tune_bins(PhaseState &ps, const BinLimits &first, void *zero, size_t zero_bytes,
+                    BinLimits *best, int *pinned, cudaStream_t s);
+constexpr int64_t kTuneMinArcs = int64_t(1) << 22;  // phases smaller than this keep their bins
+
 // lv_rebuild.cu ----------------------------------------------------------
 // newid[c] = rank of c among non-empty communities (n+1 entries, newid[n] = count)
 lv_status renumber(int32_t n, const unsigned long long *comm, int32_t *newid, cudaStream_t s);

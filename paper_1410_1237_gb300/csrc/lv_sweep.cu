@@ -843,10 +843,19 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.g_ein = ps.g_ein;
     a.g_a2 = ps.g_a2;
     a.g_moved = ps.g_moved;
-    void *args[] = {&a};
-    LV_CUDA(cudaLaunchCooperativeKernel((void *)sweep_persistent_kernel,
-                                        dim3(g_num_sms * g_sweep_blocks_per_sm), dim3(kSwBlock), args,
-                                        kSwSmemInts * sizeof(int), s));
+    // cooperative launch (all blocks co-resident, as the grid barrier needs);
+    // the launch-attribute form is also valid inside a stream capture
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_num_sms * g_sweep_blocks_per_sm);
+    cfg.blockDim = dim3(kSwBlock);
+    cfg.dynamicSmemBytes = kSwSmemInts * sizeof(int);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    LV_CUDA(cudaLaunchKernelEx(&cfg, sweep_persistent_kernel, a));
     LV_LAUNCH_CHECK();
     if (ps.coloured) ps.g_total += ps.n_act;
     return LV_OK;

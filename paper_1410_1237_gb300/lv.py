@@ -40,7 +40,8 @@ class lv_params(ctypes.Structure):
                 ("max_phases", ctypes.c_int32), ("color_seed", ctypes.c_uint64),
                 ("collect_timing", ctypes.c_int32), ("keep_graphs", ctypes.c_int32),
                 ("bin_lane_arcs", ctypes.c_int32), ("bin_warp_max", ctypes.c_int32),
-                ("bin_cta_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("bin_cta_max", ctypes.c_int32), ("autotune", ctypes.c_int32),
+                ("graph_capture", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class lv_phase_info(ctypes.Structure):
@@ -65,7 +66,7 @@ class lv_stats(ctypes.Structure):
                 ("sweep_launches", ctypes.c_int64), ("ms_total", ctypes.c_double),
                 ("ms_vf", ctypes.c_double), ("ms_color", ctypes.c_double),
                 ("ms_iterate", ctypes.c_double), ("ms_rebuild", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("graph_launches", ctypes.c_int64)]
 
 
 class lv_batch_graph_info(ctypes.Structure):

@@ -41,3 +41,36 @@ def test_status_strings_and_defaults_without_gpu():
 def test_built_for_sm103a_only():
     from paper_1410_1237_gb300 import _build
     assert "arch=compute_103a,code=sm_103a" in " ".join(_build.ARCH)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every struct of lv.h has the size and field offsets the binding uses
+    (the C compiler's view of the header against the ctypes declarations)."""
+    import shutil
+    import subprocess
+
+    from paper_1410_1237_gb300 import lv
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    structs = {"lv_params": lv.lv_params, "lv_phase_info": lv.lv_phase_info,
+               "lv_iter_stat": lv.lv_iter_stat, "lv_stats": lv.lv_stats,
+               "lv_batch_graph_info": lv.lv_batch_graph_info,
+               "lv_batch_sweep": lv.lv_batch_sweep}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lv.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

@@ -28,8 +28,8 @@ def lv():
     return lvmod
 
 
-def run_batch(lv, b, **params):
-    h = lv.lv_batch_create(b.num_graphs, b.gptr, b.rowptr, b.col, b.w)
+def run_batch(lv, b, stream=0, **params):
+    h = lv.lv_batch_create(b.num_graphs, b.gptr, b.rowptr, b.col, b.w, stream=stream)
     try:
         lv.lv_batch_run(h, lv.make_params(**params))
     except Exception:
@@ -248,3 +248,48 @@ def test_batch_errors(lv):
             lv.lv_batch_get_graph_info(h, 2)
     finally:
         lv.lv_batch_destroy(h)
+
+
+def test_autotune_and_graph_capture_keep_results(lv):
+    """Bins chosen by timing and sweeps replayed from a captured CUDA graph
+    change no result."""
+    import torch
+    b = gg.planted_batch(num_graphs=40, nmin=20_000, nmax=50_000, seed=12)
+    assert b.arcs >= 1 << 22  # large enough to be tuned
+    stream = torch.cuda.Stream()  # capture needs a stream other than the legacy default
+    runs = {}
+    for key, prm in {"plain": dict(autotune=0, graph_capture=0),
+                     "tuned": dict(autotune=1, graph_capture=1)}.items():
+        h = run_batch(lv, b, stream=stream.cuda_stream, **prm)
+        try:
+            if key == "tuned":
+                lv.lv_batch_run(h, lv.make_params(**prm))  # second run reuses the choice
+            lab = np.empty(b.n, dtype=np.int32)
+            lv.lv_batch_get_labels(h, -1, -1, lab)
+            st = lv.lv_batch_get_stats(h)
+            runs[key] = (lab, st.graph_launches, st.sweep_launches)
+            if key == "tuned":
+                for g in (0, 17, 39):
+                    check_graph(lv, h, b, g)
+        finally:
+            lv.lv_batch_destroy(h)
+    assert np.array_equal(runs["plain"][0], runs["tuned"][0])
+    assert runs["plain"][1] == 0
+    assert 0 < runs["tuned"][1] <= runs["tuned"][2]
+
+
+def test_autotune_single_graph(lv):
+    g = gg.rmat(18, 16, seed=5)
+    assert g.arcs >= 1 << 22
+    a = lv.run(g.rowptr, g.col, g.w, coloring=0)
+    h = lv.lv_graph_create(g.n, g.rowptr, g.col, g.w)
+    try:
+        for _ in range(2):
+            lv.lv_run(h, lv.make_params(coloring=0, autotune=1))
+            res = lv.collect(h, g.n)
+            assert len(res.phases) == len(a.phases)
+            for x, y in zip(res.phases, a.phases):
+                assert (x.N_end, x.iterations) == (y.N_end, y.iterations)
+                assert np.array_equal(x.labels, y.labels)
+    finally:
+        lv.lv_graph_destroy(h)
