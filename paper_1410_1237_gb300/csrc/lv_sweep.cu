@@ -422,8 +422,11 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 }
 
 // Hub arc chunk: inserts kHubChunk arcs of one hub into its global table,
-// merging equal labels within each warp first; a claimed slot is appended to
-// the hub's occupied list.
+// merging equal labels within each warp first.  Every lane's first probe is
+// a compare-and-swap issued for all its arcs at once (it claims an empty slot
+// or finds its own label in one round trip); collisions fall back to linear
+// probing.  Claimed slots are appended to the hub's occupied list with one
+// counter update per warp.
 __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
@@ -439,7 +442,8 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) 
     const int stop = min(end, start + kHubChunk);
     for (int b0 = start + w * 32; b0 < stop; b0 += kU * kSwBlock) {
         int2 ar[kU];
-        int cl[kU];
+        int cl[kU], sum[kU];
+        bool lead[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int e = b0 + u * kSwBlock + lane;
@@ -450,30 +454,53 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) 
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const bool valid = cl[u] != kEmpty;
+            const unsigned peers = __match_any_sync(0xffffffffu, valid ? cl[u] : -1 - lane);
+            sum[u] = __reduce_add_sync(peers, valid ? ar[u].y : 0);
+            lead[u] = valid && lane == __ffs(peers) - 1;
+        }
+        unsigned hslot[kU];
+        int prev[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            hslot[u] = hash32(cl[u]) & mask;
+            prev[u] = lead[u] ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
+        }
+        int claimed[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            claimed[u] = -1;
+            if (!lead[u]) continue;
             const int c = cl[u];
-            const unsigned peers = __match_any_sync(0xffffffffu, valid ? c : -1 - lane);
-            const int sum = __reduce_add_sync(peers, valid ? ar[u].y : 0);
-            if (valid && lane == __ffs(peers) - 1) {
-                unsigned h = hash32(c) & mask;
-                bool done = false;
-                for (unsigned probe = 0; probe <= mask && !done; ++probe) {
-                    int *kp = &tab[h].x;
-                    const int cur = *((volatile int *)kp);
-                    if (cur == c) {
-                        atomicAdd(&tab[h].y, sum);
-                        done = true;
-                    } else if (cur == kEmpty) {
-                        const int prev = atomicCAS(kp, kEmpty, c);
-                        if (prev == kEmpty) __stcg(&occ[atomicAdd(occ_cnt, 1)], (int)h);
-                        if (prev == kEmpty || prev == c) {
-                            atomicAdd(&tab[h].y, sum);
-                            done = true;
-                        }
-                    }
-                    h = (h + 1) & mask;
-                }
-                if (!done) acc.err = 1;
+            unsigned h = hslot[u];
+            bool done = prev[u] == kEmpty || prev[u] == c;
+            if (prev[u] == kEmpty) claimed[u] = (int)h;
+            for (unsigned probe = 1; probe <= mask && !done; ++probe) {
+                h = (h + 1) & mask;
+                const int pv = atomicCAS(&tab[h].x, kEmpty, c);
+                if (pv == kEmpty) claimed[u] = (int)h;
+                done = pv == kEmpty || pv == c;
             }
+            if (done) atomicAdd(&tab[h].y, sum[u]);
+            else acc.err = 1;
+        }
+        // one occupied-list reservation per warp for all its claims
+        int mine = 0;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) mine += claimed[u] >= 0 ? 1 : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total) {
+            int base = 0;
+            if (lane == 31) base = atomicAdd(occ_cnt, total);
+            base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                if (claimed[u] >= 0) __stcg(&occ[base++], claimed[u]);
         }
     }
 }
@@ -539,23 +566,26 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
         s_last = (atomicAdd(&s.hub_done[p], 1) == nch - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
+    if (s_last) {  // block-uniform: the last block combines the partials in parallel
         __threadfence();
         Best t;
         best_init(t);
         int eo = 0;
-        for (int q = first; q < first + nch; ++q) {
+        for (int q = first + threadIdx.x; q < first + nch; q += kSwBlock) {
             const HubPart *hq = &s.hub_part[q];
             best_take(t, __ldcg(&hq->s), __ldcg(&hq->c), __ldcg(&hq->z), __ldcg(&hq->e));
             eo += __ldcg(&hq->eo);
         }
-        __stcg(&s.hub_cnt[p], 0);
-        __stcg(&s.hub_done[p], 0);
-        atomicMax(&s.stats->max_occ, n_occ);
-        int ein = 0;
-        const bool mv = decide(s, cc, i, ci, ki, tm, t, eo, acc, ein);
-        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
-        add_terms(s, acc, i, ein, mv);
+        block_best(t, eo, red);
+        if (threadIdx.x == 0) {
+            __stcg(&s.hub_cnt[p], 0);
+            __stcg(&s.hub_done[p], 0);
+            atomicMax(&s.stats->max_occ, n_occ);
+            int ein = 0;
+            const bool mv = decide(s, cc, i, ci, ki, tm, t, eo, acc, ein);
+            if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
+            add_terms(s, acc, i, ein, mv);
+        }
     }
     __syncthreads();
 }
