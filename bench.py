@@ -46,6 +46,34 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def init_dist(world: int, dev):
+    """One process per GPU (torchrun env); NCCL on GPUs, gloo on CPU.  Returns
+    the torch.distributed module, or None for a single process."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if dev.type == "cuda":
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist.init_process_group("gloo")
+    return dist
+
+
+def max_over_ranks(x: float, pg, dev) -> float:
+    """The largest x over all ranks (the slowest replica sets the job time)."""
+    if not pg:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / seconds_max
+
+
 def measured_peak_gbs():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -257,17 +285,14 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
                 nsweeps += 1
     torch.cuda.synchronize(dev)
     total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, pg, dev)
     clk = clocks.stop()
     st = lv.lv_batch_get_stats(h)
     batch_labels = np.empty(b.n, dtype=np.int32)
     lv.lv_batch_get_labels(h, -1, -1, batch_labels)
     qs = [lv.lv_batch_get_graph_info(h, g).q for g in range(b.num_graphs)]
     lv.lv_batch_destroy(h)
-    value = world * b.num_graphs * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(b.num_graphs * args.steps, world, total_ms / 1e3)
     peak, peak_src = measured_peak_gbs()
     achieved = (sweep_bytes / (sweep_ms / 1e3) / 1e9) if sweep_ms > 0 else None
 
@@ -325,11 +350,8 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
             if i >= max(1, args.warmup // 2):
                 times.append(t1 - t0)
         tt = sum(times)
-        if pg:
-            t = torch.tensor([tt], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tt = float(t.item())
-        e2e = {"value": world * b.num_graphs * len(times) / tt, "unit": BATCH_UNIT,
+        tt = max_over_ranks(tt, pg, dev)
+        e2e = {"value": whole_job_rate(b.num_graphs * len(times), world, tt), "unit": BATCH_UNIT,
                "h2d_bytes_per_step": int(sum(x.nbytes for x in (b.gptr, b.rowptr, b.col, b.w))),
                "d2h_bytes_per_step": int(4 * b.n), "s_per_step": tt / len(times)}
 
@@ -396,11 +418,7 @@ def main():
         return 2
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    pg = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-        pg = dist
+    pg = init_dist(world, dev)
     if rank == 0 or world > 1:
         _build.build()
     if pg:
@@ -456,17 +474,14 @@ def main():
                 sweeps += 1
     torch.cuda.synchronize(dev)
     total_ms = sum(step_ms)
-    if pg:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, pg, dev)
     clk = clocks.stop()
     q = lv.lv_get_modularity(h, -1)[0]
     phases = lv.lv_num_phases(h)
     stats = lv.lv_get_stats(h)
     lv.lv_graph_destroy(h)
 
-    value = world * visits * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(visits * args.steps, world, total_ms / 1e3)
     peak, peak_src = measured_peak_gbs()
     achieved = (sweep_bytes / (sweep_ms / 1e3) / 1e9) if sweep_ms > 0 else None
 
@@ -488,11 +503,8 @@ def main():
             if i >= args.warmup:
                 times.append(t1 - t0)
         tt = sum(times)
-        if pg:
-            t = torch.tensor([tt], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            tt = float(t.item())
-        e2e = {"value": world * visits * len(times) / tt, "unit": UNIT,
+        tt = max_over_ranks(tt, pg, dev)
+        e2e = {"value": whole_job_rate(visits * len(times), world, tt), "unit": UNIT,
                "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes + g.w.nbytes),
                "d2h_bytes_per_step": int(4 * g.n), "s_per_step": tt / len(times)}
 
