@@ -1,164 +1,18 @@
 // lv_batch.cu -- batched runs: many independent graphs behind one handle.
 //
-// The graphs are held as one disjoint union (vertices numbered graph after
-// graph, gid[v] = graph of v).  Vertex following, the sweep and the rebuild
-// never cross a graph boundary, so they run on the union unchanged; what is
-// per graph is the arithmetic of the gain (each graph's own 2m), the
-// modularity terms (summed per graph inside the sweep) and the control of
-// Algorithm 1 and Sec. 4.4 (iteration and phase stopping), which the host
-// replays per graph exactly as the single-graph driver does:
-//   - each batched sweep covers the vertices of graphs still iterating in
-//     the current phase; the sweep that proposes iteration t's moves also
-//     yields N(C^{t-1}) per graph (fused modularity), the host runs every
-//     graph's stopping test and applies the moves only of graphs that go on;
-//   - phases are taken in lock step: when no graph iterates any more, one
-//     renumber / compose / coarsen pass serves all graphs.  A graph whose
-//     phase loop has stopped rides along with the identity partition (its
-//     coarse graph is rebuilt from its final communities and never swept),
-//     so its labels do not change any more.
-// Renumbering ranks communities by id, so graphs stay contiguous and ordered
-// in every coarse union and local ids are union ids minus the graph's start.
+// A batch validates the disjoint union of its graphs once (lv_batch_create);
+// each run hands the union to the multi-graph engine (lv_engine.cu), which
+// takes every graph through its own phases with batched sweeps, and records
+// per graph what lv_run records for it alone.  Graphs leave the engine when
+// their phase loop stops, so later phases sweep and rebuild only the graphs
+// still running.
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
-#include "lv_ops.cuh"
+#include "lv_engine.cuh"
 
 using namespace lv;
-
-namespace {
-
-// gid[v] = g with gptr[g] <= v < gptr[g+1] (gptr strictly increasing)
-__global__ void graph_of_kernel(int32_t n, int32_t G, const int32_t *__restrict__ gptr,
-                                int32_t *gid) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int a = 0, b = G;  // gptr[a] <= v < gptr[b]
-        while (b - a > 1) {
-            const int mid = (a + b) >> 1;
-            if (gptr[mid] <= v) a = mid; else b = mid;
-        }
-        gid[v] = a;
-    }
-}
-
-// every arc of row i must stay inside graph gid[i]; one warp per row
-__global__ void __launch_bounds__(256) cross_check_kernel(DGraph g, const int32_t *__restrict__ gid,
-                                                          const int32_t *__restrict__ gptr,
-                                                          int *bad) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * 8;
-    for (int i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
-        const int gi = gid[i];
-        const int lo = gptr[gi], hi = gptr[gi + 1];
-        bool ok = true;
-        for (int e = g.off[i] + lane; e < g.off[i + 1]; e += 32) {
-            const int c = g.arcs[e].x;
-            ok = ok && c >= lo && c < hi;
-        }
-        if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(bad, 1);
-    }
-}
-
-// Per-graph sums over vertices of graphs with active[g] != 0 (all graphs
-// when active is null): sum_k (2m), sum_loop and sum_k2.  Any output may be
-// null.  Vertices of a graph are consecutive, so whole warps form runs.
-__global__ void __launch_bounds__(256) graph_sums_kernel(int32_t n, const int32_t *__restrict__ gid,
-                                                         const int32_t *__restrict__ k,
-                                                         const int32_t *__restrict__ loop,
-                                                         const uint8_t *__restrict__ active,
-                                                         unsigned long long *sum_k,
-                                                         unsigned long long *sum_loop,
-                                                         unsigned long long *sum_k2) {
-    const int nr = (n + 31) & ~31;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nr; v += gridDim.x * blockDim.x) {
-        const bool in = v < n;
-        const int g = in ? gid[v] : 0;
-        const bool on = in && (!active || active[g]);
-        const long long kv = on ? k[v] : 0;
-        const long long lv = on ? loop[v] : 0;
-        if (sum_k) warp_run_add(g, (unsigned long long)kv, on, sum_k);
-        if (sum_loop) warp_run_add(g, (unsigned long long)lv, on, sum_loop);
-        if (sum_k2) warp_run_add(g, (unsigned long long)(kv * kv), on, sum_k2);
-    }
-}
-
-// gid_new[to[v]] = gid[v], to[v] = idx[C[v]] (or idx[v] when C is null);
-// all writers of one target write the same graph
-__global__ void gid_scatter_kernel(int32_t n, const int32_t *__restrict__ gid,
-                                   const int32_t *__restrict__ C, const int32_t *__restrict__ idx,
-                                   int32_t *gid_new) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        gid_new[idx[C ? C[v] : v]] = gid[v];
-}
-
-// gptr from a non-decreasing gid: gptr[g] = first vertex of g, gptr[G] = n
-__global__ void gptr_kernel(int32_t n, int32_t G, const int32_t *__restrict__ gid, int32_t *gptr) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        if (v == 0 || gid[v] != gid[v - 1]) gptr[gid[v]] = v;
-        if (v == 0) gptr[G] = n;
-    }
-}
-
-// out[g] = arr[gptr[g]] for g <= G (arc offsets, or new ids, at graph starts)
-__global__ void gather_at_kernel(int32_t G, const int32_t *__restrict__ gptr,
-                                 const int32_t *__restrict__ arr, int32_t *out) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x)
-        out[g] = arr[gptr[g]];
-}
-
-// apply the listed moves of graphs whose apply flag is set
-__global__ void apply_batch_kernel(int32_t *C, unsigned long long *comm,
-                                   const int4 *__restrict__ moves, const int32_t *__restrict__ count,
-                                   const int32_t *__restrict__ gid,
-                                   const uint8_t *__restrict__ apply) {
-    const int cnt = *count;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
-        const int4 m = moves[t];
-        if (!apply[gid[m.x]]) continue;
-        C[m.x] = m.z;
-        atomicAdd(&comm[m.y], comm_leave(m.w));
-        atomicAdd(&comm[m.z], comm_join(m.w));
-    }
-}
-
-// union labels -> labels local to each graph
-__global__ void localize_kernel(int32_t n, const int32_t *__restrict__ gid,
-                                const int32_t *__restrict__ gstart, int32_t *labels) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
-        labels[v] -= gstart[gid[v]];
-}
-
-// Compaction of the group bins (degree bins 0..5, positions [lo, hi) of
-// the bucketed order): vertices of graphs that stopped iterating are dropped,
-// so later sweeps of a phase hand out items over live vertices only.  The
-// kept vertices are packed at the END of [lo, hi) (CTA-bin and hub positions
-// after hi keep their places and their per-position hub arrays).
-__global__ void keep_flags_kernel(const int32_t *__restrict__ order, int lo, int hi,
-                                  const int32_t *__restrict__ gid,
-                                  const uint8_t *__restrict__ active, int32_t *flag) {
-    for (int p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x)
-        flag[p - lo] = active[gid[order[p]]] ? 1 : 0;
-}
-
-__global__ void compact_kernel(const int32_t *__restrict__ order, int lo, int hi,
-                               const int32_t *__restrict__ pos, int32_t *out) {
-    const int base = hi - pos[hi - lo];
-    for (int p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x)
-        if (pos[p - lo + 1] != pos[p - lo]) out[base + pos[p - lo]] = order[p];
-}
-
-// bucket offsets of the compacted list (class 0): group-bin starts move,
-// the rest is copied
-__global__ void compact_offsets_kernel(const int32_t *__restrict__ bo, const int32_t *__restrict__ pos,
-                                       int32_t *bo_c) {
-    const int t = threadIdx.x;
-    const int lo = bo[0], hi = bo[kBinCta];
-    if (t <= kBins) bo_c[t] = t <= kBinCta ? hi - pos[hi - lo] + pos[bo[t] - lo] : bo[t];
-}
-
-int grid_n(int64_t items) { return grid_for(items, 256, g_num_sms * 16); }
-
-}  // namespace
 
 struct lv_batch {
     int device = 0;
@@ -231,8 +85,7 @@ lv_status batch_setup(lv_batch *b) {
     LV_TRY(dalloc_n(&b->two_m_dev, (size_t)G, s));
     LV_CUDA(cudaMemcpyAsync(b->gptr_in, b->gptr.data(), sizeof(int32_t) * ((size_t)G + 1),
                             cudaMemcpyHostToDevice, s));
-    graph_of_kernel<<<grid_n(b->n), 256, 0, s>>>((int32_t)b->n, G, b->gptr_in, b->gid_in);
-    LV_LAUNCH_CHECK();
+    LV_TRY(graph_of((int32_t)b->n, G, b->gptr_in, b->gid_in, s));
     int *bad = nullptr;
     unsigned long long *sk = nullptr;
     int32_t *starts = nullptr;
@@ -241,14 +94,9 @@ lv_status batch_setup(lv_batch *b) {
     LV_TRY(dalloc_n(&starts, (size_t)G + 1, s));
     LV_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
     LV_CUDA(cudaMemsetAsync(sk, 0, sizeof(unsigned long long) * G, s));
-    cross_check_kernel<<<grid_for(b->n, 8, g_num_sms * 16), 256, 0, s>>>(b->in, b->gid_in,
-                                                                          b->gptr_in, bad);
-    LV_LAUNCH_CHECK();
-    graph_sums_kernel<<<grid_n(b->n), 256, 0, s>>>((int32_t)b->n, b->gid_in, b->k_in, b->loop_in,
-                                                   nullptr, sk, nullptr, nullptr);
-    LV_LAUNCH_CHECK();
-    gather_at_kernel<<<grid_n(G + 1), 256, 0, s>>>(G, b->gptr_in, b->in.off, starts);
-    LV_LAUNCH_CHECK();
+    LV_TRY(cross_check(b->in, b->gid_in, b->gptr_in, bad, s));
+    LV_TRY(graph_sums((int32_t)b->n, b->gid_in, b->k_in, b->loop_in, nullptr, sk, nullptr, nullptr, s));
+    LV_TRY(gather_at(G, b->gptr_in, b->in.off, starts, s));
     LV_CUDA(cudaMemcpyAsync(b->pinned, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaMemcpyAsync(b->pin_u64, sk, sizeof(unsigned long long) * G, cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaMemcpyAsync(b->pin_i32, starts, sizeof(int32_t) * ((size_t)G + 1),
@@ -374,78 +222,6 @@ lv_status lv_batch_num_graphs(const lv_batch *b, int32_t *out) {
 
 namespace {
 
-// control state of one graph (the single-graph driver's locals, per graph)
-struct GState {
-    bool done = false;     // its phase loop has stopped
-    bool running = false;  // still iterating in the current phase
-    int step = 0;          // sweeps of the current phase
-    bool have_np = false;
-    int64_t n_p = 0;
-    int64_t N_start = 0, N_end = 0;
-    int32_t iters = 0;
-};
-
-// The fixed part of a batched iteration (clearing the counters and the
-// persistent sweep launch) as an instantiated CUDA graph: captured at the
-// first sweep of a phase and again when the vertex list moves to the
-// compacted buffer, replayed by every other iteration.  If the capture is
-// refused the iterations are issued directly.
-struct SweepGraph {
-    cudaGraphExec_t exec = nullptr;
-    const int32_t *order = nullptr, *bo = nullptr;
-    bool disabled = false;
-    int captures = 0;
-    void reset() {
-        if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        order = bo = nullptr;
-    }
-    ~SweepGraph() { reset(); }
-};
-
-// device buffers of one run, released on every exit path
-struct RunBufs {
-    cudaStream_t s = nullptr;
-    DGraph g;                  // current phase graph when owned
-    bool own_g = false;
-    int32_t *k = nullptr, *loop = nullptr, *gid = nullptr;  // owned per-phase arrays
-    int32_t *map = nullptr;    // original vertex -> vertex of the phase graph
-    int32_t *gbuf[2] = {nullptr, nullptr};  // graph starts: current / next
-    int32_t *tmp = nullptr;    // G+1 scratch
-    int32_t *newid = nullptr;
-    unsigned long long *gsum = nullptr;  // 3G per-graph sums
-    uint8_t *flags = nullptr;  // G: graph iterates (sweep) / applies its moves
-    PhaseState ps;
-    Buckets b;
-    bool have_b = false;
-    int32_t *order_c = nullptr, *bo_c = nullptr, *pos = nullptr;  // compacted vertex list
-    SweepGraph sg;
-    ~RunBufs() {
-        sg.reset();
-        dfree(order_c, s);
-        dfree(bo_c, s);
-        dfree(pos, s);
-        if (own_g) free_graph(g, s);
-        dfree(k, s);
-        dfree(loop, s);
-        dfree(gid, s);
-        dfree(map, s);
-        dfree(gbuf[0], s);
-        dfree(gbuf[1], s);
-        dfree(tmp, s);
-        dfree(newid, s);
-        dfree(gsum, s);
-        dfree(flags, s);
-        dfree(ps.C, s);
-        dfree(ps.comm[0], s);
-        dfree(ps.moves[0], s);
-        dfree(ps.stats, s);
-        dfree(ps.move_count, s);
-        dfree(ps.act, s);
-        if (have_b) free_buckets(b, s);
-    }
-};
-
 lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
     cudaStream_t s = h->stream;
     BinLimits lim;
@@ -460,381 +236,93 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
         return LV_ERR_ARG;
     const int32_t G = h->G;
     const int32_t n_orig = (int32_t)h->n;
-    const double theta = P.theta_low;  // batched phases are uncoloured
     h->timer.on = P.collect_timing != 0;
     const unsigned long long launches0 = g_kernel_launches;
     const int ev_run0 = h->timer.mark();
     h->info.assign(G, std::vector<lv_phase_info>());
 
-    RunBufs r;
-    r.s = s;
-    LV_TRY(dalloc_n(&r.map, (size_t)n_orig, s));
-    LV_TRY(dalloc_n(&r.gbuf[0], (size_t)G + 1, s));
-    LV_TRY(dalloc_n(&r.gbuf[1], (size_t)G + 1, s));
-    LV_TRY(dalloc_n(&r.tmp, (size_t)G + 1, s));
-    LV_TRY(dalloc_n(&r.gsum, 3 * (size_t)G, s));
-    LV_TRY(dalloc_n(&r.flags, (size_t)G, s));
-    int cur = 0;  // r.gbuf[cur] holds the graph starts of the phase graph
+    Engine e;
+    e.s = s;
+    e.P = P;
+    e.lim = lim;
+    e.pinned = h->pinned;
+    e.timer = &h->timer;
+    e.tuned = &h->tuned;
+    e.tuned_ok = &h->tuned_ok;
 
-    // ---- vertex following on the union (Sec. 4.3; never crosses graphs)
-    DGraph Gp = h->in;
-    const int32_t *k = h->k_in, *loop = h->loop_in, *gid = h->gid_in;
+    // ---- vertex following of every graph and the engine's union
     const int ev_vf0 = h->timer.mark();
-    if (P.vertex_following) {
-        DGraph G2;
-        LV_TRY(vertex_following(Gp, h->loop_in, &G2, r.map, h->pinned, s));
-        r.g = G2;
-        r.own_g = true;
-        Gp = G2;
-        LV_TRY(dalloc_n(&r.k, (size_t)Gp.n, s));
-        LV_TRY(dalloc_n(&r.loop, (size_t)Gp.n, s));
-        LV_TRY(compute_degrees(Gp, r.k, r.loop, s));
-        LV_TRY(dalloc_n(&r.gid, (size_t)Gp.n, s));
-        gid_scatter_kernel<<<grid_n(n_orig), 256, 0, s>>>(n_orig, h->gid_in, nullptr, r.map, r.gid);
-        LV_LAUNCH_CHECK();
-        LV_CUDA(cudaMemsetAsync(r.gbuf[0], 0xff, sizeof(int32_t) * ((size_t)G + 1), s));
-        gptr_kernel<<<grid_n(Gp.n), 256, 0, s>>>(Gp.n, G, r.gid, r.gbuf[0]);
-        LV_LAUNCH_CHECK();
-        k = r.k;
-        loop = r.loop;
-        gid = r.gid;
-    } else {
-        LV_TRY(iota(n_orig, r.map, s));
-        LV_CUDA(cudaMemcpyAsync(r.gbuf[0], h->gptr_in, sizeof(int32_t) * ((size_t)G + 1),
-                                cudaMemcpyDeviceToDevice, s));
-    }
+    NewGraphs ng;
+    ng.g = h->in;
+    ng.k = h->k_in;
+    ng.loop = h->loop_in;
+    ng.gptr = h->gptr;
+    ng.two_m = h->two_m;
+    ng.tags.resize(G);
+    for (int32_t q = 0; q < G; ++q) ng.tags[q] = q;
+    LV_TRY(e.append(ng));
     const int ev_vf1 = h->timer.mark();
-    h->stats.vf_n = Gp.n;
-    std::vector<int32_t> gp((size_t)G + 1);
-    LV_CUDA(cudaMemcpyAsync(h->pin_i32, r.gbuf[0], sizeof(int32_t) * ((size_t)G + 1),
-                            cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(gp.data(), h->pin_i32, sizeof(int32_t) * gp.size());
-    for (int32_t g = 0; g < G; ++g) {
-        if (gp[g] < 0 || gp[g + 1] <= gp[g]) return LV_ERR_CUDA;  // cannot happen: m_g > 0
-        if (P.coloring && (int64_t)(gp[g + 1] - gp[g]) >= P.color_cutoff) return LV_ERR_ARG;
-    }
+    h->stats.vf_n = e.g.n;
+    if (P.coloring)
+        for (int32_t q = 0; q < G; ++q)
+            if ((int64_t)(e.gp[q + 1] - e.gp[q]) >= P.color_cutoff) return LV_ERR_ARG;
 
-    // per-vertex state, sized for the phase-0 union
-    const int nmax = Gp.n;
-    PhaseState &ps = r.ps;
-    LV_TRY(dalloc_n(&ps.C, (size_t)nmax, s));
-    LV_TRY(dalloc_n(&ps.comm[0], (size_t)nmax, s));
-    LV_TRY(dalloc_n(&ps.moves[0], (size_t)nmax, s));
-    LV_TRY(dalloc_n(&ps.stats, 1, s));
-    LV_TRY(dalloc_n(&r.newid, (size_t)nmax + 1, s));
-    LV_TRY(dalloc_n(&r.order_c, (size_t)nmax, s));
-    LV_TRY(dalloc_n(&r.bo_c, (size_t)kBins + 2, s));
-    LV_TRY(dalloc_n(&r.pos, (size_t)nmax + 1, s));
-    LV_TRY(dalloc_n(&ps.act, 1, s));
-    LV_TRY(dalloc_n(&ps.move_count, 4, s));
-    LV_CUDA(cudaMemsetAsync(ps.act, 0, sizeof(int32_t), s));
-    ps.bar = &ps.stats->bar;
-    ps.bar_err = &ps.stats->bar_err;
-    ps.coloured = false;
-    ps.n_act = 1;
-    ps.two_m = 0;
-    ps.two_m_g = h->two_m_dev;
-    ps.active_g = r.flags;
-    ps.g_ein = r.gsum;
-    ps.g_a2 = r.gsum + G;
-    ps.g_moved = r.gsum + 2 * (size_t)G;
-
-    std::vector<GState> gs((size_t)G);
-    std::vector<int64_t> garcs((size_t)G);
-    double ms_iter = 0.0, ms_rebuild = 0.0;
-    const size_t gsum_bytes = sizeof(unsigned long long) * 3 * (size_t)G;
-    std::vector<int> ev_iter, ev_reb;  // event index pairs per phase
-    std::vector<int> ev_sweep;         // event index pairs per sweep
-
-    for (int32_t p = 0; p < P.max_phases; ++p) {
-        const int32_t *gptr = r.gbuf[cur];
-        int32_t *gstart = r.gbuf[cur ^ 1];
-        // per-graph arc counts of the phase graph
-        gather_at_kernel<<<grid_n(G + 1), 256, 0, s>>>(G, gptr, Gp.off, r.tmp);
-        LV_LAUNCH_CHECK();
-        LV_CUDA(cudaMemcpyAsync(h->pin_i32, r.tmp, sizeof(int32_t) * ((size_t)G + 1),
-                                cudaMemcpyDeviceToHost, s));
-        LV_CUDA(cudaStreamSynchronize(s));
-        for (int32_t g = 0; g < G; ++g) garcs[g] = (int64_t)h->pin_i32[g + 1] - h->pin_i32[g];
-
-        // ---- initial state and N_start of every graph in the phase
-        ps.g = Gp;
-        ps.k = k;
-        ps.loop = loop;
-        ps.gid = gid;
-        const int ev_i0 = h->timer.mark();
-        LV_TRY(init_phase(ps, s));
-        int n_running = 0;
-        for (int32_t g = 0; g < G; ++g) {
-            GState &t = gs[g];
-            t.running = !t.done;
-            t.step = 0;
-            t.have_np = false;
-            t.n_p = 0;
-            t.iters = 0;
-            h->pin_flags[g] = t.running ? 1 : 0;
-            n_running += t.running ? 1 : 0;
+    // labels of every graph after each phase (final ones for graphs that left)
+    int32_t *cur = nullptr, *dst_off = nullptr;
+    struct Free {
+        cudaStream_t s;
+        int32_t **a, **b;
+        ~Free() {
+            dfree(*a, s);
+            dfree(*b, s);
         }
-        LV_CUDA(cudaMemcpyAsync(r.flags, h->pin_flags, (size_t)G, cudaMemcpyHostToDevice, s));
-        LV_CUDA(cudaMemsetAsync(r.gsum, 0, gsum_bytes, s));
-        graph_sums_kernel<<<grid_n(Gp.n), 256, 0, s>>>(Gp.n, gid, k, loop, r.flags, nullptr,
-                                                       r.gsum, r.gsum + G);
-        LV_LAUNCH_CHECK();
-        LV_CUDA(cudaMemcpyAsync(h->pin_u64, r.gsum, sizeof(unsigned long long) * 2 * (size_t)G,
-                                cudaMemcpyDeviceToHost, s));
-        LV_CUDA(cudaStreamSynchronize(s));
-        for (int32_t g = 0; g < G; ++g)
-            if (gs[g].running)
-                gs[g].N_start = h->two_m[g] * (int64_t)h->pin_u64[g] - (int64_t)h->pin_u64[G + g];
-
-        // ---- degree bins (measured once per phase index when autotuning)
-        BinLimits plim = lim;
-        if (P.autotune && Gp.A >= kTuneMinArcs) {
-            if ((int32_t)h->tuned.size() <= p || !h->tuned_ok[p]) {
-                BinLimits best = lim;
-                LV_TRY(tune_bins(ps, lim, r.gsum, gsum_bytes, &best, h->pinned, s));
-                if ((int32_t)h->tuned.size() <= p) {
-                    h->tuned.resize(p + 1);
-                    h->tuned_ok.resize(p + 1, 0);
-                }
-                h->tuned[p] = best;
-                h->tuned_ok[p] = 1;
-            }
-            plim = h->tuned[p];
-        }
-        r.have_b = true;
-        LV_TRY(bucket_vertices(Gp, nullptr, 1, plim, &r.b, h->pinned, s));
-
-        // ---- batched iterations (Alg. 1 per graph, fused modularity)
-        r.sg.reset();  // new phase graph: recapture
-        int32_t sweep_no = 0;
-        Buckets bl = r.b;  // the vertex list the sweeps walk (compacted as graphs stop)
-        const int glo = r.b.host_off[0], ghi = r.b.host_off[kBinCta];
-        int64_t listed = 0;  // vertices of the graphs in the list
-        for (int32_t g = 0; g < G; ++g)
-            if (gs[g].running) listed += gp[g + 1] - gp[g];
-        while (n_running > 0) {
-            lv_batch_sweep rec;
-            std::memset(&rec, 0, sizeof rec);
-            rec.phase = p;
-            rec.sweep = ++sweep_no;
-            rec.graphs = n_running;
-            for (int32_t g = 0; g < G; ++g)
-                if (gs[g].running) {
-                    rec.vertices += gp[g + 1] - gp[g];
-                    rec.arcs += garcs[g];
-                }
-            auto enqueue = [&]() -> lv_status {
-                LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
-                LV_CUDA(cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s));
-                LV_CUDA(cudaMemsetAsync(r.gsum, 0, gsum_bytes, s));
-                return sweep_iteration(ps, bl, s);
-            };
-            SweepGraph &sg = r.sg;
-            if (P.graph_capture && !sg.disabled &&
-                (!sg.exec || sg.order != bl.order || sg.bo != bl.bucket_off)) {
-                sg.reset();
-                const unsigned long long l0 = g_kernel_launches;
-                cudaGraph_t graph = nullptr;
-                bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-                if (ok) {
-                    const lv_status est = enqueue();
-                    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
-                    ok = est == LV_OK && ce == cudaSuccess && graph &&
-                         cudaGraphInstantiate(&sg.exec, graph, 0) == cudaSuccess;
-                    if (graph) cudaGraphDestroy(graph);
-                }
-                g_kernel_launches = l0;
-                if (ok) {
-                    sg.order = bl.order;
-                    sg.bo = bl.bucket_off;
-                    ++sg.captures;
-                } else {
-                    cudaGetLastError();
-                    sg.reset();
-                    sg.disabled = true;
-                }
-            }
-            ev_sweep.push_back(h->timer.mark());
-            if (sg.exec) {
-                LV_CUDA(cudaGraphLaunch(sg.exec, s));
-                ++g_kernel_launches;
-                ++h->stats.graph_launches;
-            } else {
-                LV_TRY(enqueue());
-            }
-            ev_sweep.push_back(h->timer.mark());
-            ++h->stats.sweep_launches;
-            LV_CUDA(cudaMemcpyAsync(h->pin_stats, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, s));
-            LV_CUDA(cudaMemcpyAsync(h->pin_u64, r.gsum, gsum_bytes, cudaMemcpyDeviceToHost, s));
-            LV_CUDA(cudaStreamSynchronize(s));
-            if (h->pin_stats->bar_err) return LV_ERR_TIMEOUT;
-            if (h->pin_stats->err) return LV_ERR_HASH;
-            for (int32_t g = 0; g < G; ++g) {
-                GState &t = gs[g];
-                if (!t.running) continue;
-                const int step = ++t.step;
-                // N(C^{step-1}) of this graph, read by the sweep under the labels it used
-                const int64_t N_prev =
-                    h->two_m[g] * (int64_t)h->pin_u64[g] - (int64_t)h->pin_u64[G + g];
-                const int64_t moved = (int64_t)h->pin_u64[2 * (size_t)G + g];
-                rec.moved += moved;
-                bool fin = false;
-                if (step == 1) {
-                    if (moved == 0) {
-                        t.iters = 1;
-                        fin = true;
-                    }
-                } else {
-                    const int tt = step - 1;
-                    if ((t.have_np && gain_below(N_prev, t.n_p, theta)) || tt >= P.max_iters) {
-                        t.iters = tt;
-                        fin = true;
-                    } else {
-                        t.n_p = N_prev;
-                        t.have_np = true;
-                        if (moved == 0) {
-                            t.iters = step;
-                            fin = true;
-                        }
-                    }
-                }
-                if (fin) {
-                    t.N_end = N_prev;
-                    t.running = false;
-                    h->pin_flags[g] = 0;
-                    --n_running;
-                }
-            }
-            h->sweeps.push_back(rec);
-            if (n_running > 0) {
-                // graphs that go on apply their moves and are swept again
-                LV_CUDA(cudaMemcpyAsync(r.flags, h->pin_flags, (size_t)G, cudaMemcpyHostToDevice, s));
-                apply_batch_kernel<<<g_num_sms * 4, 256, 0, s>>>(ps.C, ps.comm[0], ps.moves[0],
-                                                                  ps.move_count, gid, r.flags);
-                LV_LAUNCH_CHECK();
-                int64_t live_v = 0;
-                for (int32_t g = 0; g < G; ++g)
-                    if (gs[g].running) live_v += gp[g + 1] - gp[g];
-                if (ghi > glo && live_v * 4 < listed * 3) {
-                    // drop stopped graphs from the group bins (from the full list)
-                    keep_flags_kernel<<<grid_n(ghi - glo), 256, 0, s>>>(r.b.order, glo, ghi, gid,
-                                                                         r.flags, r.pos);
-                    LV_LAUNCH_CHECK();
-                    LV_TRY(scan_excl_i32(r.pos, r.pos, ghi - glo, s));
-                    compact_kernel<<<grid_n(ghi - glo), 256, 0, s>>>(r.b.order, glo, ghi, r.pos,
-                                                                     r.order_c);
-                    LV_LAUNCH_CHECK();
-                    if (bl.order != r.order_c) {  // first compaction: CTA, hub and skip bins
-                        const int tail = r.b.host_off[kBins + 1] - ghi;
-                        if (tail > 0)
-                            LV_CUDA(cudaMemcpyAsync(r.order_c + ghi, r.b.order + ghi,
-                                                    sizeof(int32_t) * (size_t)tail,
-                                                    cudaMemcpyDeviceToDevice, s));
-                        LV_CUDA(cudaMemcpyAsync(r.bo_c + kBins + 1, r.b.bucket_off + kBins + 1,
-                                                sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-                    }
-                    compact_offsets_kernel<<<1, 32, 0, s>>>(r.b.bucket_off, r.pos, r.bo_c);
-                    LV_LAUNCH_CHECK();
-                    bl.order = r.order_c;
-                    bl.bucket_off = r.bo_c;
-                    listed = live_v;
-                }
-            }
-        }
-        const int ev_i1 = h->timer.mark();
-
-        // ---- rebuild (Sec. 4.5) of all graphs at once
-        const int ev_r0 = h->timer.mark();
-        LV_TRY(renumber(Gp.n, ps.comm[0], r.newid, s));
-        gather_at_kernel<<<grid_n(G + 1), 256, 0, s>>>(G, gptr, r.newid, gstart);
-        LV_LAUNCH_CHECK();
-        LV_CUDA(cudaMemcpyAsync(h->pin_i32, gstart, sizeof(int32_t) * ((size_t)G + 1),
-                                cudaMemcpyDeviceToHost, s));
-        int32_t *lab = nullptr;
-        LV_TRY(dalloc_n(&lab, (size_t)n_orig, s));
-        h->labels.push_back(lab);
-        LV_TRY(compose_labels(n_orig, r.map, ps.C, r.newid, lab, s));
-        localize_kernel<<<grid_n(n_orig), 256, 0, s>>>(n_orig, h->gid_in, gstart, lab);
-        LV_LAUNCH_CHECK();
-        LV_CUDA(cudaStreamSynchronize(s));
-        const int32_t n_next = h->pin_i32[G];
-        bool all_done = true;
-        for (int32_t g = 0; g < G; ++g) {
-            GState &t = gs[g];
-            if (t.done) continue;
-            lv_phase_info in;
-            std::memset(&in, 0, sizeof in);
-            in.n = gp[g + 1] - gp[g];
-            in.arcs = garcs[g];
-            in.n_next = (int64_t)h->pin_i32[g + 1] - h->pin_i32[g];
-            in.two_m = h->two_m[g];
-            in.N_start = t.N_start;
-            in.N_end = t.N_end;
-            in.q = (double)t.N_end / ((double)h->two_m[g] * (double)h->two_m[g]);
-            in.theta = theta;
-            in.iterations = t.iters;
-            in.ms_color = in.ms_iterate = in.ms_rebuild = -1.0;
-            h->info[g].push_back(in);
-            if (in.n_next == in.n || gain_below(t.N_end, t.N_start, P.theta_low) ||
-                p + 1 >= P.max_phases)
-                t.done = true;
-            all_done = all_done && t.done;
-        }
-        for (int32_t g = 0; g <= G; ++g) gp[g] = h->pin_i32[g];  // starts in the coarse union
-        if (!all_done) {
-            DGraph G2;
-            LV_TRY(coarsen(Gp, ps.C, r.newid, n_next, &G2, h->pinned, s));
-            int32_t *k2 = nullptr, *l2 = nullptr, *gid2 = nullptr;
-            LV_TRY(dalloc_n(&k2, (size_t)G2.n, s));
-            LV_TRY(dalloc_n(&l2, (size_t)G2.n, s));
-            LV_TRY(dalloc_n(&gid2, (size_t)G2.n, s));
-            gid_scatter_kernel<<<grid_n(Gp.n), 256, 0, s>>>(Gp.n, gid, ps.C, r.newid, gid2);
-            LV_LAUNCH_CHECK();
-            LV_TRY(compute_degrees(G2, k2, l2, s));
-            if (r.own_g) free_graph(r.g, s);
-            dfree(r.k, s);
-            dfree(r.loop, s);
-            dfree(r.gid, s);
-            r.g = G2;
-            r.own_g = true;
-            Gp = G2;
-            k = r.k = k2;
-            loop = r.loop = l2;
-            gid = r.gid = gid2;
-            cur ^= 1;
-        }
-        const int ev_r1 = h->timer.mark();
-        free_buckets(r.b, s);
-        r.b = Buckets();
-        r.have_b = false;
-        ev_iter.push_back(ev_i0);
-        ev_iter.push_back(ev_i1);
-        ev_reb.push_back(ev_r0);
-        ev_reb.push_back(ev_r1);
-        if (all_done) break;
+    } fr{s, &cur, &dst_off};
+    LV_TRY(dalloc_n(&cur, (size_t)n_orig, s));
+    LV_TRY(dalloc_n(&dst_off, (size_t)G, s));
+    std::vector<int32_t> off_h((size_t)G);
+    std::vector<Finished> fin;
+    while (e.num_graphs() > 0) {
+        LV_TRY(e.phase_run());
+        // engine position q holds batch graph tag; its original vertices move
+        // from the engine's order to the batch's
+        const int32_t Gq = e.num_graphs();
+        for (int32_t q = 0; q < Gq; ++q)
+            off_h[q] = h->gptr[e.graphs[q].tag] - e.optr[q];
+        LV_CUDA(cudaMemcpyAsync(dst_off, off_h.data(), sizeof(int32_t) * Gq, cudaMemcpyHostToDevice, s));
+        LV_TRY(scatter_blocks((int32_t)e.n_orig, e.gid_orig, dst_off, e.labels, cur, s));
+        int32_t *snap = nullptr;
+        LV_TRY(dalloc_n(&snap, (size_t)n_orig, s));
+        h->labels.push_back(snap);
+        LV_CUDA(cudaMemcpyAsync(snap, cur, sizeof(int32_t) * (size_t)n_orig, cudaMemcpyDeviceToDevice, s));
+        LV_CUDA(cudaStreamSynchronize(s));  // off_h is read by the copy above
+        for (int32_t q = 0; q < Gq; ++q) h->info[e.graphs[q].tag] = e.graphs[q].info;
+        fin.clear();
+        LV_TRY(e.phase_end(fin));
     }
     const int ev_run1 = h->timer.mark();
     LV_CUDA(cudaStreamSynchronize(s));
 
     // totals, as lv_run would report them summed over the graphs
+    h->sweeps = e.sweeps;
+    h->stats.sweep_launches = e.sweep_launches;
+    h->stats.graph_launches = e.graph_launches;
     h->stats.num_phases = 0;
     h->stats.total_iterations = 0;
     h->stats.edge_visits = 0;
-    for (int32_t g = 0; g < G; ++g) {
-        h->stats.num_phases = std::max(h->stats.num_phases, (int32_t)h->info[g].size());
-        for (const auto &in : h->info[g]) {
+    for (int32_t q = 0; q < G; ++q) {
+        h->stats.num_phases = std::max(h->stats.num_phases, (int32_t)h->info[q].size());
+        for (const auto &in : h->info[q]) {
             h->stats.total_iterations += in.iterations;
             h->stats.edge_visits += (int64_t)in.iterations * in.arcs;
         }
     }
-    for (size_t q = 0; q + 1 < ev_iter.size(); q += 2) {
-        ms_iter += h->timer.ms(ev_iter[q], ev_iter[q + 1]);
-        ms_rebuild += h->timer.ms(ev_reb[q], ev_reb[q + 1]);
-    }
-    for (size_t q = 0; q < h->sweeps.size(); ++q)
-        h->sweeps[q].ms = h->timer.ms(ev_sweep[2 * q], ev_sweep[2 * q + 1]);
+    double ms_iter = 0.0, ms_rebuild = 0.0;
+    for (size_t q = 0; q + 1 < e.ev_iter.size(); q += 2) ms_iter += h->timer.ms(e.ev_iter[q], e.ev_iter[q + 1]);
+    for (size_t q = 0; q + 1 < e.ev_reb.size(); q += 2) ms_rebuild += h->timer.ms(e.ev_reb[q], e.ev_reb[q + 1]);
+    for (size_t q = 0; q < h->sweeps.size() && 2 * q + 1 < e.ev_sweep.size(); ++q)
+        h->sweeps[q].ms = h->timer.ms(e.ev_sweep[2 * q], e.ev_sweep[2 * q + 1]);
+    if (!h->timer.on)
+        for (auto &sw : h->sweeps) sw.ms = -1.0;
     h->stats.ms_total = h->timer.ms(ev_run0, ev_run1);
     h->stats.ms_vf = h->timer.ms(ev_vf0, ev_vf1);
     h->stats.ms_color = h->timer.on ? 0.0 : -1.0;
@@ -846,7 +334,6 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
 }
 
 }  // namespace
-
 extern "C" {
 
 lv_status lv_batch_run(lv_batch *b, const lv_params *p) {
