@@ -323,6 +323,79 @@ lv_status lv_batch_get_sweeps(const lv_batch *b, lv_batch_sweep *out, int64_t co
 /* Release the batch and its device memory (NULL is a no-op). */
 void lv_batch_destroy(lv_batch *b);
 
+/* ---------------------------------------------------------------- serving
+ * A server runs community detection for a stream of requests on one GPU
+ * with continuous batching.  A worker thread owns the GPU work: at every
+ * phase boundary it admits queued requests (first come, first served) while
+ * the estimated device footprint of the resident requests stays within the
+ * memory budget and the slot limit, appends them to the running multi-graph
+ * engine, runs one batched phase of every resident request (their sweeps
+ * share launches), and completes the requests whose phase loop stopped.  A
+ * request's CSR and labels stay on the device across its phases.  Each
+ * request gets exactly what lv_run gives for it alone with the same
+ * parameters, whatever else is resident. */
+typedef struct lv_server lv_server; /* opaque, owned by the library */
+
+typedef struct {
+    int64_t mem_budget_bytes; /* resident requests' estimated device bytes (48 per
+                                 stored arc + 64 per vertex); 0 = 120 GB.  A request
+                                 larger than the budget is admitted alone. */
+    int32_t max_graphs;       /* resident requests at most; 0 = 65,536 */
+    int32_t reserved;
+    lv_params params;         /* for every request; coloring must be 0 */
+} lv_server_config;
+
+/* Outcome of one request (times in ms since lv_server_create, host clock). */
+typedef struct {
+    int32_t status;      /* LV_OK, or the validation error of its CSR */
+    int32_t num_phases;
+    int32_t iterations;  /* over all its phases */
+    int32_t reserved;
+    int64_t n, arcs, two_m, n_final;
+    int64_t N_final;     /* modularity numerator after its last phase */
+    double q;            /* N_final / (2m)^2 */
+    double t_submit_ms, t_admit_ms, t_done_ms;
+} lv_server_result_info;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t rounds;       /* batched phases run */
+    int64_t sweeps;       /* batched sweeps */
+    int64_t peak_graphs;  /* most requests resident at once */
+    int64_t peak_bytes;   /* largest estimated resident footprint */
+} lv_server_stats;
+
+/* Start a server on the current device.  cuda_stream: the stream for its
+ * work (NULL = a stream the server creates).  LV_ERR_ARG for a NULL config,
+ * coloring != 0, or invalid parameters. */
+lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *cuda_stream);
+
+/* Queue a request: a CSR under the lv_graph_create contract in HOST memory,
+ * copied before the call returns.  *request_id receives its id (>= 0).  The
+ * CSR is validated on admission; an invalid one completes with its error. */
+lv_status lv_server_submit(lv_server *srv, int64_t n, const int64_t *rowptr, const int32_t *col,
+                           const int32_t *w, int64_t *request_id);
+
+/* Wait up to timeout_s seconds (< 0: forever) for a request; *done = 1 when
+ * it completed.  LV_ERR_ARG for an unknown id. */
+lv_status lv_server_wait(lv_server *srv, int64_t request_id, double timeout_s, int32_t *done);
+
+/* Result of a completed request: labels int32[n] in host memory (may be
+ * NULL), numbered per graph as lv_get_labels numbers the final phase, and
+ * its record.  LV_ERR_STATE while it is not done; the request's own error
+ * status when its CSR was invalid. */
+lv_status lv_server_result(lv_server *srv, int64_t request_id, int32_t *labels,
+                           lv_server_result_info *info);
+
+/* Forget a completed request (frees its stored labels). */
+lv_status lv_server_release(lv_server *srv, int64_t request_id);
+
+lv_status lv_server_get_stats(lv_server *srv, lv_server_stats *out);
+
+/* Stop the worker after its current phase and free everything; requests not
+ * completed are dropped (NULL is a no-op). */
+void lv_server_destroy(lv_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

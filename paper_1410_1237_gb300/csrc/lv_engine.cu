@@ -639,17 +639,16 @@ lv_status Engine::phase_run() {
         if (P.graph_capture && !sg.disabled &&
             (!sg.exec || sg.order != bl.order || sg.bo != bl.bucket_off)) {
             sg.reset();
-            const unsigned long long l0 = g_kernel_launches;
             cudaGraph_t graph = nullptr;
             bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
                 const lv_status est = enqueue();
+                if (est == LV_OK) g_kernel_launches.fetch_sub(1);  // captured, not launched
                 const cudaError_t ce = cudaStreamEndCapture(s, &graph);
                 ok = est == LV_OK && ce == cudaSuccess && graph &&
                      cudaGraphInstantiate(&sg.exec, graph, 0) == cudaSuccess;
                 if (graph) cudaGraphDestroy(graph);
             }
-            g_kernel_launches = l0;
             if (ok) {
                 sg.order = bl.order;
                 sg.bo = bl.bucket_off;

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "lv.h"
 
 namespace lv {
@@ -54,8 +56,9 @@ void set_cuda_error(cudaError_t e, const char *what, const char *file, int line)
         if (s_ != LV_OK) return s_;       \
     } while (0)
 
-// every kernel launch is followed by this check, which also counts it
-extern unsigned long long g_kernel_launches;
+// every kernel launch is followed by this check, which also counts it (the
+// counter is process-wide; a serving thread launches beside the caller's)
+extern std::atomic<unsigned long long> g_kernel_launches;
 #define LV_LAUNCH_CHECK()                 \
     do {                                  \
         ++::lv::g_kernel_launches;        \

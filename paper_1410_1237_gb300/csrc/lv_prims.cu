@@ -19,7 +19,7 @@ TraceBuf trace_buffer() {
 #endif
     return g_trace;
 }
-unsigned long long g_kernel_launches = 0;
+std::atomic<unsigned long long> g_kernel_launches{0};
 
 // --------------------------------------------------------------- errors
 static thread_local char t_last_error[512] = "";

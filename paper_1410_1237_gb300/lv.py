@@ -81,6 +81,27 @@ class lv_batch_sweep(ctypes.Structure):
                 ("arcs", ctypes.c_int64), ("moved", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
+class lv_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("params", lv_params)]
+
+
+class lv_server_result_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("num_phases", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("arcs", ctypes.c_int64), ("two_m", ctypes.c_int64),
+                ("n_final", ctypes.c_int64), ("N_final", ctypes.c_int64), ("q", ctypes.c_double),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
+class lv_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("rounds", ctypes.c_int64), ("sweeps", ctypes.c_int64),
+                ("peak_graphs", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 # every function declared in include/lv.h, with its ctypes signature
@@ -121,6 +142,13 @@ SIGNATURES = {
     "lv_batch_get_num_sweeps": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
     "lv_batch_get_sweeps": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "lv_batch_destroy": (None, [_vp]),
+    "lv_server_create": (ctypes.c_int, [_P(_vp), _P(lv_server_config), _vp]),
+    "lv_server_submit": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, _vp, _P(ctypes.c_int64)]),
+    "lv_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _P(ctypes.c_int32)]),
+    "lv_server_result": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _P(lv_server_result_info)]),
+    "lv_server_release": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "lv_server_get_stats": (ctypes.c_int, [_vp, _P(lv_server_stats)]),
+    "lv_server_destroy": (None, [_vp]),
 }
 
 
@@ -350,6 +378,62 @@ def lv_batch_get_sweeps(h: int) -> list:
 def lv_batch_destroy(h: int) -> None:
     if h:
         load().lv_batch_destroy(h)
+
+
+def lv_server_create(mem_budget_bytes: int = 0, max_graphs: int = 0, stream: int = 0,
+                     **params) -> int:
+    """A serving handle; params as make_params (coloring must stay 0)."""
+    cfg = lv_server_config()
+    cfg.mem_budget_bytes = int(mem_budget_bytes)
+    cfg.max_graphs = int(max_graphs)
+    cfg.params = make_params(**{"coloring": 0, **params})
+    h = ctypes.c_void_p()
+    _check(load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), stream or None),
+           "lv_server_create")
+    return h.value
+
+
+def lv_server_submit(h: int, rowptr, col, w) -> int:
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    ww = np.ascontiguousarray(w, dtype=np.int32)
+    rid = ctypes.c_int64()
+    _check(load().lv_server_submit(h, len(rp) - 1, rp.ctypes.data, cl.ctypes.data, ww.ctypes.data,
+                                   ctypes.byref(rid)), "lv_server_submit")
+    return rid.value
+
+
+def lv_server_wait(h: int, request_id: int, timeout_s: float = -1.0) -> bool:
+    done = ctypes.c_int32()
+    _check(load().lv_server_wait(h, request_id, timeout_s, ctypes.byref(done)), "lv_server_wait")
+    return bool(done.value)
+
+
+def lv_server_result(h: int, request_id: int, n: int | None = None):
+    """(labels or None, lv_server_result_info); raises LVError for a failed request."""
+    info = lv_server_result_info()
+    code = load().lv_server_result(h, request_id, None, ctypes.byref(info))
+    if code != LV_OK:
+        raise LVError(code, "lv_server_result")
+    lab = np.empty(info.n, dtype=np.int32)
+    _check(load().lv_server_result(h, request_id, lab.ctypes.data, ctypes.byref(info)),
+           "lv_server_result")
+    return lab, info
+
+
+def lv_server_release(h: int, request_id: int) -> None:
+    _check(load().lv_server_release(h, request_id), "lv_server_release")
+
+
+def lv_server_get_stats(h: int) -> lv_server_stats:
+    out = lv_server_stats()
+    _check(load().lv_server_get_stats(h, ctypes.byref(out)), "lv_server_get_stats")
+    return out
+
+
+def lv_server_destroy(h: int) -> None:
+    if h:
+        load().lv_server_destroy(h)
 
 
 # ------------------------------------------------------- convenience layer

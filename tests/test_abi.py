@@ -57,7 +57,9 @@ def test_struct_layouts_match_header(tmp_path):
     structs = {"lv_params": lv.lv_params, "lv_phase_info": lv.lv_phase_info,
                "lv_iter_stat": lv.lv_iter_stat, "lv_stats": lv.lv_stats,
                "lv_batch_graph_info": lv.lv_batch_graph_info,
-               "lv_batch_sweep": lv.lv_batch_sweep}
+               "lv_batch_sweep": lv.lv_batch_sweep, "lv_server_config": lv.lv_server_config,
+               "lv_server_result_info": lv.lv_server_result_info,
+               "lv_server_stats": lv.lv_server_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lv.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
@@ -74,3 +76,14 @@ def test_struct_layouts_match_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+
+
+def test_server_rejects_colouring_without_gpu():
+    # argument checks come before any device work
+    from paper_1410_1237_gb300 import lv
+    lv.load()
+    cfg = lv.lv_server_config()
+    cfg.params = lv.make_params(coloring=1)
+    h = ctypes.c_void_p()
+    assert lv.load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1
+    assert lv.load().lv_server_create(ctypes.byref(h), None, None) == -1
