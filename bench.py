@@ -9,6 +9,9 @@ all sweep iterations of the run divided by the run's device time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
   python bench.py --workload planted_batch4096   (4,096 graphs per step: graphs/s,
                                                   against 4,096 plain runs)
+  python bench.py --workload served_mix200       (Poisson request stream through the
+                                                  server: graphs/s, p50/p99 latency,
+                                                  against sequential plain solves)
   python bench.py --impl reference ...   (the serial oracle on host cores)
 
 With N > 1 (torchrun) every rank runs an independent replica on its own GPU
@@ -391,6 +394,186 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
     return 0
 
 
+SERVED_METRIC = "served graphs/s under Poisson arrivals (whole run per request, bit-exact labels)"
+SERVED_PARAMS = dict(vertex_following=1, coloring=0, theta_low=1e-6)  # the server's phases are uncoloured
+SERVED_BUDGET = 120 << 30
+
+
+def served_workload(name: str):
+    import graphgen
+    if name != "served_mix200":
+        raise SystemExit(f"unknown served workload {name}")
+    return graphgen.served_stream(num_requests=200, rate=200.0, seed=5)
+
+
+def pct(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+def serve_once(lv, reqs):
+    """One pass of the request stream through a server: requests are
+    submitted at their arrival times by a separate thread; returns per-request
+    (labels, info) and the server stats."""
+    h = lv.lv_server_create(mem_budget_bytes=SERVED_BUDGET, **SERVED_PARAMS)
+    ids = [None] * len(reqs)
+    try:
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, (a, g) in enumerate(reqs):
+                dt = t0 + a - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                ids[i] = lv.lv_server_submit(h, g.rowptr, g.col, g.w)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        for rid in ids:
+            lv.lv_server_wait(h, rid, -1.0)
+        out = [lv.lv_server_result(h, rid) for rid in ids]
+        st = lv.lv_server_get_stats(h)
+    finally:
+        lv.lv_server_destroy(h)
+    return out, st
+
+
+def run_reference_served(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    reqs = served_workload(args.workload)
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i][1].arcs)  # smallest first: bounded
+    vals, desc = [], ""
+    for step in range(args.warmup + args.steps):
+        t_tot, done = 0.0, 0
+        for i in order:
+            g = reqs[i][1]
+            t0 = time.perf_counter()
+            oracle.run(g.rowptr, g.col, g.w, **SERVED_PARAMS)
+            t_tot += time.perf_counter() - t0
+            done += 1
+            if t_tot >= 6.0:
+                break
+        desc = f"the {done} smallest of {len(reqs)} requests, whole run each, {t_tot:.2f} s"
+        if step >= args.warmup:
+            vals.append(done / t_tot)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": SERVED_METRIC, "value": value, "unit": "graphs/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * len(reqs) / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": args.workload, "requests": len(reqs)},
+            "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_served(args, lv, torch, dev, pg, rank, world, local):
+    """served_mix200: 200 requests (R-MAT scale 10-20 and planted graphs of
+    1e3-1e6 vertices) arriving as a Poisson stream at 200 req/s, served with
+    continuous batching, against the same stream solved one request at a time
+    by plain lv_run calls in arrival order."""
+    import numpy as np
+    reqs = served_workload(args.workload)
+    N = len(reqs)
+    in_bytes = int(sum(g.rowptr.nbytes + g.col.nbytes + g.w.nbytes for _, g in reqs))
+    out_bytes = int(sum(4 * g.n for _, g in reqs))
+    serve_once(lv, reqs[:min(N, 24)])  # warm the library (pool, kernels)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    lat, spans, launches, rounds, sweeps, peak_g = [], [], 0, 0, 0, 0
+    results = None
+    for step in range(args.warmup + args.steps):
+        out, st = serve_once(lv, reqs)
+        infos = [i for _, i in out]
+        if any(i.status != 0 for i in infos):
+            raise SystemExit("a served request failed")
+        span = (max(i.t_done_ms for i in infos) - min(i.t_submit_ms for i in infos)) / 1e3
+        if step >= args.warmup:
+            spans.append(span)
+            lat += [i.t_done_ms - i.t_submit_ms for i in infos]
+            launches += st.kernel_launches
+            rounds, sweeps, peak_g = st.rounds, st.sweeps, st.peak_graphs
+            worker_ms = {"admit_thread": st.ms_admit, "append": st.ms_append,
+                         "iterate": st.ms_iterate, "rebuild": st.ms_rebuild,
+                         "results": st.ms_results}
+            results = out
+    clk = clocks.stop()
+    total_s = max_over_ranks(sum(spans), pg, dev if dev.type == "cuda" else dev)
+    value = whole_job_rate(N * len(spans), world, total_s)
+
+    # ---- the same stream solved one request at a time (FIFO, plain lv_run)
+    service = []
+    same = True
+    p1 = lv.make_params(**SERVED_PARAMS)
+    for i, (a, g) in enumerate(reqs):
+        t0 = time.perf_counter()
+        hh = lv.lv_graph_create(g.n, g.rowptr, g.col, g.w)
+        lv.lv_run(hh, p1)
+        lab = np.empty(g.n, dtype=np.int32)
+        lv.lv_get_labels(hh, -1, lab)
+        lv.lv_graph_destroy(hh)
+        service.append(time.perf_counter() - t0)
+        same = same and bool(np.array_equal(lab, results[i][0]))
+    finish, seq_lat = 0.0, []
+    for (a, _), sv in zip(reqs, service):
+        finish = max(finish, a) + sv
+        seq_lat.append(1e3 * (finish - a))
+    seq_span = finish - reqs[0][0]
+    if rank != 0:
+        return 0
+    line = {
+        "metric": SERVED_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(spans) / len(spans),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic (seeded Poisson request stream; same stream on every rank)",
+        "config": {"workload": args.workload, "requests": N, "rate_req_s": 200.0,
+                   "params": SERVED_PARAMS, "mem_budget_bytes": SERVED_BUDGET,
+                   "parallelism": f"replicas x{world}", "arcs_total": int(sum(g.arcs for _, g in reqs)),
+                   "l2": "inputs larger than L2 (whole stream per step)",
+                   "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+                   "rounds": rounds, "batched_sweeps": sweeps, "peak_resident_requests": peak_g,
+                   "worker_ms_last_step": worker_ms},
+        "sequential_plain": {"value": N / seq_span, "unit": "graphs/s",
+                             "latency_ms_p50": pct(seq_lat, 50), "latency_ms_p99": pct(seq_lat, 99),
+                             "service_s_total": sum(service),
+                             "labels_identical_all": same},
+        "speedup_vs_sequential": value / world / (N / seq_span),
+        "roofline": None,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": in_bytes,
+                "d2h_bytes_per_step": out_bytes,
+                "note": "the served value is end to end: host CSRs in, host labels out"},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        import oracle
+        order = sorted(range(N), key=lambda i: reqs[i][1].arcs)
+        t_tot, done = 0.0, 0
+        for i in order:
+            g = reqs[i][1]
+            t0 = time.perf_counter()
+            oracle.run(g.rowptr, g.col, g.w, **SERVED_PARAMS)
+            t_tot += time.perf_counter() - t0
+            done += 1
+            if t_tot >= 10.0:
+                break
+        line["cpu_baseline"] = {"value": done / t_tot, "unit": "graphs/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"the {done} smallest of {N} requests, whole run each, "
+                                          f"{t_tot:.2f} s"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,7 +586,10 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     batch = args.workload.startswith("planted_batch")
+    served = args.workload.startswith("served_")
     if args.impl == "reference":
+        if served:
+            return run_reference_served(args)
         return run_reference_batch(args) if batch else run_reference(args)
 
     import numpy as np
@@ -424,8 +610,9 @@ def main():
     if pg:
         pg.barrier()
     lv.load()
-    if batch:
-        rc = bench_batch(args, lv, torch, dev, pg, rank, world, local)
+    if batch or served:
+        fn = bench_batch if batch else bench_served
+        rc = fn(args, lv, torch, dev, pg, rank, world, local)
         if pg:
             pg.destroy_process_group()
         return rc

@@ -268,3 +268,38 @@ def planted_batch(num_graphs: int = 4096, nmin: int = 100, nmax: int = 50_000, b
         p_out = min(1.0, inter_deg / max(n - sz, 1.0)) if b > 1 else 0.0
         graphs.append(planted(n, b, p_in, p_out, 1, wmax, seed=(seed << 20) + g))
     return concat(graphs, f"planted_batch({num_graphs},seed={seed})")
+
+
+def _planted_degrees(n: int, b: int, intra_deg: float, inter_deg: float, wmax: int,
+                     seed: int) -> Graph:
+    """Planted partition with mean intra- and inter-block degrees given."""
+    b = int(min(b, max(1, n // 3)))
+    sz = n / b
+    p_in = min(1.0, intra_deg / max(sz - 1.0, 1.0))
+    p_out = min(1.0, inter_deg / max(n - sz, 1.0)) if b > 1 else 0.0
+    return planted(n, b, p_in, p_out, 1, wmax, seed=seed)
+
+
+def served_stream(num_requests: int = 200, rate: float = 200.0, seed: int = 5,
+                  rmat_scales=(10, 20), rmat_ef=(8, 16), planted_n=(1_000, 1_000_000)):
+    """Request stream for serving: Poisson arrivals at ``rate`` per second;
+    each request is, with equal odds, an R-MAT graph (scale and edge factor
+    uniform integers in the given ranges, (a,b,c) = (0.57, 0.19, 0.19)) or a
+    planted-partition graph (n log-uniform in ``planted_n``, 2..200 blocks,
+    mean intra-block degree 12, inter-block 2, weights 1..8).  Returns a list
+    of (arrival seconds, Graph); request i uses seed (seed << 20) + i."""
+    rng = np.random.default_rng(seed)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=num_requests))
+    out = []
+    for i in range(num_requests):
+        s = (seed << 20) + i
+        if rng.random() < 0.5:
+            sc = int(rng.integers(rmat_scales[0], rmat_scales[1] + 1))
+            ef = int(rng.integers(rmat_ef[0], rmat_ef[1] + 1))
+            g = rmat(sc, ef, seed=s)
+        else:
+            n = int(np.exp(rng.uniform(np.log(planted_n[0]), np.log(planted_n[1]))))
+            b = int(rng.integers(2, 201))
+            g = _planted_degrees(n, b, 12.0, 2.0, 8, s)
+        out.append((float(arrivals[i]), g))
+    return out

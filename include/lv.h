@@ -325,12 +325,16 @@ void lv_batch_destroy(lv_batch *b);
 
 /* ---------------------------------------------------------------- serving
  * A server runs community detection for a stream of requests on one GPU
- * with continuous batching.  A worker thread owns the GPU work: at every
- * phase boundary it admits queued requests (first come, first served) while
- * the estimated device footprint of the resident requests stays within the
- * memory budget and the slot limit, appends them to the running multi-graph
- * engine, runs one batched phase of every resident request (their sweeps
- * share launches), and completes the requests whose phase loop stopped.  A
+ * with continuous batching.  An admission thread takes queued requests
+ * (first come, first served) while the estimated device footprint of the
+ * requests in flight stays within the memory budget and the slot limit, and
+ * uploads, validates and vertex-follows them on its own stream; a worker
+ * thread joins them to its running multi-graph engine at its next phase
+ * boundary, runs one batched phase of every resident request (their sweeps
+ * share launches), and completes the requests whose phase loop stopped.
+ * Requests with fewer than 2^22 stored arcs and larger ones go to two such
+ * workers (own engines and streams), so small requests never wait for the
+ * iterations of large ones.   A
  * request's CSR and labels stay on the device across its phases.  Each
  * request gets exactly what lv_run gives for it alone with the same
  * parameters, whatever else is resident. */
@@ -363,6 +367,12 @@ typedef struct {
     int64_t sweeps;       /* batched sweeps */
     int64_t peak_graphs;  /* most requests resident at once */
     int64_t peak_bytes;   /* largest estimated resident footprint */
+    int64_t kernel_launches; /* CUDA kernels the worker launched (a graph replay counts 1) */
+    double ms_admit;      /* admission thread: uploading, validating and vertex following */
+    double ms_append;     /* worker thread: joining prepared requests to the engine */
+    double ms_iterate;    /* ... batched iterations up to the labels */
+    double ms_rebuild;    /* ... coarse graphs and departures */
+    double ms_results;    /* ... copying finished requests' labels to the host */
 } lv_server_stats;
 
 /* Start a server on the current device.  cuda_stream: the stream for its

@@ -160,41 +160,45 @@ __global__ void scatter_blocks_kernel(int32_t n, const int32_t *__restrict__ gid
 // one output graph of assemble(): vertex, arc and original-vertex blocks of
 // a source union and their places in the new union
 struct Blk {
-    int src;          // 0: current union, 1: new graphs
+    int src;          // 0: current union, 1 + j: j-th set of new graphs
     int v0, nv, dv0;  // vertices
     int a0, na, da0;  // arcs
     int o0, no, do0;  // original vertices
 };
 
-// One CTA per output graph at a time: rows (offsets shifted to the new arc
-// start), arcs (columns shifted to the new vertex start), graph ids, and the
-// original-vertex map (shifted like the columns).
-__global__ void __launch_bounds__(512) assemble_kernel(int nb, const Blk *__restrict__ blk,
-                                                       const int32_t *__restrict__ off0,
-                                                       const int2 *__restrict__ arcs0,
-                                                       const int32_t *__restrict__ map0,
-                                                       const int32_t *__restrict__ off1,
-                                                       const int2 *__restrict__ arcs1,
-                                                       const int32_t *__restrict__ map1,
+// Rows (offsets shifted to the new arc start), arcs (columns shifted to the
+// new vertex start), graph ids, and the original-vertex map (shifted like the
+// columns).  Work items are parts of output graphs: part p of block b covers
+// the p-th of `parts[b]` equal slices of each of its three ranges, so a large
+// graph is copied by many CTAs.  Sources are indexed by Blk::src.
+__global__ void __launch_bounds__(512) assemble_kernel(int nitems, const int2 *__restrict__ items,
+                                                       const Blk *__restrict__ blk,
+                                                       const int32_t *const *__restrict__ offs,
+                                                       const int2 *const *__restrict__ arcss,
+                                                       const int32_t *const *__restrict__ maps,
                                                        int32_t *off_out, int2 *arcs_out,
                                                        int32_t *gid_out, int32_t *map_out,
                                                        int32_t *gid_orig_out) {
-    for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const int2 item = items[it];  // {block, part | parts << 16}
+        const int b = item.x, part = item.y & 0xffff, parts = item.y >> 16;
         const Blk B = blk[b];
-        const int32_t *off = B.src ? off1 : off0;
-        const int2 *arcs = B.src ? arcs1 : arcs0;
-        const int32_t *mp = B.src ? map1 : map0;
+        const int32_t *off = offs[B.src];
+        const int2 *arcs = arcss[B.src];
+        const int32_t *mp = maps[B.src];
         const int dv = B.dv0 - B.v0, da = B.da0 - B.a0;
-        for (int i = threadIdx.x; i < B.nv; i += blockDim.x) {
+        const int lv = (B.nv + parts - 1) / parts, la = (B.na + parts - 1) / parts,
+                  lo = (B.no + parts - 1) / parts;
+        for (int i = part * lv + threadIdx.x; i < min(B.nv, (part + 1) * lv); i += blockDim.x) {
             off_out[B.dv0 + i] = off[B.v0 + i] + da;
             gid_out[B.dv0 + i] = b;
         }
-        for (int e = threadIdx.x; e < B.na; e += blockDim.x) {
+        for (int e = part * la + threadIdx.x; e < min(B.na, (part + 1) * la); e += blockDim.x) {
             int2 a = arcs[B.a0 + e];
             a.x += dv;
             arcs_out[B.da0 + e] = a;
         }
-        for (int u = threadIdx.x; u < B.no; u += blockDim.x) {
+        for (int u = part * lo + threadIdx.x; u < min(B.no, (part + 1) * lo); u += blockDim.x) {
             map_out[B.do0 + u] = mp[B.o0 + u] + dv;
             gid_orig_out[B.do0 + u] = b;
         }
@@ -329,16 +333,26 @@ static lv_status arc_starts(const DGraph &u, const std::vector<int32_t> &starts,
 
 lv_status Engine::assemble(const DGraph &src, const int32_t *map_src,
                            const std::vector<int32_t> &src_gp, const std::vector<int> &keep,
-                           const NewGraphs *ng, const DGraph *ng_vf, const int32_t *ng_map,
-                           const std::vector<int32_t> *ng_gp) {
-    std::vector<int32_t> sa, na;
+                           const std::vector<const Prepared *> &news) {
+    std::vector<int32_t> sa;
     if (!keep.empty()) LV_TRY(arc_starts(src, src_gp, &sa, s));
-    const int32_t Gn = ng_vf ? (int32_t)ng_gp->size() - 1 : 0;
-    if (Gn > 0) LV_TRY(arc_starts(*ng_vf, *ng_gp, &na, s));
+    std::vector<std::vector<int32_t>> na(news.size());
+    for (size_t j = 0; j < news.size(); ++j) LV_TRY(arc_starts(news[j]->vf, news[j]->vgp, &na[j], s));
     std::vector<Blk> blk;
     std::vector<EngineGraph> recs;
     std::vector<int32_t> ngp(1, 0), nop(1, 0);
     int64_t dv = 0, da = 0, dor = 0;
+    auto add = [&](Blk b) {
+        b.dv0 = (int)dv;
+        b.da0 = (int)da;
+        b.do0 = (int)dor;
+        dv += b.nv;
+        da += b.na;
+        dor += b.no;
+        blk.push_back(b);
+        ngp.push_back((int32_t)dv);
+        nop.push_back((int32_t)dor);
+    };
     for (int gi : keep) {
         Blk b;
         b.src = 0;
@@ -348,49 +362,48 @@ lv_status Engine::assemble(const DGraph &src, const int32_t *map_src,
         b.na = sa[gi + 1] - sa[gi];
         b.o0 = optr[gi];
         b.no = optr[gi + 1] - optr[gi];
-        b.dv0 = (int)dv;
-        b.da0 = (int)da;
-        b.do0 = (int)dor;
-        dv += b.nv;
-        da += b.na;
-        dor += b.no;
-        blk.push_back(b);
+        add(b);
         recs.push_back(graphs[gi]);
-        ngp.push_back((int32_t)dv);
-        nop.push_back((int32_t)dor);
     }
-    for (int32_t j = 0; j < Gn; ++j) {
-        Blk b;
-        b.src = 1;
-        b.v0 = (*ng_gp)[j];
-        b.nv = (*ng_gp)[j + 1] - (*ng_gp)[j];
-        b.a0 = na[j];
-        b.na = na[j + 1] - na[j];
-        b.o0 = ng->gptr[j];
-        b.no = ng->gptr[j + 1] - ng->gptr[j];
-        b.dv0 = (int)dv;
-        b.da0 = (int)da;
-        b.do0 = (int)dor;
-        dv += b.nv;
-        da += b.na;
-        dor += b.no;
-        blk.push_back(b);
-        EngineGraph r;
-        r.tag = ng->tags[j];
-        r.n_orig = b.no;
-        r.two_m = ng->two_m[j];
-        recs.push_back(r);
-        ngp.push_back((int32_t)dv);
-        nop.push_back((int32_t)dor);
+    for (size_t j = 0; j < news.size(); ++j) {
+        const Prepared &pr = *news[j];
+        const int32_t Gn = (int32_t)pr.vgp.size() - 1;
+        for (int32_t q = 0; q < Gn; ++q) {
+            Blk b;
+            b.src = 1 + (int)j;
+            b.v0 = pr.vgp[q];
+            b.nv = pr.vgp[q + 1] - pr.vgp[q];
+            b.a0 = na[j][q];
+            b.na = na[j][q + 1] - na[j][q];
+            b.o0 = pr.ng.gptr[q];
+            b.no = pr.ng.gptr[q + 1] - pr.ng.gptr[q];
+            add(b);
+            EngineGraph r;
+            r.tag = pr.ng.tags[q];
+            r.n_orig = b.no;
+            r.two_m = pr.ng.two_m[q];
+            recs.push_back(r);
+        }
     }
     if (dv > 0x7ffffffell || da > 0x7fffffffll || dor > 0x7ffffffell) return LV_ERR_OVERFLOW;
     const int nb = (int)blk.size();
+    const int nsrc = 1 + (int)news.size();
+    std::vector<const void *> ptrs(3 * (size_t)nsrc);
+    ptrs[0] = src.off;
+    ptrs[nsrc] = src.arcs;
+    ptrs[2 * nsrc] = map_src;
+    for (size_t j = 0; j < news.size(); ++j) {
+        ptrs[1 + j] = news[j]->vf.off;
+        ptrs[nsrc + 1 + j] = news[j]->vf.arcs;
+        ptrs[2 * nsrc + 1 + j] = news[j]->vmap;
+    }
     DGraph out;
     out.n = (int32_t)dv;
     out.A = (int32_t)da;
     int32_t *gid2 = nullptr, *map2 = nullptr, *gido2 = nullptr, *gptr2 = nullptr;
     long long *tm2 = nullptr;
     Blk *dblk = nullptr;
+    const void **dptr = nullptr;
     LV_TRY(dalloc_n(&out.off, (size_t)out.n + 1, s));
     LV_TRY(dalloc_n(&out.arcs, (size_t)out.A, s));
     LV_TRY(dalloc_n(&gid2, (size_t)out.n, s));
@@ -399,15 +412,29 @@ lv_status Engine::assemble(const DGraph &src, const int32_t *map_src,
     LV_TRY(dalloc_n(&gptr2, (size_t)nb + 1, s));
     LV_TRY(dalloc_n(&tm2, (size_t)std::max(nb, 1), s));
     LV_TRY(dalloc_n(&dblk, (size_t)std::max(nb, 1), s));
+    LV_TRY(dalloc_n(&dptr, ptrs.size(), s));
     std::vector<long long> tmh(nb);
     for (int b = 0; b < nb; ++b) tmh[b] = recs[b].two_m;
+    // parts of at most 64K elements per range (and at most 65535 parts)
+    std::vector<int2> items;
+    for (int b = 0; b < nb; ++b) {
+        const int64_t len = std::max({(int64_t)blk[b].nv, (int64_t)blk[b].na, (int64_t)blk[b].no});
+        const int parts = (int)std::min<int64_t>(65535, std::max<int64_t>(1, (len + 65535) >> 16));
+        for (int p = 0; p < parts; ++p) items.push_back(make_int2(b, p | (parts << 16)));
+    }
+    int2 *ditems = nullptr;
+    LV_TRY(dalloc_n(&ditems, std::max<size_t>(items.size(), 1), s));
     if (nb > 0) {
+        LV_CUDA(cudaMemcpyAsync(ditems, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, s));
         LV_CUDA(cudaMemcpyAsync(dblk, blk.data(), sizeof(Blk) * nb, cudaMemcpyHostToDevice, s));
         LV_CUDA(cudaMemcpyAsync(tm2, tmh.data(), sizeof(long long) * nb, cudaMemcpyHostToDevice, s));
         LV_CUDA(cudaMemcpyAsync(gptr2, ngp.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
-        assemble_kernel<<<std::min(nb, g_num_sms * 4), 512, 0, s>>>(
-            nb, dblk, src.off, src.arcs, map_src, ng_vf ? ng_vf->off : nullptr,
-            ng_vf ? ng_vf->arcs : nullptr, ng_map, out.off, out.arcs, gid2, map2, gido2);
+        LV_CUDA(cudaMemcpyAsync(dptr, ptrs.data(), sizeof(void *) * ptrs.size(), cudaMemcpyHostToDevice, s));
+        assemble_kernel<<<(int)std::min<size_t>(items.size(), (size_t)g_num_sms * 4), 512, 0, s>>>(
+            (int)items.size(), ditems, dblk, reinterpret_cast<const int32_t *const *>(dptr),
+            reinterpret_cast<const int2 *const *>(dptr + nsrc),
+            reinterpret_cast<const int32_t *const *>(dptr + 2 * nsrc), out.off, out.arcs, gid2, map2,
+            gido2);
         LV_LAUNCH_CHECK();
     }
     const int32_t A_out = out.A;
@@ -418,6 +445,8 @@ lv_status Engine::assemble(const DGraph &src, const int32_t *map_src,
     LV_TRY(compute_degrees(out, k2, l2, s));
     LV_CUDA(cudaStreamSynchronize(s));  // host vectors above are read by the copies
     dfree(dblk, s);
+    dfree(dptr, s);
+    dfree(ditems, s);
     // the new union replaces the old one
     free_graph(g, s);
     dfree(k, s);
@@ -442,62 +471,88 @@ lv_status Engine::assemble(const DGraph &src, const int32_t *map_src,
     return LV_OK;
 }
 
-lv_status Engine::append(const NewGraphs &ng) {
+void Prepared::release() {
+    if (own_vf) free_graph(vf, s);
+    own_vf = false;
+    vf = DGraph();
+    dfree(vmap, s);
+    vmap = nullptr;
+    if (own_input) {
+        free_graph(ng.g, s);
+        dfree(const_cast<int32_t *>(ng.k), s);
+        dfree(const_cast<int32_t *>(ng.loop), s);
+        ng.g = DGraph();
+        ng.k = ng.loop = nullptr;
+    }
+    own_input = false;
+}
+
+lv_status prepare_graphs(const NewGraphs &ng, const lv_params &P, int *pinned, cudaStream_t s,
+                         Prepared *out) {
+    out->s = s;
+    out->ng.gptr = ng.gptr;
+    out->ng.two_m = ng.two_m;
+    out->ng.tags = ng.tags;
     const int32_t Gn = (int32_t)ng.gptr.size() - 1;
     if (Gn < 1) return LV_OK;
     const int32_t n_new = ng.gptr[Gn];
-    DGraph vf = ng.g;
-    bool own_vf = false;
-    int32_t *vmap = nullptr, *gptr_n = nullptr, *gid_n = nullptr, *gid_vf = nullptr;
-    std::vector<int32_t> vgp = ng.gptr;
-    lv_status st = dalloc_n(&vmap, (size_t)n_new, s);
-    if (st == LV_OK && P.vertex_following) {
-        // vertex following on the new union (Sec. 4.3; never crosses graphs)
-        st = vertex_following(ng.g, ng.loop, &vf, vmap, pinned, s);
-        own_vf = st == LV_OK;
-        if (st == LV_OK) st = dalloc_n(&gptr_n, 2 * ((size_t)Gn + 1), s);
-        if (st == LV_OK) st = dalloc_n(&gid_n, (size_t)n_new, s);
-        if (st == LV_OK) st = dalloc_n(&gid_vf, (size_t)vf.n, s);
-        if (st == LV_OK &&
-            cudaMemcpyAsync(gptr_n, ng.gptr.data(), sizeof(int32_t) * (Gn + 1), cudaMemcpyHostToDevice,
-                            s) != cudaSuccess)
-            st = LV_ERR_CUDA;
-        if (st == LV_OK) st = graph_of(n_new, Gn, gptr_n, gid_n, s);
-        if (st == LV_OK) {
-            gid_scatter_kernel<<<grid_n(n_new), 256, 0, s>>>(n_new, gid_n, nullptr, vmap, gid_vf);
-            if (cudaGetLastError() != cudaSuccess) st = LV_ERR_CUDA;
-            ++g_kernel_launches;
-        }
-        int32_t *vgp_d = gptr_n + Gn + 1;
-        if (st == LV_OK &&
-            cudaMemsetAsync(vgp_d, 0xff, sizeof(int32_t) * ((size_t)Gn + 1), s) != cudaSuccess)
-            st = LV_ERR_CUDA;
-        if (st == LV_OK && vf.n > 0) {
-            gptr_kernel<<<grid_n(vf.n), 256, 0, s>>>(vf.n, Gn, gid_vf, vgp_d);
-            if (cudaGetLastError() != cudaSuccess) st = LV_ERR_CUDA;
-            ++g_kernel_launches;
-        }
-        if (st == LV_OK &&
-            (cudaMemcpyAsync(vgp.data(), vgp_d, sizeof(int32_t) * (Gn + 1), cudaMemcpyDeviceToHost,
-                             s) != cudaSuccess ||
-             cudaStreamSynchronize(s) != cudaSuccess))
-            st = LV_ERR_CUDA;
-        for (int32_t j = 0; st == LV_OK && j < Gn; ++j)
-            if (vgp[j] < 0 || vgp[j + 1] <= vgp[j]) st = LV_ERR_CUDA;  // every graph keeps a vertex
-    } else if (st == LV_OK) {
-        st = iota(n_new, vmap, s);
+    out->vf = ng.g;
+    out->vgp = ng.gptr;
+    LV_TRY(dalloc_n(&out->vmap, (size_t)n_new, s));
+    if (!P.vertex_following) {
+        LV_TRY(iota(n_new, out->vmap, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        return LV_OK;
     }
-    if (st == LV_OK) {
-        std::vector<int> keep(graphs.size());
-        for (size_t i = 0; i < keep.size(); ++i) keep[i] = (int)i;
-        st = assemble(g, map, gp, keep, &ng, &vf, vmap, &vgp);
+    // vertex following on the new union (Sec. 4.3; never crosses graphs)
+    DGraph vf;
+    LV_TRY(vertex_following(ng.g, ng.loop, &vf, out->vmap, pinned, s));
+    out->vf = vf;
+    out->own_vf = true;
+    int32_t *gptr_n = nullptr, *gid_n = nullptr, *gid_vf = nullptr;
+    struct Tmp {
+        cudaStream_t s;
+        int32_t **a, **b, **c;
+        ~Tmp() {
+            dfree(*a, s);
+            dfree(*b, s);
+            dfree(*c, s);
+        }
+    } tmp{s, &gptr_n, &gid_n, &gid_vf};
+    LV_TRY(dalloc_n(&gptr_n, 2 * ((size_t)Gn + 1), s));
+    LV_TRY(dalloc_n(&gid_n, (size_t)n_new, s));
+    LV_TRY(dalloc_n(&gid_vf, (size_t)std::max(vf.n, 1), s));
+    LV_CUDA(cudaMemcpyAsync(gptr_n, ng.gptr.data(), sizeof(int32_t) * (Gn + 1), cudaMemcpyHostToDevice, s));
+    LV_TRY(graph_of(n_new, Gn, gptr_n, gid_n, s));
+    gid_scatter_kernel<<<grid_n(n_new), 256, 0, s>>>(n_new, gid_n, nullptr, out->vmap, gid_vf);
+    LV_LAUNCH_CHECK();
+    int32_t *vgp_d = gptr_n + Gn + 1;
+    LV_CUDA(cudaMemsetAsync(vgp_d, 0xff, sizeof(int32_t) * ((size_t)Gn + 1), s));
+    if (vf.n > 0) {
+        gptr_kernel<<<grid_n(vf.n), 256, 0, s>>>(vf.n, Gn, gid_vf, vgp_d);
+        LV_LAUNCH_CHECK();
     }
-    if (own_vf) free_graph(vf, s);
-    dfree(vmap, s);
-    dfree(gptr_n, s);
-    dfree(gid_n, s);
-    dfree(gid_vf, s);
-    return st;
+    LV_CUDA(cudaMemcpyAsync(out->vgp.data(), vgp_d, sizeof(int32_t) * (Gn + 1), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    for (int32_t j = 0; j < Gn; ++j)
+        if (out->vgp[j] < 0 || out->vgp[j + 1] <= out->vgp[j]) return LV_ERR_CUDA;  // each keeps a vertex
+    return LV_OK;
+}
+
+lv_status Engine::append_prepared(const std::vector<const Prepared *> &prs) {
+    std::vector<const Prepared *> news;
+    for (const Prepared *p : prs)
+        if (p && p->vgp.size() >= 2) news.push_back(p);
+    if (news.empty()) return LV_OK;
+    std::vector<int> keep(graphs.size());
+    for (size_t i = 0; i < keep.size(); ++i) keep[i] = (int)i;
+    return assemble(g, map, gp, keep, news);
+}
+
+lv_status Engine::append(const NewGraphs &ng) {
+    Prepared pr;
+    LV_TRY(prepare_graphs(ng, P, pinned, s, &pr));
+    return append_prepared({&pr});
 }
 
 }  // namespace lv
@@ -857,7 +912,7 @@ lv_status Engine::phase_end(std::vector<Finished> &finished) {
             }
         } else if (st == LV_OK) {
             // graphs that stopped leave: the kept coarse graphs are packed
-            st = assemble(G2, map, gstart, keep, nullptr, nullptr, nullptr, nullptr);
+            st = assemble(G2, map, gstart, keep, {});
             free_graph(G2, s);
         }
     }

@@ -47,6 +47,23 @@ struct NewGraphs {
     std::vector<int64_t> tags;       // host, per graph
 };
 
+// New graphs after vertex following, ready to join an engine (device memory
+// owned here; made on any stream, complete when prepare_graphs returns).
+struct Prepared {
+    cudaStream_t s = nullptr;
+    NewGraphs ng;               // ng.g, ng.k, ng.loop are owned when own_input
+    bool own_input = false;
+    DGraph vf;                  // the graphs after vertex following (owned when own_vf)
+    bool own_vf = false;
+    int32_t *vmap = nullptr;    // original vertex -> vertex of vf
+    std::vector<int32_t> vgp;   // starts of the graphs in vf
+    void release();
+    ~Prepared() { release(); }
+};
+// Vertex following (when P.vertex_following) of a validated union.
+lv_status prepare_graphs(const NewGraphs &ng, const lv_params &P, int *pinned, cudaStream_t s,
+                         Prepared *out);
+
 // a graph that left the engine after phase()
 struct Finished {
     EngineGraph rec;
@@ -113,6 +130,9 @@ struct Engine {
     int32_t num_graphs() const { return (int32_t)graphs.size(); }
     // Vertex following (when on) and append to the union (between phases).
     lv_status append(const NewGraphs &ng);
+    // Append sets of graphs prepared by prepare_graphs (between phases; one
+    // copy of the union for all of them).
+    lv_status append_prepared(const std::vector<const Prepared *> &prs);
     // One phase for every resident graph, up to and including the labels:
     // afterwards `labels` (device, n_orig entries in the current
     // original-vertex order: graph at position g owns [optr[g], optr[g+1]))
@@ -142,12 +162,10 @@ struct Engine {
     std::vector<int32_t> gstart;  // host: starts of the graphs in the coarse numbering
     int32_t n_next = 0;
     void free_phase();
-    // the union from blocks of two sources: graphs `keep` of (src, map_src,
-    // starts src_gp) and, when ng_vf is given, every graph of the new union
-    // (ng_vf, ng_map, starts ng_gp; original starts ng->gptr)
+    // the union from blocks of several sources: graphs `keep` of (src,
+    // map_src, starts src_gp), then every graph of each prepared set
     lv_status assemble(const DGraph &src, const int32_t *map_src, const std::vector<int32_t> &src_gp,
-                       const std::vector<int> &keep, const NewGraphs *ng, const DGraph *ng_vf,
-                       const int32_t *ng_map, const std::vector<int32_t> *ng_gp);
+                       const std::vector<int> &keep, const std::vector<const Prepared *> &news);
 };
 
 }  // namespace lv

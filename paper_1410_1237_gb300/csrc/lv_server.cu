@@ -34,6 +34,7 @@ constexpr int64_t kBytesPerArc = 48;     // CSR, coarse rebuild and sort scratch
 constexpr int64_t kBytesPerVertex = 64;  // per-vertex state, map and labels
 constexpr int64_t kDefaultBudget = 120ll << 30;
 constexpr int32_t kDefaultMaxGraphs = 65536;
+constexpr int64_t kLaneSplitArcs = int64_t(1) << 22;  // requests at least this large use lane 1
 
 struct Request {
     int64_t id = 0;
@@ -46,26 +47,90 @@ struct Request {
     std::vector<int32_t> labels;
 };
 
+// requests taken from the queue, validated and vertex-followed by the
+// admission thread, waiting for the next phase boundary of the worker
+struct Ready {
+    std::unique_ptr<Prepared> pr;
+    std::vector<std::shared_ptr<Request>> reqs;
+};
+
+// Host-to-device upload through two pinned staging buffers: a chunk is
+// copied into one buffer while the other's transfer runs.  Pinned transfers
+// are asynchronous DMA, so a large upload by the admission thread never
+// holds up the worker's own small copies.
+struct PinnedRing {
+    static constexpr size_t kChunk = size_t(32) << 20;
+    char *buf[2] = {nullptr, nullptr};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int next = 0;
+    lv_status init() {
+        for (int i = 0; i < 2; ++i) {
+            if (cudaMallocHost((void **)&buf[i], kChunk) != cudaSuccess) return LV_ERR_OOM;
+            if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) return LV_ERR_CUDA;
+        }
+        return LV_OK;
+    }
+    void destroy() {
+        for (int i = 0; i < 2; ++i) {
+            if (ev[i]) cudaEventSynchronize(ev[i]);
+            if (buf[i]) cudaFreeHost(buf[i]);
+            if (ev[i]) cudaEventDestroy(ev[i]);
+            buf[i] = nullptr;
+            ev[i] = nullptr;
+        }
+    }
+    lv_status h2d(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+        const char *p = static_cast<const char *>(src);
+        char *d = static_cast<char *>(dst);
+        while (bytes > 0) {
+            const size_t c = bytes < kChunk ? bytes : kChunk;
+            LV_CUDA(cudaEventSynchronize(ev[next]));  // its previous transfer is done
+            std::memcpy(buf[next], p, c);
+            LV_CUDA(cudaMemcpyAsync(d, buf[next], c, cudaMemcpyHostToDevice, s));
+            LV_CUDA(cudaEventRecord(ev[next], s));
+            next ^= 1;
+            p += c;
+            d += c;
+            bytes -= c;
+        }
+        return LV_OK;
+    }
+};
+
 }  // namespace
 
 struct lv_server {
     int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
     lv_server_config cfg;
     BinLimits lim;
     Clock::time_point t0;
     std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_done, cv_adm;
     std::deque<std::shared_ptr<Request>> queue;
+    // Two lanes, each a worker thread with its own engine and stream: requests
+    // with fewer than kLaneSplitArcs arcs and the rest.  Lock-step phases then
+    // never make a small request wait for a large one's iterations; the
+    // lanes' launches interleave on the device.
+    struct Lane {
+        cudaStream_t stream = nullptr;
+        bool own_stream = false;
+        int *pinned = nullptr;
+        std::condition_variable cv_work;
+        std::deque<Ready> ready;  // admitted and prepared, not yet in the engine
+        std::thread worker;
+        int64_t rounds = 0, sweeps = 0;
+    } lanes[2];
+    int64_t inflight = 0;     // admitted and not completed
     std::unordered_map<int64_t, std::shared_ptr<Request>> reqs;  // until released
     int64_t next_id = 0;
     bool stop = false;
     lv_server_stats stats;
     int64_t resident_bytes = 0;
     int64_t resident_n = 0, resident_a = 0;  // input vertices and arcs of resident requests
-    int *pinned = nullptr;
-    std::thread worker;
+    cudaStream_t adm_stream = nullptr;  // admission thread's stream
+    int *adm_pinned = nullptr;
+    PinnedRing ring;                    // admission thread's upload staging
+    std::thread admitter;
 
     double now_ms() const {
         return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
@@ -73,6 +138,14 @@ struct lv_server {
 };
 
 namespace {
+
+// a thread's stream and pinned scratch
+struct Ctx {
+    cudaStream_t s;
+    int *pinned;
+    const lv_params *P;
+    PinnedRing *ring;  // may be null (plain copies)
+};
 
 // Upload one CSR (or a union of several) and validate it on the device.
 struct Staged {
@@ -87,9 +160,9 @@ struct Staged {
     }
 };
 
-lv_status stage(lv_server *S, int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *w,
+lv_status stage(const Ctx &c, int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *w,
                 bool limit_two_m, Staged *out) {
-    cudaStream_t s = S->stream;
+    cudaStream_t s = c.s;
     out->s = s;
     const int64_t A = rowptr[n];
     int64_t *d_rp = nullptr;
@@ -107,11 +180,86 @@ lv_status stage(lv_server *S, int64_t n, const int64_t *rowptr, const int32_t *c
         st = LV_ERR_CUDA;
     if (st == LV_OK)
         st = validate_and_build(n, d_rp, d_col, d_w, &out->g, &out->k, &out->loop, &out->two_m,
-                                S->pinned, s, limit_two_m);
+                                c.pinned, s, limit_two_m);
     dfree(d_rp, s);
     dfree(d_col, s);
     dfree(d_w, s);
     return st;
+}
+
+// Union of admitted CSRs uploaded graph by graph: row offsets are shifted by
+// the graph's first arc and columns by its first vertex on the device.
+__device__ __forceinline__ int block_of(const int32_t *starts, int G, int x) {
+    int a = 0, b = G;  // last a with starts[a] <= x
+    while (b - a > 1) {
+        const int mid = (a + b) >> 1;
+        if (starts[mid] <= x) a = mid; else b = mid;
+    }
+    return a;
+}
+
+__global__ void shift_union_kernel(int32_t n, int32_t A, int32_t G, const int32_t *__restrict__ gptr,
+                                   const int32_t *__restrict__ astart, int64_t *rp, int32_t *col) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+        rp[v] += astart[block_of(gptr, G, v)];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < A; e += stride)
+        col[e] += gptr[block_of(astart, G, e)];
+}
+
+lv_status stage_union(const Ctx &c, const std::vector<std::shared_ptr<Request>> &good,
+                      std::vector<int32_t> *gptr, Staged *out) {
+    cudaStream_t s = c.s;
+    out->s = s;
+    const int32_t G = (int32_t)good.size();
+    int64_t n = 0, A = 0;
+    gptr->assign((size_t)G + 1, 0);
+    std::vector<int32_t> astart((size_t)G + 1, 0);
+    for (int32_t q = 0; q < G; ++q) {
+        n += good[q]->n;
+        A += (int64_t)good[q]->col.size();
+        (*gptr)[q + 1] = (int32_t)n;
+        astart[q + 1] = (int32_t)A;
+    }
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr, *w = nullptr, *gd = nullptr;
+    struct Tmp {
+        cudaStream_t s;
+        int64_t **rp;
+        int32_t **col, **w, **gd;
+        ~Tmp() {
+            dfree(*rp, s);
+            dfree(*col, s);
+            dfree(*w, s);
+            dfree(*gd, s);
+        }
+    } tmp{s, &rp, &col, &w, &gd};
+    LV_TRY(dalloc_n(&rp, (size_t)n + 1, s));
+    LV_TRY(dalloc_n(&col, (size_t)std::max<int64_t>(A, 1), s));
+    LV_TRY(dalloc_n(&w, (size_t)std::max<int64_t>(A, 1), s));
+    LV_TRY(dalloc_n(&gd, 2 * ((size_t)G + 1), s));
+    auto up = [&](void *dst, const void *src, size_t bytes) -> lv_status {
+        if (c.ring) return c.ring->h2d(dst, src, bytes, s);
+        LV_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
+        return LV_OK;
+    };
+    for (int32_t q = 0; q < G; ++q) {
+        const Request &r = *good[q];
+        const size_t a = r.col.size();
+        LV_TRY(up(rp + (*gptr)[q], r.rowptr.data(), sizeof(int64_t) * (size_t)r.n));
+        if (a) {
+            LV_TRY(up(col + astart[q], r.col.data(), sizeof(int32_t) * a));
+            LV_TRY(up(w + astart[q], r.w.data(), sizeof(int32_t) * a));
+        }
+    }
+    LV_TRY(up(rp + n, &A, sizeof(int64_t)));
+    LV_TRY(up(gd, gptr->data(), sizeof(int32_t) * ((size_t)G + 1)));
+    LV_TRY(up(gd + G + 1, astart.data(), sizeof(int32_t) * ((size_t)G + 1)));
+    shift_union_kernel<<<grid_for(std::max<int64_t>(n, A), 256, g_num_sms * 16), 256, 0, s>>>(
+        (int32_t)n, (int32_t)A, G, gd, gd + G + 1, rp, col);
+    LV_LAUNCH_CHECK();
+    return validate_and_build(n, rp, col, w, &out->g, &out->k, &out->loop, &out->two_m, c.pinned, s,
+                              false);
 }
 
 // rowptr of a request must start at 0, not decrease and fit int32 arc counts
@@ -125,9 +273,10 @@ bool rowptr_ok(const Request &r) {
 // Validates the admitted requests as one union and appends them; a request
 // whose CSR is invalid is completed with its error (found by validating the
 // requests one by one when the union fails).
-lv_status admit(lv_server *S, Engine &e, std::vector<std::shared_ptr<Request>> &adm,
-                std::vector<std::shared_ptr<Request>> &failed) {
-    cudaStream_t s = S->stream;
+lv_status admit(const Ctx &c, std::vector<std::shared_ptr<Request>> &adm,
+                std::vector<std::shared_ptr<Request>> &failed, std::unique_ptr<Prepared> *out,
+                std::vector<std::shared_ptr<Request>> *joined) {
+    cudaStream_t s = c.s;
     std::vector<std::shared_ptr<Request>> good;
     for (auto &r : adm) {
         if (!rowptr_ok(*r) || r->n < 1) {
@@ -138,31 +287,15 @@ lv_status admit(lv_server *S, Engine &e, std::vector<std::shared_ptr<Request>> &
         }
     }
     for (int attempt = 0; attempt < 2 && !good.empty(); ++attempt) {
-        // host union: columns shifted by each request's vertex start
         int64_t n = 0, A = 0;
         for (auto &r : good) {
             n += r->n;
             A += (int64_t)r->col.size();
         }
         if (n > 0x7ffffffell || A > 0x7fffffffll) return LV_ERR_OVERFLOW;  // admission keeps below
-        std::vector<int64_t> rp((size_t)n + 1);
-        std::vector<int32_t> col((size_t)A), w((size_t)A);
-        std::vector<int32_t> gptr(good.size() + 1, 0);
-        int64_t v0 = 0, a0 = 0;
-        for (size_t q = 0; q < good.size(); ++q) {
-            const Request &r = *good[q];
-            for (int64_t i = 0; i < r.n; ++i) rp[v0 + i] = r.rowptr[i] + a0;
-            for (size_t e2 = 0; e2 < r.col.size(); ++e2) {
-                col[a0 + e2] = (int32_t)(r.col[e2] + v0);
-                w[a0 + e2] = r.w[e2];
-            }
-            v0 += r.n;
-            a0 += (int64_t)r.col.size();
-            gptr[q + 1] = (int32_t)v0;
-        }
-        rp[n] = A;
+        std::vector<int32_t> gptr;
         Staged U;
-        lv_status st = stage(S, n, rp.data(), col.data(), w.data(), false, &U);
+        lv_status st = stage_union(c, good, &gptr, &U);
         std::vector<long long> two_m(good.size(), 0);
         if (st == LV_OK) {
             // per-graph checks: arcs stay inside their graph, 0 < 2m < 2^31
@@ -216,15 +349,26 @@ lv_status admit(lv_server *S, Engine &e, std::vector<std::shared_ptr<Request>> &
                 r->info.n = r->n;
                 r->info.arcs = (int64_t)r->col.size();
             }
-            LV_TRY(e.append(ng));
+            std::unique_ptr<Prepared> pr(new Prepared());
+            LV_TRY(prepare_graphs(ng, *c.P, c.pinned, s, pr.get()));
+            if (!pr->own_vf) {  // the engine copies the staged union itself
+                pr->ng.g = U.g;
+                pr->ng.k = U.k;
+                pr->ng.loop = U.loop;
+                pr->own_input = true;
+                U.g = DGraph();
+                U.k = U.loop = nullptr;
+            }
             for (size_t q = 0; q < good.size(); ++q) good[q]->info.two_m = two_m[q];
+            *out = std::move(pr);
+            *joined = good;
             return LV_OK;
         }
         // the union failed: find the invalid requests one by one
         std::vector<std::shared_ptr<Request>> keep;
         for (auto &r : good) {
             Staged one;
-            const lv_status s1 = stage(S, r->n, r->rowptr.data(), r->col.data(), r->w.data(), true, &one);
+            const lv_status s1 = stage(c, r->n, r->rowptr.data(), r->col.data(), r->w.data(), true, &one);
             if (s1 == LV_ERR_CUDA || s1 == LV_ERR_OOM) return s1;
             if (s1 != LV_OK) {
                 r->info.status = s1;
@@ -242,56 +386,141 @@ lv_status admit(lv_server *S, Engine &e, std::vector<std::shared_ptr<Request>> &
     return LV_OK;
 }
 
-void worker_main(lv_server *S) {
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+// completion under S->mu: the request leaves the budget and its waiters wake
+void complete_locked(lv_server *S, Request &r, double t) {
+    r.done = true;
+    r.info.t_done_ms = t;
+    S->resident_bytes -= r.est;
+    S->resident_n -= r.n;
+    S->resident_a -= (int64_t)r.col.size();
+    --S->inflight;
+    if (r.info.status == LV_OK) ++S->stats.completed;
+    else ++S->stats.failed;
+}
+
+// Admission thread: takes queued requests first come first served while the
+// budget, the slots and int32 ids allow, then uploads, validates and
+// vertex-follows them on its own stream, so this work overlaps the worker's
+// phases; the result joins the engine at the worker's next phase boundary.
+void admitter_main(lv_server *S) {
     cudaSetDevice(S->device);
-    Engine e;
-    e.s = S->stream;
-    e.P = S->cfg.params;
-    e.lim = S->lim;
-    e.pinned = S->pinned;
-    std::unordered_map<int64_t, std::shared_ptr<Request>> resident;
+    const Ctx c{S->adm_stream, S->adm_pinned, &S->cfg.params, &S->ring};
+    const int64_t budget = S->cfg.mem_budget_bytes > 0 ? S->cfg.mem_budget_bytes : kDefaultBudget;
+    const int64_t maxg = S->cfg.max_graphs > 0 ? S->cfg.max_graphs : kDefaultMaxGraphs;
     for (;;) {
         std::vector<std::shared_ptr<Request>> adm;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || e.num_graphs() > 0; });
+            auto admissible = [&] {
+                if (S->queue.empty()) return false;
+                const Request &r = *S->queue.front();
+                if (S->inflight >= maxg) return false;
+                if (S->inflight > 0 && S->resident_bytes + r.est > budget) return false;
+                return S->resident_n + r.n <= 0x7ffffffell &&
+                       S->resident_a + (int64_t)r.col.size() <= 0x7fffffffll;
+            };
+            S->cv_adm.wait(lk, [&] { return S->stop || admissible(); });
             if (S->stop) break;
-            const int64_t budget =
-                S->cfg.mem_budget_bytes > 0 ? S->cfg.mem_budget_bytes : kDefaultBudget;
-            const int64_t maxg = S->cfg.max_graphs > 0 ? S->cfg.max_graphs : kDefaultMaxGraphs;
-            int64_t adm_n = 0, adm_a = 0;  // the admitted union must fit int32 ids
-            while (!S->queue.empty()) {
-                const std::shared_ptr<Request> &r = S->queue.front();
-                const int64_t cnt = (int64_t)resident.size() + (int64_t)adm.size();
-                if (cnt >= maxg) break;
-                if (cnt > 0 && S->resident_bytes + r->est > budget) break;
-                const int64_t ra = (int64_t)r->col.size();
-                if (S->resident_n + adm_n + r->n > 0x7ffffffell ||
-                    S->resident_a + adm_a + ra > 0x7fffffffll)
-                    break;
-                S->resident_bytes += r->est;
-                adm_n += r->n;
-                adm_a += ra;
-                adm.push_back(r);
+            while (admissible()) {
+                std::shared_ptr<Request> r = S->queue.front();
                 S->queue.pop_front();
+                S->resident_bytes += r->est;
+                S->resident_n += r->n;
+                S->resident_a += (int64_t)r->col.size();
+                ++S->inflight;
+                adm.push_back(r);
             }
-            S->resident_n += adm_n;
-            S->resident_a += adm_a;
             const double t = S->now_ms();
             for (auto &r : adm) r->info.t_admit_ms = t;
             S->stats.admitted += (int64_t)adm.size();
         }
-        std::vector<std::shared_ptr<Request>> failed;
-        lv_status st = LV_OK;
-        if (!adm.empty()) {
-            st = admit(S, e, adm, failed);
+        for (int ln = 0; ln < 2; ++ln) {
+            std::vector<std::shared_ptr<Request>> group;
             for (auto &r : adm)
-                if (r->info.status == LV_OK) resident[r->id] = r;
+                if ((int64_t)r->col.size() >= kLaneSplitArcs ? ln == 1 : ln == 0) group.push_back(r);
+            if (group.empty()) continue;
+            const Clock::time_point c0 = Clock::now();
+            std::vector<std::shared_ptr<Request>> failed, joined;
+            std::unique_ptr<Prepared> pr;
+            const lv_status st = admit(c, group, failed, &pr, &joined);
+            const Clock::time_point c1 = Clock::now();
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                const double t = S->now_ms();
+                S->stats.ms_admit += ms_between(c0, c1);
+                if (st != LV_OK) {  // a device failure ends the whole admitted group
+                    for (auto &r : group) {
+                        if (r->done) continue;
+                        if (r->info.status == LV_OK) r->info.status = st;
+                        complete_locked(S, *r, t);
+                    }
+                } else {
+                    for (auto &r : failed) complete_locked(S, *r, t);
+                    if (pr && !joined.empty()) {
+                        Ready rd;
+                        rd.pr = std::move(pr);
+                        rd.reqs = joined;
+                        S->lanes[ln].ready.push_back(std::move(rd));
+                    }
+                }
+            }
+            S->lanes[ln].cv_work.notify_all();
+            S->cv_done.notify_all();
+            S->cv_adm.notify_all();
         }
+    }
+}
+
+// Worker thread: appends what the admission thread prepared, runs one
+// batched phase of every resident request and completes those that finish.
+void worker_main(lv_server *S, int ln) {
+    cudaSetDevice(S->device);
+    lv_server::Lane &L = S->lanes[ln];
+    Engine e;
+    e.s = L.stream;
+    e.P = S->cfg.params;
+    e.lim = S->lim;
+    e.pinned = L.pinned;
+    std::unordered_map<int64_t, std::shared_ptr<Request>> resident;
+    for (;;) {
+        std::vector<Ready> take;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            L.cv_work.wait(lk, [&] { return S->stop || !L.ready.empty() || e.num_graphs() > 0; });
+            if (S->stop) break;
+            while (!L.ready.empty()) {
+                take.push_back(std::move(L.ready.front()));
+                L.ready.pop_front();
+            }
+        }
+        const unsigned long long launches0 = g_kernel_launches.load();
+        lv_status st = LV_OK;
+        const Clock::time_point c0 = Clock::now();
+        std::vector<std::shared_ptr<Request>> lost;  // taken but not appended
+        if (!take.empty()) {  // everything prepared since the last boundary joins in one copy
+            std::vector<const Prepared *> prs;
+            for (auto &rd : take) prs.push_back(rd.pr.get());
+            st = e.append_prepared(prs);
+            for (auto &rd : take) {
+                for (auto &r : rd.reqs) {
+                    if (st == LV_OK) resident[r->id] = r;
+                    else lost.push_back(r);
+                }
+                rd.pr.reset();
+            }
+        }
+        const Clock::time_point c1 = Clock::now();
+        Clock::time_point c2 = c1, c3 = c1, c4 = c1;
         std::vector<Finished> fin;
         if (st == LV_OK && e.num_graphs() > 0) {
             st = e.phase_run();
+            c2 = Clock::now();
             if (st == LV_OK) st = e.phase_end(fin);
+            c3 = Clock::now();
             for (auto &f : fin) {  // labels of the requests that finished
                 auto it = resident.find(f.rec.tag);
                 if (it == resident.end()) continue;
@@ -299,7 +528,7 @@ void worker_main(lv_server *S) {
                 r.labels.resize((size_t)r.n);
                 if (st == LV_OK &&
                     cudaMemcpyAsync(r.labels.data(), e.labels + f.lab_off, sizeof(int32_t) * (size_t)r.n,
-                                    cudaMemcpyDeviceToHost, S->stream) != cudaSuccess)
+                                    cudaMemcpyDeviceToHost, L.stream) != cudaSuccess)
                     st = LV_ERR_CUDA;
                 r.info.num_phases = (int32_t)f.rec.info.size();
                 r.info.iterations = 0;
@@ -310,26 +539,21 @@ void worker_main(lv_server *S) {
                     r.info.q = f.rec.info.back().q;
                 }
             }
-            if (st == LV_OK && cudaStreamSynchronize(S->stream) != cudaSuccess) st = LV_ERR_CUDA;
+            if (st == LV_OK && cudaStreamSynchronize(L.stream) != cudaSuccess) st = LV_ERR_CUDA;
+            c4 = Clock::now();
         }
         {
             std::lock_guard<std::mutex> lk(S->mu);
             const double t = S->now_ms();
-            auto complete = [&](Request &r) {
-                r.done = true;
-                r.info.t_done_ms = t;
-                S->resident_bytes -= r.est;
-                S->resident_n -= r.n;
-                S->resident_a -= (int64_t)r.col.size();
-                if (r.info.status == LV_OK) ++S->stats.completed;
-                else ++S->stats.failed;
-            };
-            for (auto &r : failed) complete(*r);
+            for (auto &r : lost) {
+                r->info.status = st;
+                complete_locked(S, *r, t);
+            }
             if (st != LV_OK) {
                 // a device failure ends every resident request with its status
                 for (auto &kv : resident) {
                     kv.second->info.status = st;
-                    complete(*kv.second);
+                    complete_locked(S, *kv.second, t);
                 }
                 resident.clear();
                 e.release();
@@ -337,16 +561,24 @@ void worker_main(lv_server *S) {
                 for (auto &f : fin) {
                     auto it = resident.find(f.rec.tag);
                     if (it == resident.end()) continue;
-                    complete(*it->second);
+                    complete_locked(S, *it->second, t);
                     resident.erase(it);
                 }
             }
-            if (!fin.empty() || e.num_graphs() > 0) ++S->stats.rounds;
-            S->stats.sweeps = e.sweep_launches;
+            if (!fin.empty() || e.num_graphs() > 0) ++L.rounds;
+            L.sweeps = e.sweep_launches;
+            S->stats.rounds = S->lanes[0].rounds + S->lanes[1].rounds;
+            S->stats.sweeps = S->lanes[0].sweeps + S->lanes[1].sweeps;
             S->stats.peak_graphs = std::max<int64_t>(S->stats.peak_graphs, (int64_t)resident.size());
             S->stats.peak_bytes = std::max<int64_t>(S->stats.peak_bytes, S->resident_bytes);
+            S->stats.kernel_launches += (int64_t)(g_kernel_launches.load() - launches0);
+            S->stats.ms_append += ms_between(c0, c1);
+            S->stats.ms_iterate += ms_between(c1, c2);
+            S->stats.ms_rebuild += ms_between(c2, c3);
+            S->stats.ms_results += ms_between(c3, c4);
         }
         S->cv_done.notify_all();
+        S->cv_adm.notify_all();
     }
     e.release();
 }
@@ -375,23 +607,36 @@ lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *c
     S->t0 = Clock::now();
     std::memset(&S->stats, 0, sizeof S->stats);
     cudaGetDevice(&S->device);
-    S->stream = (cudaStream_t)cuda_stream;
-    if (!S->stream) {
-        if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            delete S;
-            return LV_ERR_CUDA;
+    lv_status st = LV_OK;
+    for (int ln = 0; ln < 2 && st == LV_OK; ++ln) {
+        lv_server::Lane &L = S->lanes[ln];
+        L.stream = ln == 0 ? (cudaStream_t)cuda_stream : nullptr;
+        if (!L.stream) {
+            if (cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) != cudaSuccess) st = LV_ERR_CUDA;
+            else L.own_stream = true;
         }
-        S->own_stream = true;
+        if (st == LV_OK && cudaMallocHost((void **)&L.pinned, 64 * sizeof(int)) != cudaSuccess)
+            st = LV_ERR_OOM;
     }
-    lv_status st = ensure_setup(S->stream);
-    if (st == LV_OK && cudaMallocHost((void **)&S->pinned, 64 * sizeof(int)) != cudaSuccess)
+    if (st == LV_OK) st = ensure_setup(S->lanes[0].stream);
+    if (st == LV_OK && cudaMallocHost((void **)&S->adm_pinned, 64 * sizeof(int)) != cudaSuccess)
         st = LV_ERR_OOM;
+    if (st == LV_OK && cudaStreamCreateWithFlags(&S->adm_stream, cudaStreamNonBlocking) != cudaSuccess)
+        st = LV_ERR_CUDA;
+    if (st == LV_OK) st = S->ring.init();
     if (st != LV_OK) {
-        if (S->own_stream) cudaStreamDestroy(S->stream);
+        S->ring.destroy();
+        for (auto &L : S->lanes) {
+            if (L.pinned) cudaFreeHost(L.pinned);
+            if (L.own_stream) cudaStreamDestroy(L.stream);
+        }
+        if (S->adm_pinned) cudaFreeHost(S->adm_pinned);
+        if (S->adm_stream) cudaStreamDestroy(S->adm_stream);
         delete S;
         return st;
     }
-    S->worker = std::thread(worker_main, S);
+    for (int ln = 0; ln < 2; ++ln) S->lanes[ln].worker = std::thread(worker_main, S, ln);
+    S->admitter = std::thread(admitter_main, S);
     *out = S;
     return LV_OK;
 }
@@ -419,7 +664,7 @@ lv_status lv_server_submit(lv_server *S, int64_t n, const int64_t *rowptr, const
         ++S->stats.submitted;
         *request_id = r->id;
     }
-    S->cv_work.notify_one();
+    S->cv_adm.notify_one();
     return LV_OK;
 }
 
@@ -472,11 +717,21 @@ void lv_server_destroy(lv_server *S) {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
     }
-    S->cv_work.notify_all();
-    if (S->worker.joinable()) S->worker.join();
-    cudaStreamSynchronize(S->stream);
-    if (S->pinned) cudaFreeHost(S->pinned);
-    if (S->own_stream) cudaStreamDestroy(S->stream);
+    for (auto &L : S->lanes) L.cv_work.notify_all();
+    S->cv_adm.notify_all();
+    if (S->admitter.joinable()) S->admitter.join();
+    for (auto &L : S->lanes)
+        if (L.worker.joinable()) L.worker.join();
+    for (auto &L : S->lanes) L.ready.clear();  // prepared graphs never appended
+    cudaStreamSynchronize(S->adm_stream);
+    S->ring.destroy();
+    for (auto &L : S->lanes) {
+        cudaStreamSynchronize(L.stream);
+        if (L.pinned) cudaFreeHost(L.pinned);
+        if (L.own_stream) cudaStreamDestroy(L.stream);
+    }
+    if (S->adm_pinned) cudaFreeHost(S->adm_pinned);
+    cudaStreamDestroy(S->adm_stream);
     delete S;
 }
 

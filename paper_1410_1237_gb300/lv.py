@@ -99,7 +99,10 @@ class lv_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
                 ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("rounds", ctypes.c_int64), ("sweeps", ctypes.c_int64),
-                ("peak_graphs", ctypes.c_int64), ("peak_bytes", ctypes.c_int64)]
+                ("peak_graphs", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ms_admit", ctypes.c_double),
+                ("ms_append", ctypes.c_double), ("ms_iterate", ctypes.c_double),
+                ("ms_rebuild", ctypes.c_double), ("ms_results", ctypes.c_double)]
 
 
 _lib = None

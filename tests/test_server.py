@@ -103,8 +103,8 @@ def test_mix_equals_alone(lv):
 
 
 def test_arrivals_while_running_join_later_rounds(lv):
-    """Requests submitted while a large one is on the GPU are admitted at a
-    phase boundary and share its sweeps."""
+    """Requests submitted while a large one is on the GPU are admitted while
+    it runs (small ones in their own lane) and most finish before it."""
     big = gg.planted(1_000_000, 100, 0.0012, 0.000002, 1, 4, seed=77)
     small = request_mix(1, 12)
     want_big = alone(lv, big)
@@ -120,8 +120,9 @@ def test_arrivals_while_running_join_later_rounds(lv):
         check(lv, h, rb, big, want_big)
         for rid, g, w in zip(ids, small, want):
             check(lv, h, rid, g, w)
-        st = lv.lv_server_get_stats(h)
-        assert st.peak_graphs >= 2  # the small ones overlapped the big one
+        done_big = lv.lv_server_result(h, rb)[1].t_done_ms
+        early = sum(lv.lv_server_result(h, rid)[1].t_done_ms < done_big for rid in ids)
+        assert early >= len(ids) // 2
     finally:
         lv.lv_server_destroy(h)
 
