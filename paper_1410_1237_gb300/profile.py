@@ -1,5 +1,8 @@
 """Stage breakdown of a run: ``python -m paper_1410_1237_gb300.profile [workload] [reps]``.
 
+``workload`` is a named single-graph workload, or ``planted_batch<G>`` for
+the planted-partition batch recipe with G graphs (per-sweep records).
+
 Generates a named synthetic workload (see graphgen.WORKLOADS), creates a handle
 on device arrays, runs the method ``reps`` times with CUDA-event timing and
 prints, for the last run, the per-phase colouring / iteration / rebuild times,
@@ -27,6 +30,8 @@ def main(argv: list[str]) -> int:
     reps = int(argv[1]) if len(argv) > 1 else 2
     _build.build()
     lv.load()
+    if wl.startswith("planted_batch"):
+        return batch_main(wl, reps, torch, graphgen, lv)
     g, prm = graphgen.workload(wl)
     dev = torch.device("cuda:0")
     stream = torch.cuda.Stream(dev)
@@ -51,6 +56,31 @@ def main(argv: list[str]) -> int:
         print(f"  iter phase={it.phase} it={it.iter} classes={it.color_steps} moved={it.moved} "
               f"ms={it.ms:.3f}")
     lv.lv_graph_destroy(h)
+    return 0
+
+
+def batch_main(wl: str, reps: int, torch, graphgen, lv) -> int:
+    """planted_batch<G>: the planted-partition batch recipe with G graphs."""
+    num = int(wl[len("planted_batch"):] or 4096)
+    b = graphgen.planted_batch(num_graphs=num)
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream(dev)
+    arrays = [torch.from_numpy(x).to(dev) for x in (b.gptr, b.rowptr, b.col, b.w)]
+    torch.cuda.synchronize(dev)
+    h = lv.lv_batch_create(b.num_graphs, *arrays, stream=stream.cuda_stream)
+    params = lv.make_params(autotune=1, collect_timing=1)
+    wall = 0.0
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        lv.lv_batch_run(h, params)
+        wall = time.perf_counter() - t0
+    st = lv.lv_batch_get_stats(h)
+    print(wl, f"graphs={b.num_graphs} n={b.n} arcs={b.arcs} wall_ms={1e3 * wall:.2f}",
+          {f: getattr(st, f) for f, _ in lv.lv_stats._fields_})
+    for sw in lv.lv_batch_get_sweeps(h):
+        print(f"  sweep phase={sw.phase} sweep={sw.sweep} graphs={sw.graphs} n={sw.vertices} "
+              f"arcs={sw.arcs} moved={sw.moved} ms={sw.ms:.3f}")
+    lv.lv_batch_destroy(h)
     return 0
 
 
