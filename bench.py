@@ -35,6 +35,19 @@ METRIC = "edge visits/s per sweep (whole run, bit-exact labels)"
 UNIT = "edge visits/s"
 BYTES_PER_ARC = 12     # col 4 + w 4 + C[col] 4
 BYTES_PER_VERTEX = 28  # rowptr 8 + C 4 + k 4 + a,|C| of own community 8 + label write 4
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
+# the dominant kernel, from ncu captures of the current kernels; None where
+# no capture applies
+MEASURED_TRAFFIC = {
+    # sweep_persistent_kernel, rmat20 phase 0 iteration 3 (all 232 classes)
+    "rmat20": {"bytes": 325_164_800 + 13_451_520,
+               "scope": "one phase-0 sweep launch (iteration 3, 232 colour classes)"},
+    # batched sweep: traffic / algorithmic bytes of a 512-graph capture
+    # (1,263.0 MB / 914.1 MB), applied to a phase-0 launch of the full batch
+    "planted_batch4096": {"ratio": 1263.0 / 914.1,
+                          "scope": "one phase-0 sweep launch of all 4,096 graphs, scaled by "
+                                   "units from a 512-graph capture"},
+}
 # bounded oracle samples (host-core baseline): the oracle's whole pipeline
 # on the same graph, cut after these many phases / iterations
 CPU_SAMPLE = {"rmat20": dict(max_phases=1, max_iters=3),
@@ -269,6 +282,7 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         pg.barrier()
     torch.cuda.synchronize(dev)
     step_ms, launches, sweep_ms, sweep_bytes, nsweeps = [], 0, 0.0, 0.0, 0
+    st0_arcs = st0_n = 0
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -281,7 +295,9 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         step_ms.append(e0.elapsed_time(e1))
         st = lv.lv_batch_get_stats(h)
         launches += st.kernel_launches
-        for sw in lv.lv_batch_get_sweeps(h):
+        sws = lv.lv_batch_get_sweeps(h)
+        st0_arcs, st0_n = (sws[0].arcs, sws[0].vertices) if sws else (0, 0)
+        for sw in sws:
             if sw.ms > 0:
                 sweep_ms += sw.ms
                 sweep_bytes += BYTES_PER_ARC * sw.arcs + BYTES_PER_VERTEX * sw.vertices
@@ -376,7 +392,13 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         "plain_launches": plain,
         "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": (MEASURED_TRAFFIC[args.workload]["ratio"] *
+                                 (BYTES_PER_ARC * st0_arcs + BYTES_PER_VERTEX * st0_n))
+                     if st0_arcs else None,
+                     "traffic_scope": MEASURED_TRAFFIC[args.workload]["scope"],
+                     "algorithmic_bytes_phase0_launch": BYTES_PER_ARC * st0_arcs +
+                     BYTES_PER_VERTEX * st0_n,
                      "kernel": "batched sweep (persistent launch over all iterating graphs)",
                      "bytes_per_unit": f"{BYTES_PER_ARC} B/arc + {BYTES_PER_VERTEX} B/vertex "
                                        "of the swept graphs",
@@ -711,8 +733,11 @@ def main():
                    "phases": phases, "iterations": stats.total_iterations,
                    "edge_visits_per_step": visits},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
-                     "kernel": "sweep iteration (all class launches of one iteration)",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("bytes"),
+                     "traffic_scope": MEASURED_TRAFFIC.get(args.workload, {}).get("scope"),
+                     "kernel": "sweep_persistent_kernel (one launch per iteration, all colour "
+                               "classes)",
                      "bytes_per_unit": f"{BYTES_PER_ARC} B/arc + {BYTES_PER_VERTEX} B/vertex",
                      "peak_source": f"{peak_src} MEASURED_PEAKS.json hbm_gbs",
                      "sweeps_timed": sweeps},
