@@ -417,7 +417,8 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
 
 
 SERVED_METRIC = "served graphs/s under Poisson arrivals (whole run per request, bit-exact labels)"
-SERVED_PARAMS = dict(vertex_following=1, coloring=0, theta_low=1e-6)  # the server's phases are uncoloured
+SERVED_PARAMS = dict(vertex_following=1, coloring=1, color_cutoff=100_000, theta_low=1e-6,
+                     theta_high=1e-2)  # every heuristic on
 SERVED_BUDGET = 120 << 30
 
 

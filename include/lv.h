@@ -332,9 +332,11 @@ void lv_batch_destroy(lv_batch *b);
  * thread joins them to its running multi-graph engine at its next phase
  * boundary, runs one batched phase of every resident request (their sweeps
  * share launches), and completes the requests whose phase loop stopped.
- * Requests with fewer than 2^22 stored arcs and larger ones go to two such
- * workers (own engines and streams), so small requests never wait for the
- * iterations of large ones.   A
+ * That is lane 0, for requests with fewer than 2^22 stored arcs that would
+ * not colour any phase.  Lane 1 (its own worker and stream) solves the other
+ * requests (large ones, and those with colouring on and at least
+ * color_cutoff vertices) one at a time with the single-graph driver, so small
+ * requests never wait for the iterations of large ones.   A
  * request's CSR and labels stay on the device across its phases.  Each
  * request gets exactly what lv_run gives for it alone with the same
  * parameters, whatever else is resident. */
@@ -346,7 +348,7 @@ typedef struct {
                                  larger than the budget is admitted alone. */
     int32_t max_graphs;       /* resident requests at most; 0 = 65,536 */
     int32_t reserved;
-    lv_params params;         /* for every request; coloring must be 0 */
+    lv_params params;         /* for every request (all heuristics allowed) */
 } lv_server_config;
 
 /* Outcome of one request (times in ms since lv_server_create, host clock). */
@@ -375,9 +377,9 @@ typedef struct {
     double ms_results;    /* ... copying finished requests' labels to the host */
 } lv_server_stats;
 
-/* Start a server on the current device.  cuda_stream: the stream for its
- * work (NULL = a stream the server creates).  LV_ERR_ARG for a NULL config,
- * coloring != 0, or invalid parameters. */
+/* Start a server on the current device.  cuda_stream: the stream of lane 0
+ * (NULL = a stream the server creates; lane 1 and admission always use their
+ * own).  LV_ERR_ARG for a NULL config or invalid parameters. */
 lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *cuda_stream);
 
 /* Queue a request: a CSR under the lv_graph_create contract in HOST memory,

@@ -1,7 +1,8 @@
 // lv_server.cu -- serving with continuous batching (lv.h, "serving").
 //
-// Requests are queued by lv_server_submit (host copies of their CSRs).  One
-// worker thread owns the device work and loops over rounds:
+// Requests are queued by lv_server_submit (host copies of their CSRs).  An
+// admission thread and two lane workers share the device.  Lane 0 (small
+// requests) loops over rounds:
 //   1. admission: queued requests, first come first served, while the
 //      resident requests' estimated footprint stays within the budget and
 //      the slot limit; the admitted CSRs are concatenated into one union,
@@ -10,8 +11,9 @@
 //   2. one batched phase of every resident request (lv_engine.cu);
 //   3. requests whose phase loop stopped leave the engine: their labels are
 //      copied to the host and their waiters are woken.
-// Every request is computed exactly as lv_run computes it alone, so results
-// do not depend on what else is resident.
+// Lane 1 solves large requests, and those that would colour a phase, one at
+// a time with the single-graph driver.  Every request is computed exactly as
+// lv_run computes it alone, so results do not depend on what else is resident.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -35,6 +37,7 @@ constexpr int64_t kBytesPerVertex = 64;  // per-vertex state, map and labels
 constexpr int64_t kDefaultBudget = 120ll << 30;
 constexpr int32_t kDefaultMaxGraphs = 65536;
 constexpr int64_t kLaneSplitArcs = int64_t(1) << 22;  // requests at least this large use lane 1
+constexpr int kPlainWorkers = 1;
 
 struct Request {
     int64_t id = 0;
@@ -107,19 +110,29 @@ struct lv_server {
     std::mutex mu;
     std::condition_variable cv_done, cv_adm;
     std::deque<std::shared_ptr<Request>> queue;
-    // Two lanes, each a worker thread with its own engine and stream: requests
-    // with fewer than kLaneSplitArcs arcs and the rest.  Lock-step phases then
-    // never make a small request wait for a large one's iterations; the
-    // lanes' launches interleave on the device.
+    // Two lanes, each a worker thread with its own stream.  Lane 0 batches
+    // the requests with fewer than kLaneSplitArcs arcs in a multi-graph
+    // engine (continuous batching at phase boundaries).  Lane 1 solves large
+    // requests, and those that would colour a phase (colouring on and at
+    // least color_cutoff vertices), one at a time with the single-graph
+    // driver.  A small request never waits for a large one's iterations, and
+    // the lanes' launches interleave on the device.
     struct Lane {
         cudaStream_t stream = nullptr;
         bool own_stream = false;
         int *pinned = nullptr;
         std::condition_variable cv_work;
-        std::deque<Ready> ready;  // admitted and prepared, not yet in the engine
+        std::deque<Ready> ready;  // lane 0: admitted and prepared, not yet in the engine
+        std::deque<std::shared_ptr<Request>> plain;  // lane 1: admitted, solved one at a time
         std::thread worker;
         int64_t rounds = 0, sweeps = 0;
     } lanes[2];
+    // lane 1 runs kPlainWorkers solves at a time, each on its own stream
+    // (lanes[1].stream is the first).  One is best on the served stream:
+    // with three, large solves ran 1% faster in total but delayed the small
+    // requests' lane (median latency 364 ms against 108 ms).
+    cudaStream_t plain_streams[kPlainWorkers] = {};
+    std::thread plain_workers[kPlainWorkers];
     int64_t inflight = 0;     // admitted and not completed
     std::unordered_map<int64_t, std::shared_ptr<Request>> reqs;  // until released
     int64_t next_id = 0;
@@ -402,6 +415,74 @@ void complete_locked(lv_server *S, Request &r, double t) {
     else ++S->stats.failed;
 }
 
+// lane 1 takes large requests and those that would colour a phase
+bool plain_lane(const lv_server *S, const Request &r) {
+    return (int64_t)r.col.size() >= kLaneSplitArcs ||
+           (S->cfg.params.coloring && r.n >= S->cfg.params.color_cutoff);
+}
+
+// Lane 1: one request at a time through the single-graph entry points.
+void plain_worker_main(lv_server *S, int wi) {
+    cudaSetDevice(S->device);
+    lv_server::Lane &L = S->lanes[1];
+    cudaStream_t stream = S->plain_streams[wi];
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            L.cv_work.wait(lk, [&] { return S->stop || !L.plain.empty(); });
+            if (S->stop) break;
+            r = L.plain.front();
+            L.plain.pop_front();
+        }
+        const Clock::time_point c0 = Clock::now();
+        lv_graph *h = nullptr;
+        lv_status st = rowptr_ok(*r) ? lv_graph_create(&h, r->n, r->rowptr.data(), r->col.data(),
+                                                       r->w.data(), 0, stream)
+                                     : LV_ERR_ARG;
+        if (st == LV_OK) st = lv_run(h, &S->cfg.params);
+        if (st == LV_OK) {
+            r->labels.resize((size_t)r->n);
+            st = lv_get_labels(h, -1, r->labels.data(), 0);
+        }
+        int32_t np = 0;
+        if (st == LV_OK) st = lv_num_phases(h, &np);
+        if (st == LV_OK) {
+            r->info.num_phases = np;
+            r->info.iterations = 0;
+            for (int32_t p = 0; p < np && st == LV_OK; ++p) {
+                lv_phase_info in;
+                st = lv_get_phase_info(h, p, &in);
+                r->info.iterations += in.iterations;
+                if (p == np - 1) {
+                    r->info.n_final = in.n_next;
+                    r->info.N_final = in.N_end;
+                    r->info.q = in.q;
+                    r->info.two_m = in.two_m;
+                }
+            }
+            lv_stats ls;
+            if (st == LV_OK && lv_get_stats(h, &ls) == LV_OK) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->stats.kernel_launches += ls.kernel_launches;
+                S->stats.sweeps += ls.sweep_launches;
+            }
+        }
+        lv_graph_destroy(h);
+        const Clock::time_point c1 = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->info.status = st;
+            ++L.rounds;
+            S->stats.rounds = S->lanes[0].rounds + S->lanes[1].rounds;
+            S->stats.ms_iterate += ms_between(c0, c1);
+            complete_locked(S, *r, S->now_ms());
+        }
+        S->cv_done.notify_all();
+        S->cv_adm.notify_all();
+    }
+}
+
 // Admission thread: takes queued requests first come first served while the
 // budget, the slots and int32 ids allow, then uploads, validates and
 // vertex-follows them on its own stream, so this work overlaps the worker's
@@ -438,11 +519,22 @@ void admitter_main(lv_server *S) {
             for (auto &r : adm) r->info.t_admit_ms = t;
             S->stats.admitted += (int64_t)adm.size();
         }
-        for (int ln = 0; ln < 2; ++ln) {
+        {
+            std::vector<std::shared_ptr<Request>> to_plain;
+            for (auto &r : adm)
+                if (plain_lane(S, *r)) to_plain.push_back(r);
+            if (!to_plain.empty()) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                for (auto &r : to_plain) S->lanes[1].plain.push_back(r);
+            }
+            if (!to_plain.empty()) S->lanes[1].cv_work.notify_all();
+        }
+        do {  // the rest joins lane 0's engine
+            const int ln = 0;
             std::vector<std::shared_ptr<Request>> group;
             for (auto &r : adm)
-                if ((int64_t)r->col.size() >= kLaneSplitArcs ? ln == 1 : ln == 0) group.push_back(r);
-            if (group.empty()) continue;
+                if (!plain_lane(S, *r)) group.push_back(r);
+            if (group.empty()) break;
             const Clock::time_point c0 = Clock::now();
             std::vector<std::shared_ptr<Request>> failed, joined;
             std::unique_ptr<Prepared> pr;
@@ -471,7 +563,7 @@ void admitter_main(lv_server *S) {
             S->lanes[ln].cv_work.notify_all();
             S->cv_done.notify_all();
             S->cv_adm.notify_all();
-        }
+        } while (false);
     }
 }
 
@@ -566,9 +658,9 @@ void worker_main(lv_server *S, int ln) {
                 }
             }
             if (!fin.empty() || e.num_graphs() > 0) ++L.rounds;
+            S->stats.sweeps += e.sweep_launches - L.sweeps;
             L.sweeps = e.sweep_launches;
             S->stats.rounds = S->lanes[0].rounds + S->lanes[1].rounds;
-            S->stats.sweeps = S->lanes[0].sweeps + S->lanes[1].sweeps;
             S->stats.peak_graphs = std::max<int64_t>(S->stats.peak_graphs, (int64_t)resident.size());
             S->stats.peak_bytes = std::max<int64_t>(S->stats.peak_bytes, S->resident_bytes);
             S->stats.kernel_launches += (int64_t)(g_kernel_launches.load() - launches0);
@@ -590,7 +682,7 @@ extern "C" {
 lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *cuda_stream) {
     if (!out) return LV_ERR_ARG;
     *out = nullptr;
-    if (!cfg || cfg->params.coloring) return LV_ERR_ARG;
+    if (!cfg) return LV_ERR_ARG;
     const lv_params &P = cfg->params;
     BinLimits lim;
     if (P.bin_lane_arcs) lim.lane_arcs = P.bin_lane_arcs;
@@ -618,6 +710,10 @@ lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *c
         if (st == LV_OK && cudaMallocHost((void **)&L.pinned, 64 * sizeof(int)) != cudaSuccess)
             st = LV_ERR_OOM;
     }
+    S->plain_streams[0] = S->lanes[1].stream;
+    for (int i = 1; i < kPlainWorkers && st == LV_OK; ++i)
+        if (cudaStreamCreateWithFlags(&S->plain_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+            st = LV_ERR_CUDA;
     if (st == LV_OK) st = ensure_setup(S->lanes[0].stream);
     if (st == LV_OK && cudaMallocHost((void **)&S->adm_pinned, 64 * sizeof(int)) != cudaSuccess)
         st = LV_ERR_OOM;
@@ -630,12 +726,15 @@ lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *c
             if (L.pinned) cudaFreeHost(L.pinned);
             if (L.own_stream) cudaStreamDestroy(L.stream);
         }
+        for (int i = 1; i < kPlainWorkers; ++i)
+            if (S->plain_streams[i]) cudaStreamDestroy(S->plain_streams[i]);
         if (S->adm_pinned) cudaFreeHost(S->adm_pinned);
         if (S->adm_stream) cudaStreamDestroy(S->adm_stream);
         delete S;
         return st;
     }
-    for (int ln = 0; ln < 2; ++ln) S->lanes[ln].worker = std::thread(worker_main, S, ln);
+    S->lanes[0].worker = std::thread(worker_main, S, 0);
+    for (int i = 0; i < kPlainWorkers; ++i) S->plain_workers[i] = std::thread(plain_worker_main, S, i);
     S->admitter = std::thread(admitter_main, S);
     *out = S;
     return LV_OK;
@@ -722,9 +821,18 @@ void lv_server_destroy(lv_server *S) {
     if (S->admitter.joinable()) S->admitter.join();
     for (auto &L : S->lanes)
         if (L.worker.joinable()) L.worker.join();
-    for (auto &L : S->lanes) L.ready.clear();  // prepared graphs never appended
+    for (auto &t : S->plain_workers)
+        if (t.joinable()) t.join();
+    for (auto &L : S->lanes) {
+        L.ready.clear();  // prepared graphs never appended
+        L.plain.clear();
+    }
     cudaStreamSynchronize(S->adm_stream);
     S->ring.destroy();
+    for (int i = 1; i < kPlainWorkers; ++i) {
+        cudaStreamSynchronize(S->plain_streams[i]);
+        cudaStreamDestroy(S->plain_streams[i]);
+    }
     for (auto &L : S->lanes) {
         cudaStreamSynchronize(L.stream);
         if (L.pinned) cudaFreeHost(L.pinned);

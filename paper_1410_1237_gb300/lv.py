@@ -385,11 +385,11 @@ def lv_batch_destroy(h: int) -> None:
 
 def lv_server_create(mem_budget_bytes: int = 0, max_graphs: int = 0, stream: int = 0,
                      **params) -> int:
-    """A serving handle; params as make_params (coloring must stay 0)."""
+    """A serving handle; params as make_params (defaults: every heuristic on)."""
     cfg = lv_server_config()
     cfg.mem_budget_bytes = int(mem_budget_bytes)
     cfg.max_graphs = int(max_graphs)
-    cfg.params = make_params(**{"coloring": 0, **params})
+    cfg.params = make_params(**params)
     h = ctypes.c_void_p()
     _check(load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), stream or None),
            "lv_server_create")

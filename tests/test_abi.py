@@ -78,12 +78,17 @@ def test_struct_layouts_match_header(tmp_path):
             assert got[(name, f)] == getattr(cls, f).offset, (name, f)
 
 
-def test_server_rejects_colouring_without_gpu():
+def test_server_rejects_bad_config_without_gpu():
     # argument checks come before any device work
     from paper_1410_1237_gb300 import lv
     lv.load()
-    cfg = lv.lv_server_config()
-    cfg.params = lv.make_params(coloring=1)
     h = ctypes.c_void_p()
-    assert lv.load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1
     assert lv.load().lv_server_create(ctypes.byref(h), None, None) == -1
+    for bad in (dict(bin_lane_arcs=9), dict(max_iters=0), dict(bin_cta_max=64, bin_warp_max=128)):
+        cfg = lv.lv_server_config()
+        cfg.params = lv.make_params(**bad)
+        assert lv.load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1, bad
+    cfg = lv.lv_server_config()
+    cfg.params = lv.make_params()
+    cfg.max_graphs = -1
+    assert lv.load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1
