@@ -28,7 +28,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_WEIGHT",
 
 DEFAULTS = dict(vertex_following=1, coloring=1, theta_low=1e-6, theta_high=1e-2,
                 color_cutoff=100_000, max_iters=10_000, max_phases=64, color_seed=0x5EED,
-                trace=0)
+                trace=0, color_phases=0, abs_threshold=0)
 
 
 class OracleError(RuntimeError):
@@ -52,7 +52,8 @@ class _Params(ctypes.Structure):
                 ("theta_low", ctypes.c_double), ("theta_high", ctypes.c_double),
                 ("color_cutoff", ctypes.c_int64), ("max_iters", ctypes.c_int32),
                 ("max_phases", ctypes.c_int32), ("color_seed", ctypes.c_uint64),
-                ("trace", ctypes.c_int32)]
+                ("trace", ctypes.c_int32), ("color_phases", ctypes.c_int32),
+                ("abs_threshold", ctypes.c_int32)]
 
 
 def _load():
@@ -102,6 +103,8 @@ def _load():
         L.orc_num_iters.argtypes = [vp]
         L.orc_iters.argtypes = [vp, vp, vp, vp, vp]
         L.orc_free.argtypes = [vp]
+        L.orc_compare.restype = ctypes.c_int
+        L.orc_compare.argtypes = [i64, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -250,6 +253,27 @@ class Result:
         return self.phases[-1].q
 
 
+def compare(labels_s, labels_p) -> dict:
+    """Qualitative comparison of two partitions (Sec. 5) by its plain
+    definition over all vertex pairs: TP, FP, FN, TN and SP = TP/(TP+FP),
+    SE = TP/(TP+FN), OQ = TP/(TP+FP+FN), Rand = (TP+TN)/all pairs (a ratio
+    with a zero denominator is reported as 1)."""
+    s = np.ascontiguousarray(labels_s, dtype=np.int32)
+    p = np.ascontiguousarray(labels_p, dtype=np.int32)
+    if s.shape != p.shape:
+        raise ValueError("partitions of different sizes")
+    out = np.zeros(4, dtype=np.uint64)
+    st = _load().orc_compare(len(s), s.ctypes.data, p.ctypes.data, out.ctypes.data)
+    if st:
+        raise OracleError(st)
+    tp, fp, fn, tn = (int(x) for x in out)
+
+    def ratio(a, b):
+        return a / b if b else 1.0
+    return dict(tp=tp, fp=fp, fn=fn, tn=tn, sp=ratio(tp, tp + fp), se=ratio(tp, tp + fn),
+                oq=ratio(tp, tp + fp + fn), rand=ratio(tp + tn, tp + fp + fn + tn))
+
+
 def run(rowptr, col, w, **params) -> Result:
     """Full multi-phase run (Sec. 4.4 steps 1-4).  Raises OracleError on an
     invalid input."""
@@ -260,7 +284,8 @@ def run(rowptr, col, w, **params) -> Result:
     L = _load()
     p = _Params(int(prm["vertex_following"]), int(prm["coloring"]), float(prm["theta_low"]),
                 float(prm["theta_high"]), int(prm["color_cutoff"]), int(prm["max_iters"]),
-                int(prm["max_phases"]), int(prm["color_seed"]), int(prm["trace"]))
+                int(prm["max_phases"]), int(prm["color_seed"]), int(prm["trace"]),
+                int(prm["color_phases"]), int(prm["abs_threshold"]))
     h = ctypes.c_void_p()
     st = L.orc_run(n, rowptr.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(p),
                    ctypes.byref(h))

@@ -77,6 +77,10 @@ typedef struct {
     int32_t max_phases;       /* guard on phases */
     uint64_t color_seed;      /* priority hash seed; phase p uses seed + p */
     int32_t trace;            /* keep phase graphs, colourings, per-iteration labels */
+    int32_t color_phases;     /* colour at most this many phases (0 = no limit; 1 = only the
+                                 first phase, the variant of the Sec. 5 experiments) */
+    int32_t abs_threshold;    /* 1: every threshold test uses |N_C - N_P| (the form printed
+                                 in Alg. 1) instead of the signed net gain of R9 */
 } orc_params;
 
 typedef struct {
@@ -578,8 +582,9 @@ static int64_t abs64(int64_t x) { return x < 0 ? -x : x; }
  * |N_P|, on exact numerators.  Alg. 1 prints the relative form; Sec. 4.1
  * (last paragraph) relies on a minimum net gain to continue, so a negative
  * gain stops the loop.  |N| < 2^62, so both differences fit in int64. */
-static int gain_below(i128 Nc, i128 Np, double theta) {
-    const int64_t d = (int64_t)(Nc - Np);
+static int gain_below(i128 Nc, i128 Np, double theta, int abs_mode) {
+    int64_t d = (int64_t)(Nc - Np);
+    if (abs_mode) d = abs64(d);  /* the printed form of Alg. 1 (variant) */
     const int64_t b = abs64((int64_t)Np);
     return (double)d < theta * (double)b;
 }
@@ -609,13 +614,15 @@ int orc_run(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t 
     memcpy(r->vf_map, map, (size_t)n * sizeof(int32_t));
     r->vf_n = G->n;
 
-    int colour_stopped = 0;
+    int colour_stopped = 0, coloured_phases = 0;
     for (int32_t p = 0; p < prm->max_phases; ++p) {
         const int64_t np = G->n;
         orc_phase *ph = new_phase(r);
         ph->n = np;
         ph->arcs = G->arcs;
-        const int colour_on = prm->coloring && !colour_stopped && np >= prm->color_cutoff;
+        const int colour_on = prm->coloring && !colour_stopped && np >= prm->color_cutoff &&
+                              (prm->color_phases <= 0 || coloured_phases < prm->color_phases);
+        coloured_phases += colour_on;
         const double theta = (colour_on && prm->theta_high > 0.0) ? prm->theta_high
                                                                   : prm->theta_low;
         ph->colored = colour_on;
@@ -692,7 +699,7 @@ int orc_run(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t 
                 memcpy(itl[iter - 1], C, (size_t)np * sizeof(int32_t));
             }
             if (moved == 0) break;
-            if (have_NP && gain_below(N_C, N_P, theta)) break;
+            if (have_NP && gain_below(N_C, N_P, theta, prm->abs_threshold)) break;
             if (iter >= prm->max_iters) break;
             N_P = N_C;
             have_NP = 1;
@@ -715,9 +722,10 @@ int orc_run(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t 
         int stop = 0;
         if (nn == np) stop = 1;
         else if (colour_on) {
-            if (prm->theta_high > 0.0 && gain_below(N_C, ph->N_start, prm->theta_high))
+            if (prm->theta_high > 0.0 &&
+                gain_below(N_C, ph->N_start, prm->theta_high, prm->abs_threshold))
                 colour_stopped = 1;
-        } else if (gain_below(N_C, ph->N_start, prm->theta_low)) {
+        } else if (gain_below(N_C, ph->N_start, prm->theta_low, prm->abs_threshold)) {
             stop = 1;
         }
         if (p + 1 >= prm->max_phases) stop = 1;
@@ -809,4 +817,30 @@ void orc_free(orc_result *r) {
     free(r->it);
     free(r->vf_map);
     free(r);
+}
+
+
+/* ------------------------------------------------------------------------
+ * Qualitative comparison of two partitions (Sec. 5): every unordered pair
+ * {u, v} of the n vertices is a true positive (same community in both s and
+ * p), a false positive (same only in p), a false negative (same only in s)
+ * or a true negative (different in both).  Plain definition: all n(n-1)/2
+ * pairs are examined.  out = {TP, FP, FN, TN}.
+ * ---------------------------------------------------------------------- */
+int orc_compare(int64_t n, const int32_t *s, const int32_t *p, uint64_t *out) {
+    if (n < 0 || !out || (n > 0 && (!s || !p))) return ORC_ERR_ARG;
+    uint64_t tp = 0, fp = 0, fn = 0, tn = 0;
+    for (int64_t u = 0; u < n; ++u)
+        for (int64_t v = u + 1; v < n; ++v) {
+            const int same_s = s[u] == s[v], same_p = p[u] == p[v];
+            if (same_s && same_p) ++tp;
+            else if (same_p) ++fp;
+            else if (same_s) ++fn;
+            else ++tn;
+        }
+    out[0] = tp;
+    out[1] = fp;
+    out[2] = fn;
+    out[3] = tn;
+    return ORC_OK;
 }

@@ -422,3 +422,69 @@ def test_isolated_vertices_stay():
     lab = r.final_labels
     assert len({lab[3], lab[4], lab[7]}) == 3
     assert lab[0] == lab[1] == lab[2] and lab[5] == lab[6]
+
+
+# --------------------------------------------------------------------------
+# Heuristic variants of the Sec. 5 experiments and the qualitative comparison
+# --------------------------------------------------------------------------
+def test_compare_hand_example():
+    # pairs of {0,1,2,3} under s = {01|23}, p = {012|3}: TP {01}; FP {02},{12};
+    # FN {23}; TN {03},{13}
+    c = oracle.compare([0, 0, 1, 1], [5, 5, 5, 7])
+    assert (c["tp"], c["fp"], c["fn"], c["tn"]) == (1, 2, 1, 2)
+    assert c["sp"] == 1 / 3 and c["se"] == 1 / 2 and c["oq"] == 1 / 4 and c["rand"] == 1 / 2
+
+
+def test_compare_identical_and_symmetric():
+    rng = np.random.default_rng(3)
+    s = rng.integers(0, 7, size=60)
+    perm = rng.permutation(7)
+    c = oracle.compare(s, perm[s])  # same partition under other labels
+    assert c["fp"] == c["fn"] == 0 and c["sp"] == c["se"] == c["oq"] == c["rand"] == 1.0
+    p = rng.integers(0, 5, size=60)
+    a, b = oracle.compare(s, p), oracle.compare(p, s)
+    assert (a["tp"], a["fp"], a["fn"], a["tn"]) == (b["tp"], b["fn"], b["fp"], b["tn"])
+    assert a["tp"] + a["fp"] + a["fn"] + a["tn"] == 60 * 59 // 2
+
+
+def test_compare_matches_contingency_counts():
+    # independent route: TP = sum over the contingency table of C(n_ij, 2)
+    rng = np.random.default_rng(4)
+    s = rng.integers(0, 9, size=300)
+    p = rng.integers(0, 4, size=300) + 3 * (s % 3)
+    c = oracle.compare(s, p)
+    pairs = lambda x: int((x * (x - 1) // 2).sum())
+    _, nij = np.unique(np.stack([s, p], 1), axis=0, return_counts=True)
+    _, ni = np.unique(s, return_counts=True)
+    _, nj = np.unique(p, return_counts=True)
+    tp = pairs(nij)
+    assert c["tp"] == tp and c["fn"] == pairs(ni) - tp and c["fp"] == pairs(nj) - tp
+    sk = pytest.importorskip("sklearn.metrics")
+    assert abs(c["rand"] - sk.rand_score(s, p)) < 1e-12
+
+
+def test_absolute_threshold_two_cycles_on_planted1k():
+    # R9: with |N_C - N_P| the synchronous uncoloured sweep of the 1,000-vertex
+    # planted graph falls into a 2-cycle and only the max_iters guard ends it;
+    # the signed test stops it
+    g, _ = gg.workload("planted1k")
+    signed = oracle.run(g.rowptr, g.col, g.w, coloring=0, max_iters=40)
+    absm = oracle.run(g.rowptr, g.col, g.w, coloring=0, max_iters=40, abs_threshold=1)
+    assert signed.phases[0].iterations < 40
+    assert absm.phases[0].iterations == 40
+    # the cycle: labels two iterations apart agree, consecutive ones differ
+    tr = oracle.run(g.rowptr, g.col, g.w, coloring=0, max_iters=40, abs_threshold=1, trace=1,
+                    max_phases=1)
+    it = tr.phases[0].iter_labels
+    assert np.array_equal(it[-1], it[-3]) and not np.array_equal(it[-1], it[-2])
+
+
+def test_colour_first_phase_only():
+    g = gg.rmat(12, 12, seed=9)
+    full = oracle.run(g.rowptr, g.col, g.w, color_cutoff=0, theta_high=0.0)
+    first = oracle.run(g.rowptr, g.col, g.w, color_cutoff=0, theta_high=0.0, color_phases=1)
+    assert [p.colored for p in full.phases][:2] == [True, True]
+    assert first.phases[0].colored and not any(p.colored for p in first.phases[1:])
+    # phase 0 is the same run in both
+    assert np.array_equal(full.phases[0].labels, first.phases[0].labels)
+    assert full.phases[0].N_end == first.phases[0].N_end
