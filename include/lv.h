@@ -83,7 +83,13 @@ typedef struct {
      * of its counters) from a captured CUDA graph; default 1.  Ignored on the
      * legacy default stream (NULL), which cannot be captured. */
     int32_t graph_capture;
-    int32_t reserved;
+    /* Variants of the Sec. 5 experiments: colour at most this many phases
+     * (0 = no limit, 1 = the first phase only), and */
+    int32_t color_phases;
+    /* 0/1: every threshold test uses |N_C - N_P| < theta |N_P|, the form
+     * printed in Alg. 1, instead of the signed net gain (default 0; the
+     * absolute form can cycle between two labellings until max_iters). */
+    int32_t abs_threshold;
 } lv_params;
 
 /* Per-phase record.  N values are exact modularity numerators: Q = N/(2m)^2. */
@@ -200,6 +206,24 @@ lv_status lv_get_phase_graph(const lv_graph *g, int32_t phase, int64_t *n, int64
 /* Colour of each vertex of G_p (requires keep_graphs = 1 and a coloured
  * phase): int32[n_p]. */
 lv_status lv_get_phase_colors(const lv_graph *g, int32_t phase, int32_t *out, int ptr_on_device);
+
+/* Qualitative comparison of two partitions of the same n vertices (Sec. 5):
+ * over all unordered vertex pairs, TP = same community in both, FP = same
+ * only in p, FN = same only in s, TN = different in both; SP = TP/(TP+FP),
+ * SE = TP/(TP+FN), OQ = TP/(TP+FP+FN), Rand = (TP+TN)/(n(n-1)/2) (a ratio
+ * whose denominator is 0 is 1).  Computed from the contingency table of the
+ * two labellings (sort by label pairs), not pair by pair. */
+typedef struct {
+    uint64_t tp, fp, fn, tn;
+    double sp, se, oq, rand;
+} lv_partition_compare;
+
+/*   n            vertices, 0 <= n < 2^31
+ *   labels_s/p   int32[n], any values (equal values = same community)
+ *   ptrs_on_device  0: host arrays, 1: device arrays
+ *   cuda_stream  the stream for the work; the call returns after it */
+lv_status lv_compare_partitions(int64_t n, const int32_t *labels_s, const int32_t *labels_p,
+                                int ptrs_on_device, lv_partition_compare *out, void *cuda_stream);
 
 /* Modularity numerator of a caller-given labelling, computed without any
  * device allocation.  (This entry point has no counterpart in the paper; it

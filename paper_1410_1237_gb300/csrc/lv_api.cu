@@ -214,7 +214,7 @@ struct IterRecord {
 
 // Uncoloured phase: fused Jacobi sweeps (see the file comment).
 lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const BinLimits &lim,
-                         double theta, int32_t max_iters, int phase,
+                         double theta, bool abs_mode, int32_t max_iters, int phase,
                          std::vector<IterRecord> &recs, IterResult *out) {
     cudaStream_t s = h->stream;
     bool have_np = false;
@@ -255,7 +255,7 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
         } else {
             const int t = step - 1;
             record(t, moved_prev, N_prev, ev_prev0, ev_prev1);
-            if ((have_np && gain_below(N_prev, n_p, theta)) || t >= max_iters) {
+            if ((have_np && gain_below(N_prev, n_p, theta, abs_mode)) || t >= max_iters) {
                 out->iters = t;
                 out->N = N_prev;
                 return LV_OK;
@@ -278,8 +278,8 @@ lv_status iterate_jacobi(lv_graph *h, PhaseState &ps, const Buckets &b, const Bi
 
 // Coloured phase: classes in ascending colour, moves applied after each class.
 lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const BinLimits &lim,
-                          double theta, int32_t max_iters, int phase, int64_t sum_loops,
-                          std::vector<IterRecord> &recs, IterResult *out) {
+                          double theta, bool abs_mode, int32_t max_iters, int phase,
+                          int64_t sum_loops, std::vector<IterRecord> &recs, IterResult *out) {
     cudaStream_t s = h->stream;
     bool have_np = false;
     int64_t n_p = 0;
@@ -306,7 +306,7 @@ lv_status iterate_colored(lv_graph *h, PhaseState &ps, const Buckets &b, const B
         r.ev0 = e0;
         r.ev1 = e1;
         recs.push_back(r);
-        if (hs.moved == 0 || (have_np && gain_below(N, n_p, theta)) || t >= max_iters) {
+        if (hs.moved == 0 || (have_np && gain_below(N, n_p, theta, abs_mode)) || t >= max_iters) {
             out->iters = t;
             out->N = N;
             return LV_OK;
@@ -396,6 +396,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     };
     std::vector<PhaseEvents> phase_events;
     bool colour_stopped = false;
+    int32_t coloured_phases = 0;
     lv_status st = LV_OK;
     for (int32_t p = 0; p < P.max_phases; ++p) {
         PhaseRec rec;
@@ -404,7 +405,9 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         info.n = G.n;
         info.arcs = G.A;
         info.two_m = h->two_m;
-        const bool colour_on = P.coloring && !colour_stopped && (int64_t)G.n >= P.color_cutoff;
+        const bool colour_on = P.coloring && !colour_stopped && (int64_t)G.n >= P.color_cutoff &&
+                               (P.color_phases <= 0 || coloured_phases < P.color_phases);
+        coloured_phases += colour_on ? 1 : 0;
         const double theta = (colour_on && P.theta_high > 0.0) ? P.theta_high : P.theta_low;
         info.colored = colour_on ? 1 : 0;
         info.theta = theta;
@@ -485,9 +488,11 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         info.N_start = ps.two_m * (int64_t)hs0.sum_ein - (int64_t)hs0.sum_a2;
         IterResult ir;
         if (colour_on)
-            st = iterate_colored(h, ps, b, lim, theta, P.max_iters, p, (int64_t)hs0.sum_ein, recs, &ir);
+            st = iterate_colored(h, ps, b, lim, theta, P.abs_threshold != 0, P.max_iters, p,
+                                 (int64_t)hs0.sum_ein, recs, &ir);
         else
-            st = iterate_jacobi(h, ps, b, lim, theta, P.max_iters, p, recs, &ir);
+            st = iterate_jacobi(h, ps, b, lim, theta, P.abs_threshold != 0, P.max_iters, p, recs,
+                                &ir);
         if (st != LV_OK) return st;
         const int ev_i1 = h->timer.mark();
         info.iterations = ir.iters;
@@ -507,9 +512,10 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         bool stop = false;
         if (n_next == G.n) stop = true;
         else if (colour_on) {
-            if (P.theta_high > 0.0 && gain_below(info.N_end, info.N_start, P.theta_high))
+            if (P.theta_high > 0.0 &&
+                gain_below(info.N_end, info.N_start, P.theta_high, P.abs_threshold != 0))
                 colour_stopped = true;
-        } else if (gain_below(info.N_end, info.N_start, P.theta_low)) {
+        } else if (gain_below(info.N_end, info.N_start, P.theta_low, P.abs_threshold != 0)) {
             stop = true;
         }
         if (p + 1 >= P.max_phases) stop = true;

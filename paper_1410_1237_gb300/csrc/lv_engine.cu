@@ -744,7 +744,8 @@ lv_status Engine::phase_run() {
                 }
             } else {
                 const int tt = step - 1;
-                if ((t.have_np && gain_below(N_prev, t.n_p, theta)) || tt >= P.max_iters) {
+                if ((t.have_np && gain_below(N_prev, t.n_p, theta, P.abs_threshold != 0)) ||
+                    tt >= P.max_iters) {
                     t.iters = tt;
                     fin = true;
                 } else {
@@ -832,7 +833,8 @@ lv_status Engine::phase_run() {
         in.iterations = t.iters;
         in.ms_color = in.ms_iterate = in.ms_rebuild = -1.0;
         t.info.push_back(in);
-        t.stop = in.n_next == in.n || gain_below(t.N_end, t.N_start, P.theta_low) ||
+        t.stop = in.n_next == in.n ||
+                 gain_below(t.N_end, t.N_start, P.theta_low, P.abs_threshold != 0) ||
                  (int32_t)t.info.size() >= P.max_phases;
     }
     if (timer) {

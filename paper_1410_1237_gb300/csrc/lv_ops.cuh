@@ -136,9 +136,11 @@ lv_status sweep_setup();  // one-time kernel attributes (large dynamic shared me
 lv_status ensure_setup(cudaStream_t s);
 
 // Signed relative stopping test of Sec. 4.1 on exact numerators:
-// (N_C - N_P) < theta |N_P|, converted to double once.
-inline bool gain_below(int64_t Nc, int64_t Np, double theta) {
-    const int64_t d = Nc - Np;
+// (N_C - N_P) < theta |N_P|, converted to double once; abs_mode takes
+// |N_C - N_P| (the form printed in Alg. 1, a variant).
+inline bool gain_below(int64_t Nc, int64_t Np, double theta, bool abs_mode = false) {
+    int64_t d = Nc - Np;
+    if (abs_mode && d < 0) d = -d;
     const int64_t b = Np < 0 ? -Np : Np;
     return (double)d < theta * (double)b;
 }

@@ -41,7 +41,8 @@ class lv_params(ctypes.Structure):
                 ("collect_timing", ctypes.c_int32), ("keep_graphs", ctypes.c_int32),
                 ("bin_lane_arcs", ctypes.c_int32), ("bin_warp_max", ctypes.c_int32),
                 ("bin_cta_max", ctypes.c_int32), ("autotune", ctypes.c_int32),
-                ("graph_capture", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("graph_capture", ctypes.c_int32), ("color_phases", ctypes.c_int32),
+                ("abs_threshold", ctypes.c_int32)]
 
 
 class lv_phase_info(ctypes.Structure):
@@ -79,6 +80,12 @@ class lv_batch_sweep(ctypes.Structure):
     _fields_ = [("phase", ctypes.c_int32), ("sweep", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("vertices", ctypes.c_int64),
                 ("arcs", ctypes.c_int64), ("moved", ctypes.c_int64), ("ms", ctypes.c_double)]
+
+
+class lv_partition_compare(ctypes.Structure):
+    _fields_ = [("tp", ctypes.c_uint64), ("fp", ctypes.c_uint64), ("fn", ctypes.c_uint64),
+                ("tn", ctypes.c_uint64), ("sp", ctypes.c_double), ("se", ctypes.c_double),
+                ("oq", ctypes.c_double), ("rand", ctypes.c_double)]
 
 
 class lv_server_config(ctypes.Structure):
@@ -130,6 +137,8 @@ SIGNATURES = {
     "lv_modularity_noalloc": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, _vp,
                                              _P(ctypes.c_int64), _P(ctypes.c_uint64),
                                              _P(ctypes.c_int64), _vp]),
+    "lv_compare_partitions": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, ctypes.c_int,
+                                             _P(lv_partition_compare), _vp]),
     "lv_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "lv_last_error": (ctypes.c_char_p, []),
     "lv_graph_destroy": (None, [_vp]),
@@ -306,6 +315,22 @@ def lv_modularity_noalloc(n: int, rowptr, col, w, labels, stream: int = 0) -> tu
                                         ctypes.byref(lo), ctypes.byref(den), stream or None),
            "lv_modularity_noalloc")
     return (hi.value << 64) | lo.value, den.value
+
+
+def lv_compare_partitions(labels_s, labels_p, stream: int = 0) -> dict:
+    """SP, SE, OQ, Rand index and the pair counts of two labellings (Sec. 5);
+    numpy (host) or CUDA tensors, both alike."""
+    ps, d0 = _ptr(_arr(labels_s, np.int32))
+    pp, d1 = _ptr(_arr(labels_p, np.int32))
+    if d0 != d1:
+        raise ValueError("both labellings must be host or both device arrays")
+    n = len(labels_s)
+    if len(labels_p) != n:
+        raise ValueError("labellings of different sizes")
+    out = lv_partition_compare()
+    _check(load().lv_compare_partitions(n, ps, pp, int(d0), ctypes.byref(out), stream or None),
+           "lv_compare_partitions")
+    return {f: getattr(out, f) for f, _ in lv_partition_compare._fields_}
 
 
 def lv_status_string(code: int) -> str:

@@ -59,7 +59,8 @@ def test_struct_layouts_match_header(tmp_path):
                "lv_batch_graph_info": lv.lv_batch_graph_info,
                "lv_batch_sweep": lv.lv_batch_sweep, "lv_server_config": lv.lv_server_config,
                "lv_server_result_info": lv.lv_server_result_info,
-               "lv_server_stats": lv.lv_server_stats}
+               "lv_server_stats": lv.lv_server_stats,
+               "lv_partition_compare": lv.lv_partition_compare}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lv.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')

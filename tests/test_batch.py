@@ -293,3 +293,16 @@ def test_autotune_single_graph(lv):
                 assert np.array_equal(x.labels, y.labels)
     finally:
         lv.lv_graph_destroy(h)
+
+
+def test_batch_variants(lv, golden):
+    """The absolute-threshold variant in batches (colouring does not batch)."""
+    graphs = mixed_graphs(golden)
+    b = gg.concat(graphs, "mixed")
+    prm = dict(vertex_following=1, coloring=0, abs_threshold=1, max_iters=25)
+    h = run_batch(lv, b, **prm)
+    try:
+        for g in range(b.num_graphs):
+            check_graph(lv, h, b, g, **prm)
+    finally:
+        lv.lv_batch_destroy(h)

@@ -176,3 +176,65 @@ def test_chunglu24_full_invariants(lv):
             assert p.N_start == prev.N_end
         assert -0.5 <= p.q < 1
         prev = p
+
+
+# ----------------------------------------------------- heuristic variants
+@pytest.mark.parametrize("name", ["two_k5.txt", "ring3_triangles.txt", "star_vf.txt"])
+def test_variant_golden_abs_threshold(lv, golden, name):
+    fx = golden(name)
+    g = gg.from_edges(fx["n"], fx["edges"])
+    compare(lv, g, coloring=0, abs_threshold=1, max_iters=30)
+
+
+def test_variant_abs_threshold_cycles_to_guard(lv):
+    # the absolute test 2-cycles on the planted graph until max_iters (R9)
+    g, _ = gg.workload("planted1k")
+    res, ref = compare(lv, g, graphs=False, coloring=0, abs_threshold=1, max_iters=40)
+    assert res.phases[0].iterations == 40
+
+
+def test_variant_first_phase_colouring(lv):
+    g = gg.rmat(16, 8, seed=31)
+    res, ref = compare(lv, g, graphs=True, color_cutoff=0, theta_high=0.0, color_phases=1)
+    assert res.phases[0].colored and not any(p.colored for p in res.phases[1:])
+
+
+def test_variant_colour_phase_theta(lv):
+    g = gg.rmat(16, 8, seed=32)
+    compare(lv, g, graphs=False, color_cutoff=0, theta_high=1e-4)
+
+
+# --------------------------------------------- qualitative comparison (Sec. 5)
+def test_compare_partitions_against_oracle(lv):
+    rng = np.random.default_rng(5)
+    for n, ks, kp in [(2, 1, 1), (3, 2, 3), (500, 7, 5), (2000, 40, 3), (1500, 1500, 1)]:
+        s = rng.integers(0, ks, size=n).astype(np.int32)
+        p = rng.integers(0, kp, size=n).astype(np.int32)
+        got = lv.lv_compare_partitions(s, p)
+        want = oracle.compare(s, p)
+        for key in ("tp", "fp", "fn", "tn", "sp", "se", "oq", "rand"):
+            assert got[key] == want[key], (n, key, got[key], want[key])
+    assert lv.lv_compare_partitions(np.zeros(0, np.int32), np.zeros(0, np.int32))["rand"] == 1.0
+    # labels of any value, negative ones included
+    s = np.array([-5, -5, 7, 2**31 - 1, 2**31 - 1], dtype=np.int32)
+    p = np.array([0, 1, 1, 3, 3], dtype=np.int32)
+    assert lv.lv_compare_partitions(s, p) == oracle.compare(s, p)
+
+
+def test_compare_partitions_large_device(lv):
+    """A phase's labels against the final ones on R-MAT 20 (device arrays),
+    against the contingency-table counts computed in numpy."""
+    import torch
+    g, prm = gg.workload("rmat20")
+    res = lv.run(g.rowptr, g.col, g.w, **prm)
+    s, p = res.phases[0].labels, res.final_labels
+    got = lv.lv_compare_partitions(torch.from_numpy(s).cuda(), torch.from_numpy(p).cuda())
+    pairs = lambda x: int((x.astype(np.int64) * (x.astype(np.int64) - 1) // 2).sum())
+    _, nij = np.unique(np.stack([s, p], 1), axis=0, return_counts=True)
+    tp = pairs(nij)
+    assert got["tp"] == tp
+    assert got["fn"] == pairs(np.unique(s, return_counts=True)[1]) - tp
+    assert got["fp"] == pairs(np.unique(p, return_counts=True)[1]) - tp
+    n = len(s)
+    assert got["tp"] + got["fp"] + got["fn"] + got["tn"] == n * (n - 1) // 2
+    assert got["fn"] == 0  # phase-0 communities nest inside the final ones
