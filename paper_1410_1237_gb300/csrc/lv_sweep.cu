@@ -421,14 +421,16 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
     return a;
 }
 
-// Hub arc chunk: inserts kHubChunk arcs of one hub into its global table,
-// merging equal labels within each warp first.  Every lane's first probe is
-// a compare-and-swap issued for all its arcs at once (it claims an empty slot
-// or finds its own label in one round trip); collisions fall back to linear
+// Hub arc chunk: kHubChunk arcs of one hub are first summed per label in a
+// shared-memory table of the block, then each distinct label is added to the
+// hub's global table once (so a popular label costs one global atomic per
+// chunk, not one per warp).  Global first probes are compare-and-swaps issued
+// for all of a thread's labels at once; collisions fall back to linear
 // probing.  Claimed slots are appended to the hub's occupied list with one
 // counter update per warp.
-__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
+__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, int *dyn, Acc &acc) {
+    const int lane = threadIdx.x & 31;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
     const int p = lo + a;
     const int i = s.order[p];
@@ -440,36 +442,31 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, Acc &acc) 
     int32_t *occ_cnt = s.hub_cnt + p;
     const int start = beg + (chunk - s.hub_chunk_off[p]) * kHubChunk;
     const int stop = min(end, start + kHubChunk);
-    for (int b0 = start + w * 32; b0 < stop; b0 += kU * kSwBlock) {
-        int2 ar[kU];
+    int *key = dyn, *val = dyn + kHubSmemSlots;
+    for (int sl = threadIdx.x; sl < kHubSmemSlots; sl += kSwBlock) {
+        key[sl] = kEmpty;
+        val[sl] = 0;
+    }
+    __syncthreads();
+    insert_arcs<1>(s, i, start + threadIdx.x, stop, kSwBlock, key, val, kHubSmemSlots - 1, acc);
+    __syncthreads();
+    static_assert(kHubSmemSlots % (kU * kSwBlock) == 0, "slots per pass");
+    for (int s0 = threadIdx.x; s0 < kHubSmemSlots; s0 += kU * kSwBlock) {
         int cl[kU], sum[kU];
-        bool lead[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int e = b0 + u * kSwBlock + lane;
-            ar[u] = e < stop ? s.arcs[e] : make_int2(i, 0);
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) cl[u] = ar[u].x != i ? ldC(s, ar[u].x) : kEmpty;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const bool valid = cl[u] != kEmpty;
-            const unsigned peers = __match_any_sync(0xffffffffu, valid ? cl[u] : -1 - lane);
-            sum[u] = __reduce_add_sync(peers, valid ? ar[u].y : 0);
-            lead[u] = valid && lane == __ffs(peers) - 1;
-        }
         unsigned hslot[kU];
         int prev[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
+            cl[u] = key[s0 + u * kSwBlock];
+            sum[u] = val[s0 + u * kSwBlock];
             hslot[u] = hash32(cl[u]) & mask;
-            prev[u] = lead[u] ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
+            prev[u] = cl[u] != kEmpty ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
         }
         int claimed[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             claimed[u] = -1;
-            if (!lead[u]) continue;
+            if (cl[u] == kEmpty) continue;
             const int c = cl[u];
             unsigned h = hslot[u];
             bool done = prev[u] == kEmpty || prev[u] == c;
@@ -654,7 +651,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
 #ifdef LV_TRACE
                 const unsigned long long ti0 = gtimer();
 #endif
-                if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, acc);
+                if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, dyn, acc);
                 else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
                 __syncthreads();
 #ifdef LV_TRACE
