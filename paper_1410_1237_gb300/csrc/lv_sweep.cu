@@ -429,7 +429,11 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 // probing.  Claimed slots are appended to the hub's occupied list with one
 // counter update per warp.
 constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
-__device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, int *dyn, Acc &acc) {
+constexpr int kHubSoloChunks = 24;             // largest hub decided by one block
+__device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc);
+__device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, int *dyn,
+                          BlockRed &red, Acc &acc, bool solo) {
+    __shared__ int s_last_chunk;
     const int lane = threadIdx.x & 31;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
     const int p = lo + a;
@@ -500,29 +504,24 @@ __device__ void hub_chunk(const Sweep &s, int lo, int cnt, int chunk, int *dyn, 
                 if (claimed[u] >= 0) __stcg(&occ[base++], claimed[u]);
         }
     }
+    if (solo) {  // the class's only hub: the block finishing its last chunk decides
+        const int nch = s.hub_chunk_off[p + 1] - s.hub_chunk_off[p];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last_chunk = atomicAdd(&s.hub_done[p], 1) == nch - 1;
+        __syncthreads();
+        if (s_last_chunk) {
+            __threadfence();
+            hub_decide_solo(s, cc, p, red, acc);
+        }
+    }
 }
 
-// Hub decision, one block per chunk of the occupied list: evaluates its
-// slots (resetting them to empty) and stores a partial best; the last block
-// of the hub to finish (counted with a fenced atomic, no waiting) combines
-// the partials and decides.
-__device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk,
-                                 BlockRed &red, Acc &acc) {
-    __shared__ int s_last;
-    const int a = hub_of_chunk(s, lo, cnt, chunk);
-    const int p = lo + a;
-    const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
-    const int i = s.order[p];
-    if (!live(s, i)) return;  // block-uniform; its chunks inserted nothing
-    const long long tm = tm_of(s, i);
-    const int ci = ldC(s, i), ki = s.k[i];
-    int2 *tab = s.hub_table + s.hub_off[p];
-    const int32_t *occ = s.hub_occ + s.hub_off[p];
-    const int n_occ = __ldcg(&s.hub_cnt[p]);
-    const int t0 = (chunk - first) * kHubChunk, t1 = min(n_occ, t0 + kHubChunk);
-    Best b;
-    best_init(b);
-    int e_old = 0;
+// Evaluates (and resets) the hub table slots listed in occ[t0, t1): the best
+// candidate and the weight to the hub's own community, per thread.
+__device__ __forceinline__ void hub_eval(const Sweep &s, const Cls &cc, int2 *tab, const int32_t *occ,
+                                         int t0, int t1, int ci, int ki, long long tm, Best &b,
+                                         int &e_old) {
     for (int q0 = t0 + threadIdx.x; q0 < t1; q0 += kU * kSwBlock) {
         int hh[kU];
         int2 kv[kU];
@@ -550,6 +549,57 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
                       comm_size(cm[u]), kv[u].y);
         }
     }
+}
+
+// Decision of a hub whose table is complete: the last arc chunk of a class's
+// only hub evaluates every occupied slot with its whole block and decides, so
+// the class needs no grid barrier before the hub's move.
+__device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc) {
+    const int i = s.order[p];
+    const long long tm = tm_of(s, i);
+    const int ci = ldC(s, i), ki = s.k[i];
+    int2 *tab = s.hub_table + s.hub_off[p];
+    const int32_t *occ = s.hub_occ + s.hub_off[p];
+    const int n_occ = __ldcg(&s.hub_cnt[p]);
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    hub_eval(s, cc, tab, occ, 0, n_occ, ci, ki, tm, b, e_old);
+    block_best(b, e_old, red);
+    if (threadIdx.x == 0) {
+        __stcg(&s.hub_cnt[p], 0);
+        __stcg(&s.hub_done[p], 0);
+        atomicMax(&s.stats->max_occ, n_occ);
+        int ein = 0;
+        const bool mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
+        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+        add_terms(s, acc, i, ein, mv);
+    }
+    __syncthreads();
+}
+
+// Hub decision, one block per chunk of the occupied list: evaluates its
+// slots (resetting them to empty) and stores a partial best; the last block
+// of the hub to finish (counted with a fenced atomic, no waiting) combines
+// the partials and decides.
+__device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk,
+                                 BlockRed &red, Acc &acc) {
+    __shared__ int s_last;
+    const int a = hub_of_chunk(s, lo, cnt, chunk);
+    const int p = lo + a;
+    const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
+    const int i = s.order[p];
+    if (!live(s, i)) return;  // block-uniform; its chunks inserted nothing
+    const long long tm = tm_of(s, i);
+    const int ci = ldC(s, i), ki = s.k[i];
+    int2 *tab = s.hub_table + s.hub_off[p];
+    const int32_t *occ = s.hub_occ + s.hub_off[p];
+    const int n_occ = __ldcg(&s.hub_cnt[p]);
+    const int t0 = (chunk - first) * kHubChunk, t1 = min(n_occ, t0 + kHubChunk);
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    hub_eval(s, cc, tab, occ, t0, t1, ci, ki, tm, b, e_old);
     block_best(b, e_old, red);
     if (threadIdx.x == 0) {
         HubPart hp;
@@ -637,6 +687,10 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         const int32_t *ca = s.chunk_at + c * (kBins + 1);
         const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
         const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
+        // a class's only hub, if it is not too large, is decided by the block
+        // that finishes its last chunk (no grid barrier); larger ones are
+        // evaluated by many blocks after a barrier
+        const bool hub_solo = n_hub == 1 && nchunks <= kHubSoloChunks;
         // block items, handed out by a class counter (the next index is
         // fetched while the current item runs)
         const int n_bitems = nchunks + n_cta;
@@ -651,7 +705,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
 #ifdef LV_TRACE
                 const unsigned long long ti0 = gtimer();
 #endif
-                if (it < nchunks) hub_chunk(s, b_hub, n_hub, chunk0 + it, dyn, acc);
+                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_solo);
                 else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
                 __syncthreads();
 #ifdef LV_TRACE
@@ -719,7 +773,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         if (threadIdx.x == 0 && g < (long long)(kTraceCap / 4))
             atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g], gtimer());
 #endif
-        if (n_hub > 0) {
+        if (n_hub > 0 && !hub_solo) {
             if (!grid_sync(s.bar, s.err)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
                 hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
