@@ -8,6 +8,8 @@
 //      a community's self-loop is the sum over its directed intra arcs and
 //      each coarse row lists its neighbours in ascending order.
 // All sums are integer, so the coarse graph is identical on every run.
+#include <algorithm>
+
 #include "lv_ops.cuh"
 
 namespace lv {
@@ -33,62 +35,299 @@ __global__ void cmap_kernel(int n, const int32_t *__restrict__ C, const int32_t 
         cm[v] = (uint32_t)newid[C[v]];
 }
 
-// one warp per row: key = c'(u) << b | c'(v), value = w
-__global__ void __launch_bounds__(256) arc_keys_kernel(DGraph g, const uint32_t *__restrict__ cm,
-                                                       int b, uint64_t *keys, uint32_t *vals) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * 8;
-    for (int64_t u = blockIdx.x * 8 + (threadIdx.x >> 5); u < g.n; u += nw) {
-        const uint64_t hi = (uint64_t)cm[u] << b;
-        const int beg = g.off[u], end = g.off[u + 1];
-        for (int e = beg + lane; e < end; e += 32) {
-            const int2 a = g.arcs[e];
-            keys[e] = hi | cm[a.x];
-            vals[e] = (uint32_t)a.y;
-        }
-    }
-}
-
 __global__ void heads_kernel(const uint64_t *__restrict__ keys, int A, int32_t *head) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < A; e += gridDim.x * blockDim.x)
         head[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1 : 0;
 }
 
-// seg(e) = pos[e] + head[e] - 1; weights summed per segment with a warp
-// segmented scan first (segments are contiguous), then one atomic per piece
-__global__ void __launch_bounds__(256) emit_kernel(const uint64_t *__restrict__ keys,
-                                                   const uint32_t *__restrict__ vals,
-                                                   const int32_t *__restrict__ head,
-                                                   const int32_t *__restrict__ pos, int A, int b,
-                                                   int2 *arcs2, int32_t *rowcnt) {
+// ---------------------------------------------------------------- grouped
+// Coarse rows from the members of each community (the same coarse graph as
+// the sort of all arcs, which is kept for communities with many arcs):
+// vertices are grouped by coarse id (a radix sort of n keys instead of A),
+// then each community's arcs (its members' rows, concatenated) are summed
+// per neighbouring community in a shared-memory table, the distinct
+// neighbours are ranked (ascending) and written to the community's slice of a
+// scratch array, and a scan of the distinct counts packs the rows.
+constexpr int kGrpWarps = 8;          // warps per block of the grouped kernels
+constexpr int kGrpWarpArcs = 256;     // communities with at most this many arcs: one warp
+constexpr int kGrpWarpSlots = 512;    // its table (power of two, 2x the arcs)
+constexpr int kGrpBlockArcs = 1024;   // at most this many: one block (larger: the sort)
+constexpr int kGrpBlockSlots = 2048;
+constexpr int kGrpBlockThreads = 512;
+
+__global__ void group_starts_kernel(int n, const uint32_t *__restrict__ cm_sorted, int n_next,
+                                    int32_t *gs) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (j == 0 || cm_sorted[j] != cm_sorted[j - 1]) gs[cm_sorted[j]] = j;
+        if (j == 0) gs[n_next] = n;
+    }
+}
+
+__global__ void member_deg_kernel(int n, const uint32_t *__restrict__ vo, const int32_t *__restrict__ off,
+                                  int32_t *deg) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int u = (int)vo[j];
+        deg[j] = off[u + 1] - off[u];
+    }
+}
+
+// class of each community: 0 warp, 1 block, 2 sort; flags of classes 1 and 2
+__global__ void group_class_kernel(int n_next, const int32_t *__restrict__ ga, int32_t *f_mid,
+                                   int32_t *f_big, int32_t *big_arcs) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_next; c += gridDim.x * blockDim.x) {
+        const int na = ga[c + 1] - ga[c];
+        f_mid[c] = na > kGrpWarpArcs && na <= kGrpBlockArcs ? 1 : 0;
+        f_big[c] = na > kGrpBlockArcs ? 1 : 0;
+        big_arcs[c] = na > kGrpBlockArcs ? na : 0;
+    }
+}
+
+__global__ void list_kernel(int n, const int32_t *__restrict__ flag, const int32_t *__restrict__ pos,
+                            int32_t *list) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
+        if (flag[c]) list[pos[c]] = c;
+}
+
+// the k-th arc (0-based) of community c's concatenated member rows
+__device__ __forceinline__ int2 group_arc(const DGraph &g, const uint32_t *__restrict__ vo,
+                                          const int32_t *__restrict__ apos, int m0, int m1, int a0,
+                                          int k) {
+    int lo = m0, hi = m1;  // apos[lo] <= a0 + k < apos[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (apos[mid] <= a0 + k) lo = mid; else hi = mid;
+    }
+    const int u = (int)vo[lo];
+    return g.arcs[g.off[u] + (a0 + k - apos[lo])];
+}
+
+// communities with at most kGrpWarpArcs arcs, one warp each
+__global__ void __launch_bounds__(kGrpWarps * 32) group_warp_kernel(
+    DGraph g, int n_next, const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
+    const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm,
+    int2 *tmp, int32_t *cnt, int *err) {
+    __shared__ int key[kGrpWarps][kGrpWarpSlots];
+    __shared__ int val[kGrpWarps][kGrpWarpSlots];
+    constexpr int kPer = kGrpWarpSlots / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int *K = key[w], *V = val[w];
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c = blockIdx.x * kGrpWarps + w; c < n_next; c += gridDim.x * kGrpWarps) {
+        const int a0 = ga[c], na = ga[c + 1] - a0;
+        if (na > kGrpWarpArcs) continue;  // warp-uniform
+        const int m0 = gs[c], m1 = gs[c + 1];
+        for (int sl = lane; sl < kGrpWarpSlots; sl += 32) {
+            K[sl] = kEmpty;
+            V[sl] = 0;
+        }
+        __syncwarp();
+        for (int k = lane; k < na; k += 32) {
+            const int2 a = group_arc(g, vo, apos, m0, m1, a0, k);
+            unsigned h = hash32((int)cm[a.x]) & (kGrpWarpSlots - 1);
+            const int cv = (int)cm[a.x];
+            bool done = false;
+            for (int probe = 0; probe < kGrpWarpSlots && !done; ++probe) {
+                const int prev = atomicCAS(&K[h], kEmpty, cv);
+                if (prev == kEmpty || prev == cv) {
+                    atomicAdd(&V[h], a.y);
+                    done = true;
+                }
+                h = (h + 1) & (kGrpWarpSlots - 1);
+            }
+            if (!done) atomicExch(err, 1);
+        }
+        __syncwarp();
+        // pack the occupied slots to the front of the table
+        int kr[kPer], vr[kPer], d = 0;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            kr[t] = K[t * 32 + lane];
+            vr[t] = V[t * 32 + lane];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const unsigned bm = __ballot_sync(0xffffffffu, kr[t] != kEmpty);
+            if (kr[t] != kEmpty) {
+                K[d + __popc(bm & lt)] = kr[t];
+                V[d + __popc(bm & lt)] = vr[t];
+            }
+            d += __popc(bm);
+        }
+        __syncwarp();
+        // rank (ascending neighbour) and write the row into c's slice
+        for (int x = lane; x < d; x += 32) {
+            const int kx = K[x];
+            int r = 0;
+            for (int y = 0; y < d; ++y) r += K[y] < kx ? 1 : 0;
+            tmp[a0 + r] = make_int2(kx, V[x]);
+        }
+        if (lane == 0) cnt[c] = d;
+        __syncwarp();
+    }
+}
+
+// communities with kGrpWarpArcs < arcs <= kGrpBlockArcs, one block each
+__global__ void __launch_bounds__(kGrpBlockThreads) group_block_kernel(
+    DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ gs,
+    const int32_t *__restrict__ ga, const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo,
+    const uint32_t *__restrict__ cm, int2 *tmp, int32_t *cnt, int *err) {
+    __shared__ int K[kGrpBlockSlots], V[kGrpBlockSlots];
+    __shared__ int s_d;
+    constexpr int kPer = kGrpBlockSlots / kGrpBlockThreads;
+    for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+        const int c = list[li];
+        const int a0 = ga[c], na = ga[c + 1] - a0;
+        const int m0 = gs[c], m1 = gs[c + 1];
+        for (int sl = threadIdx.x; sl < kGrpBlockSlots; sl += kGrpBlockThreads) {
+            K[sl] = kEmpty;
+            V[sl] = 0;
+        }
+        if (threadIdx.x == 0) s_d = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < na; k += kGrpBlockThreads) {
+            const int2 a = group_arc(g, vo, apos, m0, m1, a0, k);
+            const int cv = (int)cm[a.x];
+            unsigned h = hash32(cv) & (kGrpBlockSlots - 1);
+            bool done = false;
+            for (int probe = 0; probe < kGrpBlockSlots && !done; ++probe) {
+                const int prev = atomicCAS(&K[h], kEmpty, cv);
+                if (prev == kEmpty || prev == cv) {
+                    atomicAdd(&V[h], a.y);
+                    done = true;
+                }
+                h = (h + 1) & (kGrpBlockSlots - 1);
+            }
+            if (!done) atomicExch(err, 1);
+        }
+        __syncthreads();
+        int kr[kPer], vr[kPer];
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            kr[t] = K[t * kGrpBlockThreads + threadIdx.x];
+            vr[t] = V[t * kGrpBlockThreads + threadIdx.x];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kPer; ++t)
+            if (kr[t] != kEmpty) {
+                const int at = atomicAdd(&s_d, 1);  // order is fixed by the ranking below
+                K[at] = kr[t];
+                V[at] = vr[t];
+            }
+        __syncthreads();
+        const int d = s_d;
+        for (int x = threadIdx.x; x < d; x += kGrpBlockThreads) {
+            const int kx = K[x];
+            int r = 0;
+            for (int y = 0; y < d; ++y) r += K[y] < kx ? 1 : 0;
+            tmp[a0 + r] = make_int2(kx, V[x]);
+        }
+        if (threadIdx.x == 0) cnt[c] = d;
+        __syncthreads();
+    }
+}
+
+// communities with more arcs: their arcs as (c << b | c(v), w), one thread
+// per arc (the community by a search of the list's arc starts lstart)
+__global__ void __launch_bounds__(256) group_keys_kernel(
+    DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ lstart,
+    int AL, const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
+    const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm,
+    int b, uint64_t *keys, uint32_t *vals) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < AL; e += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_list;  // lstart[lo] <= e < lstart[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (lstart[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int c = list[lo];
+        const int2 a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], e - lstart[lo]);
+        keys[e] = ((uint64_t)c << b) | cm[a.x];
+        vals[e] = (uint32_t)a.y;
+    }
+}
+
+// sorted arcs of the large communities: distinct (c, c(v)) summed into c's
+// slice at its rank (heads counted from the community's first sorted arc)
+__global__ void __launch_bounds__(256) group_emit_kernel(const uint64_t *__restrict__ keys,
+                                                         const uint32_t *__restrict__ vals,
+                                                         const int32_t *__restrict__ head,
+                                                         const int32_t *__restrict__ pos,
+                                                         const int32_t *__restrict__ lpos,
+                                                         const int32_t *__restrict__ ga, int AL, int b,
+                                                         int2 *tmp) {
     const int lane = threadIdx.x & 31;
-    const uint64_t lowmask = (b >= 64) ? ~0ull : ((1ull << b) - 1ull);
+    const uint64_t lowmask = (1ull << b) - 1ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < A; base += stride) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < AL; base += stride) {
         const int64_t e = base + threadIdx.x;
-        const bool valid = e < A;
-        int seg = -1 - lane;  // distinct per invalid lane
+        const bool valid = e < AL;
+        int slot = -1 - lane;
         int w = 0;
         if (valid) {
+            const uint64_t k = keys[e];
+            const int c = (int)(k >> b);
             const int h = head[e];
-            seg = pos[e] + h - 1;
+            slot = ga[c] + (pos[e] + h - 1 - pos[lpos[c]]);
             w = (int)vals[e];
-            if (h) {
-                const uint64_t k = keys[e];
-                arcs2[seg].x = (int)(k & lowmask);
-                atomicAdd(&rowcnt[(int)(k >> b)], 1);
-            }
+            if (h) tmp[slot].x = (int)(k & lowmask);
         }
-        // inclusive segmented scan of w within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int ws = __shfl_up_sync(0xffffffffu, w, o);
-            const int ss = __shfl_up_sync(0xffffffffu, seg, o);
-            if (lane >= o && ss == seg) w += ws;
+            const int ss = __shfl_up_sync(0xffffffffu, slot, o);
+            if (lane >= o && ss == slot) w += ws;
         }
-        const int snext = __shfl_down_sync(0xffffffffu, seg, 1);
-        if (valid && (lane == 31 || snext != seg)) atomicAdd(&arcs2[seg].y, w);
+        const int snext = __shfl_down_sync(0xffffffffu, slot, 1);
+        if (valid && (lane == 31 || snext != slot)) atomicAdd(&tmp[slot].y, w);
     }
+}
+
+__global__ void group_big_count_kernel(int n_list, const int32_t *__restrict__ list,
+                                       const int32_t *__restrict__ ga, const int32_t *__restrict__ lpos,
+                                       const int32_t *__restrict__ pos, int32_t *cnt) {
+    for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < n_list; li += gridDim.x * blockDim.x) {
+        const int c = list[li];
+        const int o = lpos[c], na = ga[c + 1] - ga[c];
+        cnt[c] = pos[o + na] - pos[o];
+    }
+}
+
+// pack: row c = tmp[ga[c], ga[c] + cnt[c]) at off[c]; one warp per community
+__global__ void __launch_bounds__(256) group_pack_kernel(int n_next, const int32_t *__restrict__ ga,
+                                                         const int32_t *__restrict__ off,
+                                                         const int2 *__restrict__ tmp, int2 *arcs) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * 8;
+    for (int c = blockIdx.x * 8 + (threadIdx.x >> 5); c < n_next; c += nw) {
+        const int a0 = ga[c], o = off[c], d = off[c + 1] - o;
+        for (int x = lane; x < d; x += 32) arcs[o + x] = tmp[a0 + x];
+    }
+}
+
+// device scratch freed (stream-ordered) when the set goes out of scope
+struct ScratchSet {
+    static constexpr int kMax = 32;
+    cudaStream_t s = nullptr;
+    void *p[kMax] = {};
+    int k = 0;
+    template <typename T>
+    lv_status get(T **x, size_t count) {
+        if (k >= kMax) return LV_ERR_STATE;  // more buffers than the set holds
+        LV_TRY(dalloc_n(x, count, s));
+        p[k++] = *x;
+        return LV_OK;
+    }
+    ~ScratchSet() {
+        for (int i = 0; i < k; ++i) dfree(p[i], s);
+    }
+};
+
+__global__ void gather_idx_kernel(int G, const int32_t *__restrict__ idx,
+                                  const int32_t *__restrict__ arr, int32_t *out) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g <= G; g += gridDim.x * blockDim.x)
+        out[g] = arr[idx[g]];
 }
 
 }  // namespace
@@ -110,48 +349,118 @@ lv_status compose_labels(int32_t n_orig, int32_t *map, const int32_t *C, const i
 
 lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32_t n_next,
                   DGraph *out, int *pinned, cudaStream_t s) {
-    const int A = g.A;
-    const int b = bits_for((uint64_t)(n_next > 0 ? n_next - 1 : 0));
-    uint32_t *cm = nullptr;
-    uint64_t *keys = nullptr, *keys_alt = nullptr;
-    uint32_t *vals = nullptr, *vals_alt = nullptr;
-    int32_t *head = nullptr, *pos = nullptr, *rowcnt = nullptr;
-    LV_TRY(dalloc_n(&cm, (size_t)g.n, s));
-    LV_TRY(dalloc_n(&keys, (size_t)A, s));
-    LV_TRY(dalloc_n(&keys_alt, (size_t)A, s));
-    LV_TRY(dalloc_n(&vals, (size_t)A, s));
-    LV_TRY(dalloc_n(&vals_alt, (size_t)A, s));
-    cmap_kernel<<<grid_items(g.n), 256, 0, s>>>(g.n, C, newid, cm);
+    const int n = g.n, A = g.A;
+    const int b = std::max(1, bits_for((uint64_t)(n_next > 0 ? n_next - 1 : 0)));
+    ScratchSet t;
+    t.s = s;
+    uint32_t *cm, *cms, *cm_alt, *vo, *vo_alt;
+    int32_t *gs, *deg, *apos, *ga, *cnt, *f_mid, *f_big, *big_arcs, *pmid, *pbig, *lpos, *lists;
+    int2 *tmp;
+    int *err;
+    LV_TRY(t.get(&cm, (size_t)n));
+    LV_TRY(t.get(&cms, (size_t)n));
+    LV_TRY(t.get(&cm_alt, (size_t)n));
+    LV_TRY(t.get(&vo, (size_t)n));
+    LV_TRY(t.get(&vo_alt, (size_t)n));
+    LV_TRY(t.get(&gs, (size_t)n_next + 1));
+    LV_TRY(t.get(&deg, (size_t)n));
+    LV_TRY(t.get(&apos, (size_t)n + 1));
+    LV_TRY(t.get(&ga, (size_t)n_next + 1));
+    LV_TRY(t.get(&cnt, (size_t)n_next + 1));
+    LV_TRY(t.get(&f_mid, (size_t)n_next + 1));
+    LV_TRY(t.get(&f_big, (size_t)n_next + 1));
+    LV_TRY(t.get(&big_arcs, (size_t)n_next + 1));
+    LV_TRY(t.get(&pmid, (size_t)n_next + 1));
+    LV_TRY(t.get(&pbig, (size_t)n_next + 1));
+    LV_TRY(t.get(&lpos, (size_t)n_next + 1));
+    LV_TRY(t.get(&lists, 2 * (size_t)n_next + 2));
+    LV_TRY(t.get(&tmp, (size_t)std::max(A, 1)));
+    LV_TRY(t.get(&err, 1));
+    LV_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    LV_CUDA(cudaMemsetAsync(tmp, 0, sizeof(int2) * (size_t)A, s));
+    // vertices grouped by coarse id (ascending id inside a group)
+    cmap_kernel<<<grid_items(n), 256, 0, s>>>(n, C, newid, cm);
     LV_LAUNCH_CHECK();
-    arc_keys_kernel<<<grid_for(g.n, 8, g_num_sms * 16), 256, 0, s>>>(g, cm, b, keys, vals);
+    LV_CUDA(cudaMemcpyAsync(cms, cm, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    LV_TRY(iota(n, reinterpret_cast<int32_t *>(vo), s));
+    LV_TRY(radix_sort_u32(cms, vo, cm_alt, vo_alt, n, b, s));
+    group_starts_kernel<<<grid_items(n), 256, 0, s>>>(n, cms, n_next, gs);
     LV_LAUNCH_CHECK();
-    LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, A, 2 * b, s));
-    dfree(keys_alt, s);
-    dfree(vals_alt, s);
-    dfree(cm, s);
-    LV_TRY(dalloc_n(&head, (size_t)A, s));
-    LV_TRY(dalloc_n(&pos, (size_t)A + 1, s));
-    heads_kernel<<<grid_items(A), 256, 0, s>>>(keys, A, head);
+    member_deg_kernel<<<grid_items(n), 256, 0, s>>>(n, vo, g.off, deg);
     LV_LAUNCH_CHECK();
-    LV_TRY(scan_excl_i32(head, pos, A, s));
-    LV_CUDA(cudaMemcpyAsync(pinned, pos + A, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_TRY(scan_excl_i32(deg, apos, n, s));
+    gather_idx_kernel<<<grid_items(n_next + 1), 256, 0, s>>>(n_next, gs, apos, ga);
+    LV_LAUNCH_CHECK();
+    // size classes
+    group_class_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, ga, f_mid, f_big, big_arcs);
+    LV_LAUNCH_CHECK();
+    LV_TRY(scan_excl_i32(f_mid, pmid, n_next, s));
+    LV_TRY(scan_excl_i32(f_big, pbig, n_next, s));
+    LV_TRY(scan_excl_i32(big_arcs, lpos, n_next, s));
+    int32_t *list_mid = lists, *list_big = lists + n_next + 1;
+    list_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, f_mid, pmid, list_mid);
+    LV_LAUNCH_CHECK();
+    list_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, f_big, pbig, list_big);
+    LV_LAUNCH_CHECK();
+    LV_CUDA(cudaMemcpyAsync(pinned, pmid + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned + 1, pbig + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned + 2, lpos + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
+    const int n_mid = pinned[0], n_big = pinned[1], AL = pinned[2];
+    // small and medium communities
+    group_warp_kernel<<<grid_for(n_next, kGrpWarps, g_num_sms * 16), kGrpWarps * 32, 0, s>>>(
+        g, n_next, gs, ga, apos, vo, cm, tmp, cnt, err);
+    LV_LAUNCH_CHECK();
+    if (n_mid > 0) {
+        group_block_kernel<<<std::min(n_mid, g_num_sms * 4), kGrpBlockThreads, 0, s>>>(
+            g, n_mid, list_mid, gs, ga, apos, vo, cm, tmp, cnt, err);
+        LV_LAUNCH_CHECK();
+    }
+    // large communities: sort of their arcs by (community, neighbour)
+    if (n_big > 0) {
+        uint64_t *keys, *keys_alt;
+        uint32_t *vals, *vals_alt;
+        int32_t *head, *pos;
+        LV_TRY(t.get(&keys, (size_t)AL));
+        LV_TRY(t.get(&keys_alt, (size_t)AL));
+        LV_TRY(t.get(&vals, (size_t)AL));
+        LV_TRY(t.get(&vals_alt, (size_t)AL));
+        int32_t *lstart;
+        LV_TRY(t.get(&lstart, (size_t)n_big + 1));
+        gather_idx_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big - 1, list_big, lpos, lstart);
+        LV_LAUNCH_CHECK();
+        LV_CUDA(cudaMemcpyAsync(lstart + n_big, &AL, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        group_keys_kernel<<<grid_items(AL), 256, 0, s>>>(g, n_big, list_big, lstart, AL, gs, ga,
+                                                          apos, vo, cm, b, keys, vals);
+        LV_LAUNCH_CHECK();
+        LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, AL, 2 * b, s));
+        LV_TRY(t.get(&head, (size_t)AL));
+        LV_TRY(t.get(&pos, (size_t)AL + 1));
+        heads_kernel<<<grid_items(AL), 256, 0, s>>>(keys, AL, head);
+        LV_LAUNCH_CHECK();
+        LV_TRY(scan_excl_i32(head, pos, AL, s));
+        group_emit_kernel<<<grid_items(AL), 256, 0, s>>>(keys, vals, head, pos, lpos, ga, AL, b, tmp);
+        LV_LAUNCH_CHECK();
+        group_big_count_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big, list_big, ga, lpos, pos, cnt);
+        LV_LAUNCH_CHECK();
+    }
+    // pack the rows
     DGraph h;
     h.n = n_next;
-    h.A = pinned[0];
     LV_TRY(dalloc_n(&h.off, (size_t)n_next + 1, s));
-    LV_TRY(dalloc_n(&h.arcs, (size_t)h.A, s));
-    LV_TRY(dalloc_n(&rowcnt, (size_t)n_next + 1, s));
-    LV_CUDA(cudaMemsetAsync(h.arcs, 0, sizeof(int2) * (size_t)h.A, s));
-    LV_CUDA(cudaMemsetAsync(rowcnt, 0, sizeof(int32_t) * ((size_t)n_next + 1), s));
-    emit_kernel<<<grid_items(A), 256, 0, s>>>(keys, vals, head, pos, A, b, h.arcs, rowcnt);
+    LV_TRY(scan_excl_i32(cnt, h.off, n_next, s));
+    LV_CUDA(cudaMemcpyAsync(pinned, h.off + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned + 1, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    if (pinned[1]) {
+        dfree(h.off, s);
+        return LV_ERR_HASH;
+    }
+    h.A = pinned[0];
+    LV_TRY(dalloc_n(&h.arcs, (size_t)std::max(h.A, 1), s));
+    group_pack_kernel<<<grid_for(n_next, 8, g_num_sms * 16), 256, 0, s>>>(n_next, ga, h.off, tmp,
+                                                                           h.arcs);
     LV_LAUNCH_CHECK();
-    LV_TRY(scan_excl_i32(rowcnt, h.off, n_next, s));
-    dfree(keys, s);
-    dfree(vals, s);
-    dfree(head, s);
-    dfree(pos, s);
-    dfree(rowcnt, s);
     *out = h;
     return LV_OK;
 }

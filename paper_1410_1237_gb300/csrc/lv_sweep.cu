@@ -247,11 +247,12 @@ __device__ __forceinline__ void eval_slots(const Sweep &s, const Cls &cc, const 
 
 // decision for vertex i given the reduced candidate; true on a move.  ein
 // receives e_{i->C(i)} including the self-loop (the vertex's modularity term).
-__device__ __forceinline__ bool decide(const Sweep &s, const Cls &cc, int i, int ci, int ki,
-                                       long long tm, const Best &b, int e_old, Acc &acc, int &ein) {
-    const unsigned long long cmi = __ldcg(&cc.xr[ci]);
+// cmi = the vertex's own community state and lp its self-loop, loaded by the
+// caller together with its other per-vertex data (one round trip less).
+__device__ __forceinline__ bool decide(int ci, int ki, unsigned long long cmi, int lp, long long tm,
+                                       const Best &b, int e_old, Acc &acc, int &ein) {
     const long long s_old = tm * (long long)e_old - (long long)ki * (comm_a(cmi) - ki);
-    ein = e_old + s.loop[i];
+    ein = e_old + lp;
     if (b.c == INT_MAX) return false;
     if (b.s - s_old <= 0) return false;
     if (comm_size(cmi) == 1 && b.size == 1 && b.c > ci) return false;  // singlet rule
@@ -317,8 +318,9 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
     const unsigned lt = (1u << lane) - 1u;
     const int vi = base + lane / G;
     bool valid = vi < nverts;
-    int i = 0, beg = 0, end = 0, ci = 0, ki = 0;
+    int i = 0, beg = 0, end = 0, ci = 0, ki = 0, lp = 0;
     long long tm = 0;
+    unsigned long long cmi = 0;
     unsigned mask = 0;
     if (valid) {
         i = verts[vi];
@@ -330,6 +332,10 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
         end = s.off[i + 1];
         ci = ldC(s, i);
         ki = s.k[i];
+        if (gl == 0) {
+            lp = s.loop[i];
+            cmi = __ldcg(&cc.xr[ci]);
+        }
         const int h = pow2_at_least(2 * (end - beg));
         mask = (unsigned)((h < 4 ? 4 : h) - 1);
     }
@@ -352,7 +358,7 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
     bool mv = false;
     int ein = 0;
     const bool leader = valid && gl == 0;
-    if (leader) mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
+    if (leader) mv = decide(ci, ki, cmi, lp, tm, b, e_old, acc, ein);
     const unsigned bm = __ballot_sync(0xffffffffu, mv);
     if (bm) {
         int pos = 0;
@@ -386,6 +392,12 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
     const long long tm = tm_of(s, i);
     const int beg = s.off[i], end = s.off[i + 1];
     const int ci = ldC(s, i), ki = s.k[i];
+    unsigned long long cmi = 0;
+    int lp = 0;
+    if (threadIdx.x == 0) {
+        cmi = __ldcg(&cc.xr[ci]);
+        lp = s.loop[i];
+    }
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
     int *key = dyn;
     int *val = dyn + kCtaSlots;
@@ -403,7 +415,7 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
     block_best(b, e_old, red);
     if (threadIdx.x == 0) {
         int ein = 0;
-        const bool mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
+        const bool mv = decide(ci, ki, cmi, lp, tm, b, e_old, acc, ein);
         if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
         add_terms(s, acc, i, ein, mv);
     }
@@ -558,6 +570,8 @@ __device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &
     const int i = s.order[p];
     const long long tm = tm_of(s, i);
     const int ci = ldC(s, i), ki = s.k[i];
+    const unsigned long long cmi = __ldcg(&cc.xr[ci]);
+    const int lp = s.loop[i];
     int2 *tab = s.hub_table + s.hub_off[p];
     const int32_t *occ = s.hub_occ + s.hub_off[p];
     const int n_occ = __ldcg(&s.hub_cnt[p]);
@@ -571,7 +585,7 @@ __device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &
         __stcg(&s.hub_done[p], 0);
         atomicMax(&s.stats->max_occ, n_occ);
         int ein = 0;
-        const bool mv = decide(s, cc, i, ci, ki, tm, b, e_old, acc, ein);
+        const bool mv = decide(ci, ki, cmi, lp, tm, b, e_old, acc, ein);
         if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
         add_terms(s, acc, i, ein, mv);
     }
@@ -629,7 +643,7 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
             __stcg(&s.hub_done[p], 0);
             atomicMax(&s.stats->max_occ, n_occ);
             int ein = 0;
-            const bool mv = decide(s, cc, i, ci, ki, tm, t, eo, acc, ein);
+            const bool mv = decide(ci, ki, __ldcg(&cc.xr[ci]), s.loop[i], tm, t, eo, acc, ein);
             if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
             add_terms(s, acc, i, ein, mv);
         }
