@@ -158,9 +158,10 @@ def test_device_pointers_and_stream(lv):
 
 @pytest.mark.slow
 def test_chunglu24_first_iterations(lv):
+    # two iterations of phase 0 in full: labels after them, and each
+    # iteration's moves and exact numerator
     g, prm = gg.workload("chunglu24")
-    for it in (1, 2):
-        compare(lv, g, graphs=False, max_phases=1, max_iters=it, **prm)
+    compare(lv, g, graphs=False, max_phases=1, max_iters=2, **prm)
 
 
 @pytest.mark.slow
