@@ -166,22 +166,22 @@ __device__ __forceinline__ bool smem_insert(int *key, int *val, unsigned mask, i
 }
 
 // insert the arcs e = first, first + step, ... < end of vertex i into a
-// shared-memory table, kU arcs (and their label gathers) at a time
-template <int ST>
+// shared-memory table, U arcs (and their label gathers) at a time
+template <int ST, int U = kU>
 __device__ __forceinline__ void insert_arcs(const Sweep &s, int i, int first, int end, int step,
                                             int *key, int *val, unsigned mask, Acc &acc) {
-    for (int e0 = first; e0 < end; e0 += kU * step) {
-        int2 a[kU];
-        int c[kU];
+    for (int e0 = first; e0 < end; e0 += U * step) {
+        int2 a[U];
+        int c[U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < U; ++u) {
             const int e = e0 + u * step;
             a[u] = e < end ? s.arcs[e] : make_int2(i, 0);
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) c[u] = a[u].x != i ? ldC(s, a[u].x) : kEmpty;
+        for (int u = 0; u < U; ++u) c[u] = a[u].x != i ? ldC(s, a[u].x) : kEmpty;
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < U; ++u)
             if (c[u] != kEmpty && !smem_insert<ST>(key, val, mask, c[u], a[u].y)) acc.err = 1;
     }
 }
@@ -344,7 +344,8 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
         val[sl * ST] = 0;
     }
     __syncwarp();
-    insert_arcs<ST>(s, i, beg + gl, end, G, key, val, mask, acc);
+    // up to kLaneArcsLimit arcs per lane: all of a lane's arcs and labels in flight at once
+    insert_arcs<ST, kLaneArcsLimit>(s, i, beg + gl, end, G, key, val, mask, acc);
     __syncwarp();
     Best b;
     best_init(b);
