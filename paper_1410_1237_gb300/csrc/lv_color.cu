@@ -36,6 +36,7 @@ struct JpState {
     int32_t *counts;       // [3 ring slots][3 kinds]
     int32_t *max_color;
     unsigned *huge_bm;     // 32-word first-window bitmap per slot of the huge list
+    int32_t *huge_done;    // finished parts per slot of the huge list
     GridBarrier *bar;
     int *err;
     int32_t *rounds;
@@ -171,14 +172,15 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
 //            neighbours; big ones: one block each (mark, release, colour);
 //            small ones: one warp each
 //   barrier
-//   stage 2  one warp per huge vertex turns its bitmap into its colour and
-//            clears the bitmap                             [barrier]
+//            the last block to finish a huge vertex's parts turns its
+//            bitmap into its colour and clears it
 // The vertices released in round r are coloured in round r + 1, after the
 // colours they depend on have been written.
 __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsigned long long seed,
                                                                  JpState st) {
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
+    __shared__ int s_last_part;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kJpWarps + wib;
     const int nwarps = gridDim.x * kJpWarps;
@@ -196,11 +198,28 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
             for (int item = blockIdx.x; item < n_huge * P; item += gridDim.x) {
                 const int t = item % n_huge, part = item / n_huge;
                 const int v = __ldcg(&st.list[2][in_list][t]);
+                const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
                 const int beg = g.off[v], end = g.off[v + 1];
                 const int L = (end - beg + P - 1) / P;
                 const int e0 = beg + part * L, e1 = min(end, e0 + L);
-                jp_pass(g, seed, st, v, prio_hash((unsigned long long)v ^ seed), e0, e1, wib, kJpWarps,
-                        st.huge_bm + (size_t)t * 32, cnt_next, out_list);
+                unsigned *gbm = st.huge_bm + (size_t)t * 32;
+                jp_pass(g, seed, st, v, hv, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
+                // the last of the P parts to finish takes the colour (no second barrier)
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0) s_last_part = atomicAdd(&st.huge_done[t], 1) == P - 1;
+                __syncthreads();
+                if (s_last_part && wib == 0) {
+                    __threadfence();
+                    const unsigned w0 = __ldcg(&gbm[lane]);
+                    __stcg(&gbm[lane], 0u);
+                    const int mex = warp_mex(g, seed, st, v, hv, w0, bm_warp[0]);
+                    if (lane == 0) {
+                        set_color(st, v, mex);
+                        st.huge_done[t] = 0;
+                    }
+                }
+                __syncthreads();
             }
         }
         for (int t = blockIdx.x; t < n_big; t += gridDim.x) {
@@ -238,19 +257,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
         if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
             trace4(st.tb, 0x200000000ull | (unsigned)r,
                    ((unsigned long long)n_small << 32) | (unsigned)(n_big + n_huge), gtimer(), 0);
-        if (n_huge > 0) {
-            for (int t = gw; t < n_huge; t += nwarps) {
-                const int v = __ldcg(&st.list[2][in_list][t]);
-                unsigned *gbm = st.huge_bm + (size_t)t * 32;
-                const unsigned w0 = __ldcg(&gbm[lane]);
-                __stcg(&gbm[lane], 0u);
-                const int mex = warp_mex(g, seed, st, v, prio_hash((unsigned long long)v ^ seed), w0,
-                                         bm_warp[wib]);
-                if (lane == 0) set_color(st, v, mex);
-                __syncwarp();
-            }
-            if (!grid_sync(st.bar, st.err)) return;
-        }
+
         if (__ldcg(&cnt_next[0]) + __ldcg(&cnt_next[1]) + __ldcg(&cnt_next[2]) == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *st.rounds = r + 1;
             return;
@@ -334,6 +341,8 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     const size_t max_huge = (size_t)g.A / kJpHuge + 1;  // each has >= kJpHuge arcs
     LV_TRY(dalloc_n(&st.huge_bm, 32 * max_huge, s));
     LV_CUDA(cudaMemsetAsync(st.huge_bm, 0, sizeof(unsigned) * 32 * max_huge, s));
+    LV_TRY(dalloc_n(&st.huge_done, max_huge, s));
+    LV_CUDA(cudaMemsetAsync(st.huge_done, 0, sizeof(int32_t) * max_huge, s));
     // counts[9], max_color, err, barrier (2 words), rounds
     int32_t *small_state = nullptr;
     LV_TRY(dalloc_n(&small_state, 16, s));
@@ -354,7 +363,8 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     unsigned long long seed_arg = seed;
     DGraph garg = g;
     void *args[] = {&garg, &seed_arg, &st};
-    LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms * blocks_per_sm),
+    // one block per SM: a second one per SM only adds barrier arrivals
+    LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms),
                                         dim3(kJpBlock), args, 0, s));
     LV_LAUNCH_CHECK();
     LV_CUDA(cudaMemcpyAsync(pinned, small_state + 9, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -367,6 +377,7 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     for (int k = 0; k < 3; ++k)
         for (int p = 0; p < 2; ++p) dfree(st.list[k][p], s);
     dfree(st.huge_bm, s);
+    dfree(st.huge_done, s);
     dfree(small_state, s);
     return LV_OK;
 }
