@@ -202,7 +202,7 @@ lv_status read_stats(lv_graph *h, const PhaseState &ps, IterStats *hs) {
     LV_CUDA(cudaMemcpyAsync(h->pinned, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, h->stream));
     LV_CUDA(cudaStreamSynchronize(h->stream));
     std::memcpy(hs, h->pinned, sizeof(IterStats));
-    if (hs->bar_err) return LV_ERR_TIMEOUT;
+    if (barrier_flags(hs->bar)) return LV_ERR_TIMEOUT;
     if (hs->err) return LV_ERR_HASH;
     return LV_OK;
 }
@@ -385,7 +385,6 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     LV_TRY(dalloc_n(&ps.moves[1], (size_t)nmax, s));
     LV_TRY(dalloc_n(&ps.stats, 1, s));
     ps.bar = &ps.stats->bar;
-    ps.bar_err = &ps.stats->bar_err;
     LV_TRY(dalloc_n(&newid, (size_t)nmax + 1, s));
     LV_TRY(dalloc_n(&color, (size_t)nmax, s));
     ps.two_m = h->two_m;

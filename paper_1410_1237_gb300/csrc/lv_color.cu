@@ -10,13 +10,15 @@
 // R-MAT and Chung-Lu inputs), so all rounds run inside one cooperative launch
 // separated by a bounded grid barrier.  Ready vertices are handled by size:
 // small (< 256 arcs) one warp each; big (< 4,096 arcs) one block each; huge
-// ones are split over all blocks, which mark a shared global colour bitmap,
-// and get their colour after a second barrier.
+// ones are split over the blocks left over, which mark a shared global colour
+// bitmap; the last of them to finish computes the colour.
 //
 // Vertex order: a stable radix sort of (colour, degree bin) keys, so each
 // colour class is split into the group / warp / CTA / hub bins of the sweep,
 // ascending vertex id inside each bucket.  Bins: groups of 1..32 lanes per
 // vertex (about lane_arcs arcs per lane), CTA, hub (several CTAs).
+#include <cstring>
+
 #include "lv_ops.cuh"
 
 namespace lv {
@@ -27,32 +29,33 @@ constexpr int kJpWarps = kJpBlock / 32;
 constexpr int kJpBig = 256;          // arcs: from here a vertex uses a whole block
 constexpr int kJpHuge = 4096;        // arcs: from here a vertex is split over blocks
 constexpr int kMexWindow = 1024;     // colours examined per pass of the mex search
+constexpr int kJpSmallU = 8;         // 32-arc chunks in flight per warp: a small vertex in one pass
 
-// device state; the ring of list lengths has 3 slots of {small, big, huge}
+// device state; the ring of list lengths has 3 slots of {small, big, huge}.
+// A list entry is {v, off[v], off[v + 1], 0}: whoever queues a vertex has
+// its row bounds already, so the round that colours it starts at its arcs.
 struct JpState {
     int32_t *cnt;          // higher-priority neighbours not yet processed
     int32_t *color;
-    int32_t *list[3][2];   // [kind][round parity]
+    int4 *list[3][2];      // [kind][round parity]
     int32_t *counts;       // [3 ring slots][3 kinds]
     int32_t *max_color;
     unsigned *huge_bm;     // 32-word first-window bitmap per slot of the huge list
     int32_t *huge_done;    // finished parts per slot of the huge list
-    GridBarrier *bar;
-    int *err;
+    GridBarrier *bar;      // flag 1: a wait expired; flag 2: more rounds than vertices
     int32_t *rounds;
     TraceBuf tb;
 };
 
-__device__ __forceinline__ int degree_of(const DGraph &g, int u) { return g.off[u + 1] - g.off[u]; }
-
-// append u to the next round's list of its kind; warp-aggregated
-__device__ __forceinline__ void push_ready(const DGraph &g, const JpState &st, int32_t *cnt_next,
-                                           int nxt_list, bool ready, int u) {
+// append u (arcs [beg, end)) to the next round's list of its kind;
+// warp-aggregated
+__device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next, int nxt_list,
+                                           bool ready, int u, int beg, int end) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int kind = 0;
     if (ready) {
-        const int d = degree_of(g, u);
+        const int d = end - beg;
         kind = d >= kJpHuge ? 2 : (d >= kJpBig ? 1 : 0);
     }
 #pragma unroll
@@ -63,7 +66,7 @@ __device__ __forceinline__ void push_ready(const DGraph &g, const JpState &st, i
             int pos = 0;
             if (lane == 0) pos = atomicAdd(&cnt_next[k], __popc(bm));
             pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (mine) st.list[k][nxt_list][pos + __popc(bm & lt)] = u;
+            if (mine) st.list[k][nxt_list][pos + __popc(bm & lt)] = make_int4(u, beg, end, 0);
         }
     }
 }
@@ -73,11 +76,12 @@ __device__ __forceinline__ void push_ready(const DGraph &g, const JpState &st, i
 // first window [0, kMexWindow) of bm (shared or global memory), and every
 // lower-priority neighbour's count is decremented (and the neighbour queued
 // for the next round when it reaches zero).  The two kinds of arcs are
-// disjoint, so one pass serves both.
+// disjoint, so one pass serves both.  The row bounds of a lower-priority
+// neighbour are loaded beside its decrement, for the queue entry.
+template <int kU>  // chunks of 32 arcs in flight per warp
 __device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState &st, int v,
                         unsigned long long hv, int e0, int e1, int wrank, int nw, unsigned *bm,
                         int32_t *cnt_next, int nxt_list) {
-    constexpr int kU = 4;  // chunks of 32 arcs in flight per warp
     const int lane = threadIdx.x & 31;
     const int stride = nw * 32;
     for (int b0 = e0 + wrank * 32; b0 < e1; b0 += kU * stride) {
@@ -92,18 +96,24 @@ __device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState 
         for (int u = 0; u < kU; ++u)
             higher[u] = uu[u] != v &&
                         prio_greater(prio_hash((unsigned long long)uu[u] ^ seed), uu[u], hv, v);
-        int res[kU];
+        int res[kU], ob[kU], oe[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
+            ob[u] = oe[u] = 0;
             if (uu[u] == v) res[u] = 0;
             else if (higher[u]) res[u] = __ldcg(&st.color[uu[u]]);
-            else res[u] = atomicSub(&st.cnt[uu[u]], 1);
+            else {
+                res[u] = atomicSub(&st.cnt[uu[u]], 1);
+                ob[u] = g.off[uu[u]];
+                oe[u] = g.off[uu[u] + 1];
+            }
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             if (uu[u] != v && higher[u] && res[u] < kMexWindow)
                 atomicOr(&bm[res[u] >> 5], 1u << (res[u] & 31));
-            push_ready(g, st, cnt_next, nxt_list, uu[u] != v && !higher[u] && res[u] == 1, uu[u]);
+            push_ready(st, cnt_next, nxt_list, uu[u] != v && !higher[u] && res[u] == 1, uu[u], ob[u],
+                       oe[u]);
         }
     }
 }
@@ -162,49 +172,51 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
             st.cnt[v] = c;
             st.color[v] = -1;
         }
-        push_ready(g, st, st.counts, 0, lane == 0 && c == 0, v);  // round 0, ring slot 0
+        push_ready(st, st.counts, 0, lane == 0 && c == 0, v, beg, end);  // round 0, ring slot 0
     }
 }
 
-// All rounds of Jones-Plassmann in one cooperative launch.  Round r:
-//   stage 1  huge ready vertices: split over P = grid / n_huge blocks each,
-//            which mark a global bitmap and release lower-priority
-//            neighbours; big ones: one block each (mark, release, colour);
-//            small ones: one warp each
-//   barrier
-//            the last block to finish a huge vertex's parts turns its
-//            bitmap into its colour and clears it
-// The vertices released in round r are coloured in round r + 1, after the
-// colours they depend on have been written.
+// All rounds of Jones-Plassmann in one cooperative launch.  Round r colours
+// the vertices queued in round r - 1, in units of one block each:
+//   huge  split over P blocks each, which mark a global bitmap and release
+//         lower-priority neighbours; the last of the P to finish (a
+//         per-vertex arrival counter) turns the bitmap into the colour
+//   big   one block each (mark, release, colour)
+//   small one warp each, 32 to a block
+// Huge vertices get the blocks that big and small ones leave (P >= 1), so
+// a block takes one unit per round unless the units outnumber the blocks.
+// A grid barrier ends the round; the vertices released in round r are
+// coloured in round r + 1, after the colours they depend on have been
+// written.
 __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsigned long long seed,
                                                                  JpState st) {
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
     __shared__ int s_last_part;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * kJpWarps + wib;
-    const int nwarps = gridDim.x * kJpWarps;
+    unsigned bar_passed = 0;
+    int n_small = __ldcg(&st.counts[0]), n_big = __ldcg(&st.counts[1]),
+        n_huge = __ldcg(&st.counts[2]);
     for (int r = 0;; ++r) {
-        const int cur = r % 3, nxt = (r + 1) % 3, clr = (r + 2) % 3;
+        const int nxt = (r + 1) % 3, clr = (r + 2) % 3;
         if (blockIdx.x == 0 && threadIdx.x < 3) st.counts[3 * clr + threadIdx.x] = 0;
-        const int n_small = __ldcg(&st.counts[3 * cur]);
-        const int n_big = __ldcg(&st.counts[3 * cur + 1]);
-        const int n_huge = __ldcg(&st.counts[3 * cur + 2]);
         const int in_list = r & 1, out_list = (r + 1) & 1;
         int32_t *cnt_next = st.counts + 3 * nxt;
         const unsigned long long tr0 = LV_TRACE_ON ? gtimer() : 0;
-        if (n_huge > 0) {
-            const int P = max(1, (int)gridDim.x / n_huge);
-            for (int item = blockIdx.x; item < n_huge * P; item += gridDim.x) {
-                const int t = item % n_huge, part = item / n_huge;
-                const int v = __ldcg(&st.list[2][in_list][t]);
+        const int small_units = (n_small + kJpWarps - 1) / kJpWarps;
+        const int P = n_huge > 0 ? max(1, ((int)gridDim.x - n_big - small_units) / n_huge) : 0;
+        const int huge_units = n_huge * P;
+        const int units = huge_units + n_big + small_units;
+        for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
+            if (unit < huge_units) {
+                const int t = unit % n_huge, part = unit / n_huge;
+                const int4 it = __ldcg(&st.list[2][in_list][t]);
+                const int v = it.x;
                 const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
-                const int beg = g.off[v], end = g.off[v + 1];
-                const int L = (end - beg + P - 1) / P;
-                const int e0 = beg + part * L, e1 = min(end, e0 + L);
+                const int L = (it.z - it.y + P - 1) / P;
+                const int e0 = it.y + part * L, e1 = min(it.z, e0 + L);
                 unsigned *gbm = st.huge_bm + (size_t)t * 32;
-                jp_pass(g, seed, st, v, hv, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
-                // the last of the P parts to finish takes the colour (no second barrier)
+                jp_pass<4>(g, seed, st, v, hv, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
                 __threadfence();
                 __syncthreads();
                 if (threadIdx.x == 0) s_last_part = atomicAdd(&st.huge_done[t], 1) == P - 1;
@@ -220,50 +232,54 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
                     }
                 }
                 __syncthreads();
+            } else if (unit < huge_units + n_big) {
+                const int4 it = __ldcg(&st.list[1][in_list][unit - huge_units]);
+                const int v = it.x;
+                const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+                if (threadIdx.x < 32) bm_cta[threadIdx.x] = 0u;
+                __syncthreads();
+                jp_pass<4>(g, seed, st, v, hv, it.y, it.z, wib, kJpWarps, bm_cta, cnt_next, out_list);
+                __syncthreads();
+                if (wib == 0) {
+                    const int mex = warp_mex(g, seed, st, v, hv, bm_cta[lane], bm_warp[0]);
+                    if (lane == 0) set_color(st, v, mex);
+                }
+                __syncthreads();
+            } else {
+                const int t = (unit - huge_units - n_big) * kJpWarps + wib;
+                if (t < n_small) {
+                    const int4 it = __ldcg(&st.list[0][in_list][t]);
+                    const int v = it.x;
+                    const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+                    unsigned *bm = bm_warp[wib];
+                    bm[lane] = 0u;
+                    __syncwarp();
+                    jp_pass<kJpSmallU>(g, seed, st, v, hv, it.y, it.z, 0, 1, bm, cnt_next, out_list);
+                    __syncwarp();
+                    const unsigned w0 = bm[lane];
+                    __syncwarp();
+                    const int mex = warp_mex(g, seed, st, v, hv, w0, bm);
+                    if (lane == 0) set_color(st, v, mex);
+                    __syncwarp();
+                }
             }
-        }
-        for (int t = blockIdx.x; t < n_big; t += gridDim.x) {
-            const int v = __ldcg(&st.list[1][in_list][t]);
-            const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
-            if (threadIdx.x < 32) bm_cta[threadIdx.x] = 0u;
-            __syncthreads();
-            jp_pass(g, seed, st, v, hv, g.off[v], g.off[v + 1], wib, kJpWarps, bm_cta, cnt_next,
-                    out_list);
-            __syncthreads();
-            if (wib == 0) {
-                const int mex = warp_mex(g, seed, st, v, hv, bm_cta[lane], bm_warp[0]);
-                if (lane == 0) set_color(st, v, mex);
-            }
-            __syncthreads();
-        }
-        for (int t = gw; t < n_small; t += nwarps) {
-            const int v = __ldcg(&st.list[0][in_list][t]);
-            const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
-            unsigned *bm = bm_warp[wib];
-            bm[lane] = 0u;
-            __syncwarp();
-            jp_pass(g, seed, st, v, hv, g.off[v], g.off[v + 1], 0, 1, bm, cnt_next, out_list);
-            __syncwarp();
-            const unsigned w0 = bm[lane];
-            __syncwarp();
-            const int mex = warp_mex(g, seed, st, v, hv, w0, bm);
-            if (lane == 0) set_color(st, v, mex);
-            __syncwarp();
         }
         const unsigned long long tr1 = LV_TRACE_ON ? gtimer() : 0;
         if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 8)
             trace4(st.tb, 0x100000000ull | (unsigned)r, (unsigned long long)blockIdx.x, tr0, tr1);
-        if (!grid_sync(st.bar, st.err)) return;
+        if (!grid_sync(st.bar, bar_passed)) return;
         if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
             trace4(st.tb, 0x200000000ull | (unsigned)r,
                    ((unsigned long long)n_small << 32) | (unsigned)(n_big + n_huge), gtimer(), 0);
-
-        if (__ldcg(&cnt_next[0]) + __ldcg(&cnt_next[1]) + __ldcg(&cnt_next[2]) == 0) {
+        n_small = __ldcg(&cnt_next[0]);
+        n_big = __ldcg(&cnt_next[1]);
+        n_huge = __ldcg(&cnt_next[2]);
+        if (n_small + n_big + n_huge == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *st.rounds = r + 1;
             return;
         }
         if (r > g.n) {  // every round colours at least one vertex
-            if (threadIdx.x == 0) atomicExch(st.err, 2);
+            if (threadIdx.x == 0) barrier_raise(st.bar, 2);
             return;
         }
     }
@@ -343,15 +359,14 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     LV_CUDA(cudaMemsetAsync(st.huge_bm, 0, sizeof(unsigned) * 32 * max_huge, s));
     LV_TRY(dalloc_n(&st.huge_done, max_huge, s));
     LV_CUDA(cudaMemsetAsync(st.huge_done, 0, sizeof(int32_t) * max_huge, s));
-    // counts[9], max_color, err, barrier (2 words), rounds
+    // counts[9], max_color, barrier (2 words, 8-byte aligned), rounds
     int32_t *small_state = nullptr;
     LV_TRY(dalloc_n(&small_state, 16, s));
     LV_CUDA(cudaMemsetAsync(small_state, 0, 16 * sizeof(int32_t), s));
     st.counts = small_state;
     st.max_color = small_state + 9;
-    st.err = small_state + 10;
-    st.bar = reinterpret_cast<GridBarrier *>(small_state + 11);
-    st.rounds = small_state + 13;
+    st.bar = reinterpret_cast<GridBarrier *>(small_state + 10);
+    st.rounds = small_state + 12;
     jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, st);
     LV_LAUNCH_CHECK();
     static int blocks_per_sm = 0;
@@ -367,12 +382,14 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms),
                                         dim3(kJpBlock), args, 0, s));
     LV_LAUNCH_CHECK();
-    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 9, 5 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 9, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
-    if (pinned[1] == 1) return LV_ERR_TIMEOUT;
-    if (pinned[1] != 0) return LV_ERR_STATE;
+    GridBarrier bar;
+    std::memcpy(&bar, pinned + 1, sizeof bar);
+    if (barrier_flags(bar) & 1) return LV_ERR_TIMEOUT;
+    if (barrier_flags(bar) != 0) return LV_ERR_STATE;
     *num_colors = pinned[0] + 1;
-    *rounds = pinned[4];
+    *rounds = pinned[3];
     dfree(st.cnt, s);
     for (int k = 0; k < 3; ++k)
         for (int p = 0; p < 2; ++p) dfree(st.list[k][p], s);

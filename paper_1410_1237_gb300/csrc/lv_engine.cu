@@ -595,7 +595,6 @@ lv_status Engine::phase_run() {
     LV_TRY(dalloc_n(&ps.move_count, 4, s));
     LV_TRY(dalloc_n(&newid, (size_t)n + 1, s));
     ps.bar = &ps.stats->bar;
-    ps.bar_err = &ps.stats->bar_err;
     LV_CUDA(cudaMemsetAsync(ps.act, 0, sizeof(int32_t), s));
     // per-phase scratch, freed below
     struct Scratch {
@@ -726,7 +725,7 @@ lv_status Engine::phase_run() {
         LV_CUDA(cudaMemcpyAsync(pin_stats, ps.stats, sizeof(IterStats), cudaMemcpyDeviceToHost, s));
         LV_CUDA(cudaMemcpyAsync(pin_u64, sc.gsum, gsum_bytes, cudaMemcpyDeviceToHost, s));
         LV_CUDA(cudaStreamSynchronize(s));
-        if (pin_stats->bar_err) return LV_ERR_TIMEOUT;
+        if (barrier_flags(pin_stats->bar)) return LV_ERR_TIMEOUT;
         if (pin_stats->err) return LV_ERR_HASH;
         for (int32_t q = 0; q < G; ++q) {
             EngineGraph &t = graphs[q];

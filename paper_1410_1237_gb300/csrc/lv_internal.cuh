@@ -154,38 +154,58 @@ __device__ __forceinline__ bool prio_greater(unsigned long long hu, int u, unsig
 }
 
 // ------------------------------------------------------------ grid barrier
-// Barrier across all blocks of a cooperative (co-resident) launch, on a
-// monotonic ticket counter: the k-th barrier of a launch completes when the
-// counter reaches k * gridDim.x, so arriving is one atomic and nobody resets
-// anything.  The counter starts at 0 for every launch (callers clear it).
-// The wait is bounded: a block that waits longer than the limit sets *err
-// and gets false, and callers then return, so a fault cannot hang the device.
-struct GridBarrier {
-    unsigned int count;
-    unsigned int unused;
+// Barrier across all blocks of a cooperative (co-resident) launch.  One
+// 64-bit word holds the arrivals (bits 0..47, monotonic: the k-th barrier of
+// a launch completes when they reach k * gridDim.x) and error flags (bits
+// 48..63).  Callers clear the word before every launch, and each block keeps
+// its own count of barriers passed, so arriving is one fire-and-forget
+// release add and waiting polls the word with acquire loads, which see the
+// error flags in the same load.  The wait is bounded: a block that waits
+// longer than the limit raises flag 1 and gets false, as does every block
+// that sees a flag raised; callers then return, so a fault cannot hang the
+// device.
+struct alignas(8) GridBarrier {
+    unsigned long long word;
 };
+constexpr int kBarrierFlagShift = 48;
+constexpr unsigned long long kBarrierCountMask = (1ull << kBarrierFlagShift) - 1;
 constexpr unsigned long long kBarrierSpinLimit = 1ull << 27;  // x ~20-100 ns sleeps
 
-__device__ __forceinline__ bool grid_sync(GridBarrier *gb, int *err) {
+__host__ __device__ __forceinline__ int barrier_flags(const GridBarrier &b) {
+    return (int)(b.word >> kBarrierFlagShift);
+}
+
+// raise error flag(s) `f` (1: a wait expired; others are the caller's)
+__device__ __forceinline__ void barrier_raise(GridBarrier *gb, int f) {
+    atomicOr(&gb->word, (unsigned long long)f << kBarrierFlagShift);
+}
+
+// `passed` counts the barriers this block has completed in this launch
+// (start it at 0; only thread 0's copy is used)
+__device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned &passed) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        const unsigned int ticket = atomicAdd(&gb->count, 1u);
-        const unsigned int target = (ticket / gridDim.x + 1u) * gridDim.x;
-        volatile unsigned int *vc = &gb->count;
+        const unsigned long long target = (unsigned long long)(++passed) * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&gb->word) : "memory");
         unsigned long long spins = 0;
-        while ((int)(*vc - target) < 0) {
+        for (;;) {
+            unsigned long long w;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(&gb->word) : "memory");
+            if (w >> kBarrierFlagShift) {
+                ok = 0;
+                break;
+            }
+            if ((w & kBarrierCountMask) >= target) break;
             if (++spins > kBarrierSpinLimit) {
                 ok = 0;
-                atomicExch(err, 1);
+                barrier_raise(gb, 1);
                 break;
             }
             __nanosleep(20);
         }
-        __threadfence();
-        s_ok = ok && (*(volatile int *)err == 0);
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;

@@ -65,9 +65,9 @@ struct IterStats {
     unsigned long long sum_a2;     // sum over communities of a_C^2
     int moved;
     int err;                       // a hash probe bound was exceeded
-    GridBarrier bar;               // barrier state of the persistent sweep (reset with the stats)
-    int bar_err;                   // a grid barrier wait expired
     int max_occ;                   // largest distinct-label count of a hub this sweep
+    int pad;
+    GridBarrier bar;               // barrier of the persistent sweep (reset with the stats)
 };
 struct PhaseState {
     DGraph g;
@@ -83,7 +83,6 @@ struct PhaseState {
     long long g_total = 0;          // classes swept so far in the phase (buffer parity)
     IterStats *stats = nullptr;
     GridBarrier *bar = nullptr;   // &stats->bar
-    int *bar_err = nullptr;       // &stats->bar_err
     long long two_m = 0;
     // batched runs over a disjoint union of graphs (all null otherwise): the
     // sweep skips graphs whose active flag is 0 and sums the modularity terms

@@ -86,7 +86,6 @@ struct Sweep {
     int n;
     long long two_m;
     GridBarrier *bar;
-    int *err;
     TraceBuf tb;
     // batched runs (disjoint union of graphs); gid == nullptr otherwise
     const int32_t *__restrict__ gid;       // graph of each vertex
@@ -676,6 +675,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
     int *region = dyn + wib * kWarpRegion;
     const int gthread = blockIdx.x * kSwBlock + threadIdx.x;
     const int nthreads = gridDim.x * kSwBlock;
+    unsigned bar_passed = 0;
     for (int q = 0; q < s.n_act; ++q) {
         const int c = s.act[q];
         const long long g = s.g0 + q;
@@ -789,7 +789,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g], gtimer());
 #endif
         if (n_hub > 0 && !hub_solo) {
-            if (!grid_sync(s.bar, s.err)) return;
+            if (!grid_sync(s.bar, bar_passed)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
                 hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
 #ifdef LV_TRACE
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g + 1], gtimer());
 #endif
         if (s.coloured || q + 1 < s.n_act)
-            if (!grid_sync(s.bar, s.err)) return;
+            if (!grid_sync(s.bar, bar_passed)) return;
     }
     if (s.coloured && blockIdx.x == 0 && threadIdx.x == 0 && s.n_act > 0)
         s.move_count[3 * s.n_act] = __ldcg(&s.move_count[s.n_act - 1]);  // carry for the next launch
@@ -931,7 +931,6 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.n = ps.g.n;
     a.two_m = ps.two_m;
     a.bar = ps.bar;
-    a.err = ps.bar_err;
     a.tb = trace_buffer();
     a.gid = ps.gid;
     a.two_m_g = ps.two_m_g;

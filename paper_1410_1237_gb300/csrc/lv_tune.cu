@@ -57,7 +57,7 @@ lv_status tune_bins(PhaseState &ps, const BinLimits &first, void *zero, size_t z
             IterStats hs;
             if (cudaMemcpy(&hs, ps.stats, sizeof hs, cudaMemcpyDeviceToHost) != cudaSuccess)
                 st = LV_ERR_CUDA;
-            else if (hs.bar_err)
+            else if (barrier_flags(hs.bar))
                 st = LV_ERR_TIMEOUT;
             else if (hs.err)
                 st = LV_ERR_HASH;
