@@ -180,6 +180,12 @@ __device__ __forceinline__ void barrier_raise(GridBarrier *gb, int f) {
     atomicOr(&gb->word, (unsigned long long)f << kBarrierFlagShift);
 }
 
+__device__ __forceinline__ int ld_acquire_i32(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // `passed` counts the barriers this block has completed in this launch
 // (start it at 0; only thread 0's copy is used)
 __device__ __forceinline__ bool grid_sync(GridBarrier *gb, unsigned &passed) {

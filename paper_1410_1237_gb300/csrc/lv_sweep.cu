@@ -438,14 +438,24 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 // hub's global table once (so a popular label costs one global atomic per
 // chunk, not one per warp).  Global first probes are compare-and-swaps issued
 // for all of a thread's labels at once; collisions fall back to linear
-// probing.  Claimed slots are appended to the hub's occupied list with one
-// counter update per warp.
+// probing.
+//
+// With `par` (every chunk of the class's hubs has a block of its own), the
+// blocks of a hub then wait for all of its chunks (a bounded wait on the
+// hub's arrival counter), each evaluates the slots it claimed (at most
+// kHubChunk, one pass) and stores a partial best, and the last to finish
+// combines the partials and decides: no grid barrier, and the evaluation is
+// spread over the hub's blocks.  Chunks are handed out before any other item
+// of the class and a block holding one claims nothing else until it is done,
+// so every block waited for is running.  Otherwise claimed slots are
+// appended to the hub's occupied list (one counter update per warp) for the
+// evaluation after a grid barrier.
 constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
-constexpr int kHubSoloChunks = 24;             // largest hub decided by one block
-__device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc);
+__device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
+                            int ki, long long tm, BlockRed &red, Acc &acc);
 __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, int *dyn,
-                          BlockRed &red, Acc &acc, bool solo) {
-    __shared__ int s_last_chunk;
+                          BlockRed &red, Acc &acc, bool par) {
+    __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
     const int p = lo + a;
@@ -454,9 +464,8 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const int beg = s.off[i], end = s.off[i + 1];
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
     int2 *tab = s.hub_table + s.hub_off[p];
-    int32_t *occ = s.hub_occ + s.hub_off[p];
-    int32_t *occ_cnt = s.hub_cnt + p;
-    const int start = beg + (chunk - s.hub_chunk_off[p]) * kHubChunk;
+    const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
+    const int start = beg + (chunk - first) * kHubChunk;
     const int stop = min(end, start + kHubChunk);
     int *key = dyn, *val = dyn + kHubSmemSlots;
     for (int sl = threadIdx.x; sl < kHubSmemSlots; sl += kSwBlock) {
@@ -466,19 +475,19 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     __syncthreads();
     insert_arcs<1>(s, i, start + threadIdx.x, stop, kSwBlock, key, val, kHubSmemSlots - 1, acc);
     __syncthreads();
-    static_assert(kHubSmemSlots % (kU * kSwBlock) == 0, "slots per pass");
-    for (int s0 = threadIdx.x; s0 < kHubSmemSlots; s0 += kU * kSwBlock) {
+    static_assert(kHubSmemSlots == kU * kSwBlock, "one pass over the chunk's table");
+    int claimed[kU];
+    {
         int cl[kU], sum[kU];
         unsigned hslot[kU];
         int prev[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            cl[u] = key[s0 + u * kSwBlock];
-            sum[u] = val[s0 + u * kSwBlock];
+            cl[u] = key[threadIdx.x + u * kSwBlock];
+            sum[u] = val[threadIdx.x + u * kSwBlock];
             hslot[u] = hash32(cl[u]) & mask;
             prev[u] = cl[u] != kEmpty ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
         }
-        int claimed[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             claimed[u] = -1;
@@ -496,7 +505,9 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
             if (done) atomicAdd(&tab[h].y, sum[u]);
             else acc.err = 1;
         }
-        // one occupied-list reservation per warp for all its claims
+    }
+    if (!par) {  // one occupied-list reservation per warp for all its claims
+        int32_t *occ = s.hub_occ + s.hub_off[p];
         int mine = 0;
 #pragma unroll
         for (int u = 0; u < kU; ++u) mine += claimed[u] >= 0 ? 1 : 0;
@@ -509,24 +520,76 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
         const int total = __shfl_sync(0xffffffffu, incl, 31);
         if (total) {
             int base = 0;
-            if (lane == 31) base = atomicAdd(occ_cnt, total);
+            if (lane == 31) base = atomicAdd(s.hub_cnt + p, total);
             base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
 #pragma unroll
             for (int u = 0; u < kU; ++u)
                 if (claimed[u] >= 0) __stcg(&occ[base++], claimed[u]);
         }
+        return;
     }
-    if (solo) {  // the class's only hub: the block finishing its last chunk decides
-        const int nch = s.hub_chunk_off[p + 1] - s.hub_chunk_off[p];
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) s_last_chunk = atomicAdd(&s.hub_done[p], 1) == nch - 1;
-        __syncthreads();
-        if (s_last_chunk) {
-            __threadfence();
-            hub_decide_solo(s, cc, p, red, acc);
+    // wait until every chunk of the hub has added its labels
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&s.hub_done[p], 1);
+        int ok = 1;
+        for (unsigned long long spins = 0; ld_acquire_i32(&s.hub_done[p]) < nch;) {
+            if (++spins > kBarrierSpinLimit) {
+                ok = 0;
+                barrier_raise(s.bar, 1);
+                break;
+            }
+            __nanosleep(20);
+        }
+        s_flag = ok;
+    }
+    __syncthreads();
+    if (!s_flag) return;
+    const long long tm = tm_of(s, i);
+    const int ci = ldC(s, i), ki = s.k[i];
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    {
+        int2 kv[kU];
+        unsigned long long cm[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) kv[u] = claimed[u] >= 0 ? __ldcg(&tab[claimed[u]]) : make_int2(kEmpty, 0);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (claimed[u] >= 0) __stcg(&tab[claimed[u]], make_int2(kEmpty, 0));
+            cm[u] = (kv[u].x != kEmpty && kv[u].x != ci) ? __ldcg(&cc.xr[kv[u].x]) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (kv[u].x == kEmpty) continue;
+            if (kv[u].x == ci) {
+                e_old = kv[u].y;
+                continue;
+            }
+            best_take(b, tm * (long long)kv[u].y - (long long)ki * comm_a(cm[u]), kv[u].x,
+                      comm_size(cm[u]), kv[u].y);
         }
     }
+    block_best(b, e_old, red);
+    if (threadIdx.x == 0) {
+        HubPart hp;
+        hp.s = b.s;
+        hp.c = b.c;
+        hp.z = b.size;
+        hp.e = b.e;
+        hp.eo = e_old;
+        s.hub_part[chunk] = hp;
+        __threadfence();
+        s_flag = atomicAdd(&s.hub_done[p], 1) == 2 * nch - 1;
+    }
+    __syncthreads();
+    if (s_flag) {  // block-uniform: the last block combines the partials
+        __threadfence();
+        hub_combine(s, cc, p, first, nch, i, ci, ki, tm, red, acc);
+    }
+    __syncthreads();
 }
 
 // Evaluates (and resets) the hub table slots listed in occ[t0, t1): the best
@@ -563,33 +626,26 @@ __device__ __forceinline__ void hub_eval(const Sweep &s, const Cls &cc, int2 *ta
     }
 }
 
-// Decision of a hub whose table is complete: the last arc chunk of a class's
-// only hub evaluates every occupied slot with its whole block and decides, so
-// the class needs no grid barrier before the hub's move.
-__device__ void hub_decide_solo(const Sweep &s, const Cls &cc, int p, BlockRed &red, Acc &acc) {
-    const int i = s.order[p];
-    const long long tm = tm_of(s, i);
-    const int ci = ldC(s, i), ki = s.k[i];
-    const unsigned long long cmi = __ldcg(&cc.xr[ci]);
-    const int lp = s.loop[i];
-    int2 *tab = s.hub_table + s.hub_off[p];
-    const int32_t *occ = s.hub_occ + s.hub_off[p];
-    const int n_occ = __ldcg(&s.hub_cnt[p]);
-    Best b;
-    best_init(b);
-    int e_old = 0;
-    hub_eval(s, cc, tab, occ, 0, n_occ, ci, ki, tm, b, e_old);
-    block_best(b, e_old, red);
+// Combines the partial bests of a hub's nch chunks (its counter is reset)
+// and decides the hub's move; the whole block takes part, thread 0 decides.
+__device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
+                            int ki, long long tm, BlockRed &red, Acc &acc) {
+    Best t;
+    best_init(t);
+    int eo = 0;
+    for (int q = first + threadIdx.x; q < first + nch; q += kSwBlock) {
+        const HubPart *hq = &s.hub_part[q];
+        best_take(t, __ldcg(&hq->s), __ldcg(&hq->c), __ldcg(&hq->z), __ldcg(&hq->e));
+        eo += __ldcg(&hq->eo);
+    }
+    block_best(t, eo, red);
     if (threadIdx.x == 0) {
-        __stcg(&s.hub_cnt[p], 0);
         __stcg(&s.hub_done[p], 0);
-        atomicMax(&s.stats->max_occ, n_occ);
         int ein = 0;
-        const bool mv = decide(ci, ki, cmi, lp, tm, b, e_old, acc, ein);
-        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+        const bool mv = decide(ci, ki, __ldcg(&cc.xr[ci]), s.loop[i], tm, t, eo, acc, ein);
+        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
         add_terms(s, acc, i, ein, mv);
     }
-    __syncthreads();
 }
 
 // Hub decision, one block per chunk of the occupied list: evaluates its
@@ -629,24 +685,11 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
     __syncthreads();
     if (s_last) {  // block-uniform: the last block combines the partials in parallel
         __threadfence();
-        Best t;
-        best_init(t);
-        int eo = 0;
-        for (int q = first + threadIdx.x; q < first + nch; q += kSwBlock) {
-            const HubPart *hq = &s.hub_part[q];
-            best_take(t, __ldcg(&hq->s), __ldcg(&hq->c), __ldcg(&hq->z), __ldcg(&hq->e));
-            eo += __ldcg(&hq->eo);
-        }
-        block_best(t, eo, red);
         if (threadIdx.x == 0) {
             __stcg(&s.hub_cnt[p], 0);
-            __stcg(&s.hub_done[p], 0);
             atomicMax(&s.stats->max_occ, n_occ);
-            int ein = 0;
-            const bool mv = decide(ci, ki, __ldcg(&cc.xr[ci]), s.loop[i], tm, t, eo, acc, ein);
-            if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
-            add_terms(s, acc, i, ein, mv);
         }
+        hub_combine(s, cc, p, first, nch, i, ci, ki, tm, red, acc);
     }
     __syncthreads();
 }
@@ -685,6 +728,8 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         cc.xw = s.coloured && (g & 1) ? s.comm0 : s.comm1;
         cc.mw = s.coloured && (g & 1) ? s.moves1 : s.moves0;
         cc.cnt = s.move_count + q;
+        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
+            trace4(s.tb, 0x600000000ull | (unsigned)q, (unsigned long long)g, gtimer(), 0);
         if (s.coloured) {
             // bring the write buffer up to date with the previous class's moves
             const int4 *mp = (g & 1) ? s.moves0 : s.moves1;
@@ -695,17 +740,16 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
                 atomicAdd(&cc.xw[m.z], comm_join(m.w));
             }
         }
-        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
-            trace4(s.tb, 0x600000000ull | (unsigned)q, (unsigned long long)g, gtimer(), 0);
         const int32_t *bo = s.bucket_off + c * (kBins + 1);
         const int b_cta = bo[kBinCta], b_hub = bo[kBinHub], b_end = bo[kBins];
         const int32_t *ca = s.chunk_at + c * (kBins + 1);
         const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
         const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
-        // a class's only hub, if it is not too large, is decided by the block
-        // that finishes its last chunk (no grid barrier); larger ones are
-        // evaluated by many blocks after a barrier
-        const bool hub_solo = n_hub == 1 && nchunks <= kHubSoloChunks;
+        // in coloured sweeps hubs are decided by their chunk blocks (no grid
+        // barrier) when every chunk gets a block of its own; otherwise (and
+        // in a one-class sweep, which has its barrier anyway) many blocks
+        // evaluate them after a barrier
+        const bool hub_par = s.coloured && n_hub > 0 && nchunks <= (int)gridDim.x;
         // block items, handed out by a class counter (the next index is
         // fetched while the current item runs)
         const int n_bitems = nchunks + n_cta;
@@ -715,12 +759,15 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             __syncthreads();
             int it = s_item;
             while (it < n_bitems) {
+                // a block holding a chunk that waits for its hub claims
+                // nothing else meanwhile
+                const bool wait_item = hub_par && it < nchunks;
                 int nxt = 0;
-                if (threadIdx.x == 0) nxt = atomicAdd(bctr, 1);
+                if (threadIdx.x == 0 && !wait_item) nxt = atomicAdd(bctr, 1);
 #ifdef LV_TRACE
                 const unsigned long long ti0 = gtimer();
 #endif
-                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_solo);
+                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_par);
                 else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
                 __syncthreads();
 #ifdef LV_TRACE
@@ -731,7 +778,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
                            (unsigned long long)g, (unsigned long long)dd, gtimer() - ti0);
                 }
 #endif
-                if (threadIdx.x == 0) s_item = nxt;
+                if (threadIdx.x == 0) s_item = wait_item ? atomicAdd(bctr, 1) : nxt;
                 __syncthreads();
                 it = s_item;
             }
@@ -750,6 +797,11 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         // the class counter sees few atomics even with millions of items
         int32_t *wctr = s.move_count + 2 * s.n_act + q;
         const int claim = max(1, item_end[0] / (gridDim.x * kSwWarps * 8));
+        if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
+            trace4(s.tb, 0x900000000ull | (unsigned)q, (unsigned long long)g,
+                   (unsigned long long)n_hub | ((unsigned long long)nchunks << 20) |
+                       ((unsigned long long)hub_par << 40),
+                   (unsigned long long)n_cta | ((unsigned long long)item_end[0] << 32));
         int it = 0;
         if (item_end[0] > 0) {
             if (lane == 0) it = atomicAdd(wctr, claim);
@@ -788,7 +840,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         if (threadIdx.x == 0 && g < (long long)(kTraceCap / 4))
             atomicMax(&s.tb.buf[kTraceCap / 2 + 2 * g], gtimer());
 #endif
-        if (n_hub > 0 && !hub_solo) {
+        if (n_hub > 0 && !hub_par) {
             if (!grid_sync(s.bar, bar_passed)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
                 hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
