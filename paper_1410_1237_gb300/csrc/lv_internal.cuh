@@ -180,6 +180,16 @@ __device__ __forceinline__ void barrier_raise(GridBarrier *gb, int f) {
     atomicOr(&gb->word, (unsigned long long)f << kBarrierFlagShift);
 }
 
+__device__ __forceinline__ void red_release_add_i32(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int atom_acq_rel_add_i32(int *p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ int ld_acquire_i32(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

@@ -452,7 +452,8 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 // evaluation after a grid barrier.
 constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
 __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
-                            int ki, long long tm, BlockRed &red, Acc &acc);
+                            int ki, unsigned long long cmi, int lp, long long tm, BlockRed &red,
+                            Acc &acc);
 __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, int *dyn,
                           BlockRed &red, Acc &acc, bool par) {
     __shared__ int s_flag;
@@ -465,6 +466,10 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
     int2 *tab = s.hub_table + s.hub_off[p];
     const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
+    // the hub's own terms, loaded ahead of the arcs (used after the wait)
+    const long long tm = tm_of(s, i);
+    const int ci = ldC(s, i), ki = s.k[i], lp = s.loop[i];
+    const unsigned long long cmi = __ldcg(&cc.xr[ci]);
     const int start = beg + (chunk - first) * kHubChunk;
     const int stop = min(end, start + kHubChunk);
     int *key = dyn, *val = dyn + kHubSmemSlots;
@@ -529,10 +534,9 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
         return;
     }
     // wait until every chunk of the hub has added its labels
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        atomicAdd(&s.hub_done[p], 1);
+        red_release_add_i32(&s.hub_done[p], 1);
         int ok = 1;
         for (unsigned long long spins = 0; ld_acquire_i32(&s.hub_done[p]) < nch;) {
             if (++spins > kBarrierSpinLimit) {
@@ -546,8 +550,6 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     }
     __syncthreads();
     if (!s_flag) return;
-    const long long tm = tm_of(s, i);
-    const int ci = ldC(s, i), ki = s.k[i];
     Best b;
     best_init(b);
     int e_old = 0;
@@ -581,14 +583,11 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
         hp.e = b.e;
         hp.eo = e_old;
         s.hub_part[chunk] = hp;
-        __threadfence();
-        s_flag = atomicAdd(&s.hub_done[p], 1) == 2 * nch - 1;
+        s_flag = atom_acq_rel_add_i32(&s.hub_done[p], 1) == 2 * nch - 1;
     }
     __syncthreads();
-    if (s_flag) {  // block-uniform: the last block combines the partials
-        __threadfence();
-        hub_combine(s, cc, p, first, nch, i, ci, ki, tm, red, acc);
-    }
+    if (s_flag)  // block-uniform: the last block combines the partials
+        hub_combine(s, cc, p, first, nch, i, ci, ki, cmi, lp, tm, red, acc);
     __syncthreads();
 }
 
@@ -629,7 +628,8 @@ __device__ __forceinline__ void hub_eval(const Sweep &s, const Cls &cc, int2 *ta
 // Combines the partial bests of a hub's nch chunks (its counter is reset)
 // and decides the hub's move; the whole block takes part, thread 0 decides.
 __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
-                            int ki, long long tm, BlockRed &red, Acc &acc) {
+                            int ki, unsigned long long cmi, int lp, long long tm, BlockRed &red,
+                            Acc &acc) {
     Best t;
     best_init(t);
     int eo = 0;
@@ -642,7 +642,7 @@ __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int
     if (threadIdx.x == 0) {
         __stcg(&s.hub_done[p], 0);
         int ein = 0;
-        const bool mv = decide(ci, ki, __ldcg(&cc.xr[ci]), s.loop[i], tm, t, eo, acc, ein);
+        const bool mv = decide(ci, ki, cmi, lp, tm, t, eo, acc, ein);
         if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, t.c, ki);
         add_terms(s, acc, i, ein, mv);
     }
@@ -689,7 +689,7 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
             __stcg(&s.hub_cnt[p], 0);
             atomicMax(&s.stats->max_occ, n_occ);
         }
-        hub_combine(s, cc, p, first, nch, i, ci, ki, tm, red, acc);
+        hub_combine(s, cc, p, first, nch, i, ci, ki, __ldcg(&cc.xr[ci]), s.loop[i], tm, red, acc);
     }
     __syncthreads();
 }
