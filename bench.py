@@ -43,8 +43,8 @@ MEASURED_TRAFFIC = {
     "rmat20": {"bytes": 327_858_688 + 16_245_760,
                "scope": "one phase-0 sweep launch (iteration 3, 232 colour classes)"},
     # batched sweep: traffic / algorithmic bytes of a 512-graph capture
-    # (1,289.0 MB / 914.1 MB), applied to a phase-0 launch of the full batch
-    "planted_batch4096": {"ratio": 1289.0 / 914.1,
+    # (1,290.2 MB / 914.1 MB), applied to a phase-0 launch of the full batch
+    "planted_batch4096": {"ratio": 1290.2 / 914.1,
                           "scope": "one phase-0 sweep launch of all 4,096 graphs, scaled by "
                                    "units from a 512-graph capture"},
 }
