@@ -41,50 +41,90 @@ __global__ void convert_kernel(const int64_t *__restrict__ rowptr, const int32_t
         arcs[e] = make_int2(col[e], w[e]);
 }
 
-// one warp per row: column range, ascending order, weights, degrees
-__global__ void __launch_bounds__(256) row_check_kernel(DGraph g, int *sev, int32_t *k,
-                                                        int32_t *loop,
-                                                        unsigned long long *two_m) {
+// row of every arc (one warp per row)
+__global__ void __launch_bounds__(256) row_of_kernel(DGraph g, int32_t *row_of) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * 8;
-    unsigned long long acc = 0;
     for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
         const int beg = g.off[i], end = g.off[i + 1];
-        long long s = 0;
-        int lp = 0;
-        for (int e = beg + lane; e < end; e += 32) {
-            const int2 a = g.arcs[e];
+        for (int e = beg + lane; e < end; e += 32) row_of[e] = (int32_t)i;
+    }
+}
+
+// one thread per arc: column range, ascending order without duplicates,
+// positive weight; 64-bit weighted degrees k64 (zeroed by the caller; runs
+// of equal rows within a warp, one atomic per run), self-loop weights; 2m
+__global__ void __launch_bounds__(256) arc_check_kernel(DGraph g, const int32_t *__restrict__ row_of,
+                                                        int *sev, unsigned long long *k64,
+                                                        int32_t *loop, unsigned long long *two_m) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t a_pad = ((int64_t)g.A + 31) & ~31ll;  // whole warps take part in the runs
+    long long acc = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a_pad; e += stride) {
+        const bool in = e < g.A;
+        int r = 0;
+        int2 a = make_int2(0, 0);
+        if (in) {
+            r = row_of[e];
+            a = g.arcs[e];
             if (a.x < 0 || a.x >= g.n) raise_sev(sev, kSevArg);
-            if (e > beg) {
+            if (a.y < 1) raise_sev(sev, kSevWeight);
+            if (e > 0 && row_of[e - 1] == r) {
                 const int prev = g.arcs[e - 1].x;
                 if (a.x == prev) raise_sev(sev, kSevDup);
                 else if (a.x < prev) raise_sev(sev, kSevArg);
             }
-            if (a.y < 1) raise_sev(sev, kSevWeight);
-            s += a.y;
-            if (a.x == i) lp = a.y;
+            if (a.x == r) loop[r] = a.y;
+            acc += a.y;
         }
-        s = warp_sum(s);
-        lp = warp_sum(lp);
-        if (lane == 0) {
-            k[i] = s > 0x7fffffffll ? 0x7fffffff : (int32_t)s;
-            loop[i] = lp;
-            acc += (unsigned long long)s;
-        }
+        warp_run_add(r, (unsigned long long)(unsigned)a.y, in && a.y > 0, k64);
     }
-    if (lane == 0 && acc) atomicAdd(two_m, acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(two_m, (unsigned long long)acc);
 }
 
-// every (i, j, w), j != i, must have (j, i, w): row j is bisected
-__device__ __forceinline__ void check_mirror(const DGraph &g, int i, int2 a, int *sev) {
-    if (a.x == i) return;
-    int lo = g.off[a.x], hi = g.off[a.x + 1];
-    const int hend = hi;
-    while (lo < hi) {
-        const int mid = lo + ((hi - lo) >> 1);
-        if (g.arcs[mid].x < i) lo = mid + 1; else hi = mid;
+// k = k64, saturated at 2^31 - 1 (a larger degree fails the 2m < 2^31 test)
+__global__ void degree_store_kernel(int32_t n, const unsigned long long *__restrict__ k64, int32_t *k) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        k[i] = k64[i] > 0x7fffffffull ? 0x7fffffff : (int32_t)k64[i];
+}
+
+// Symmetry, one thread per non-loop arc.  Of the two arcs of a pair {i, j},
+// the one stored in the longer row (ties: the larger row id) looks for its
+// mirror, with the same weight, by bisection of the shorter row; the other
+// is only counted.  Rows hold no duplicates, so the mirrors of the searching
+// arcs are distinct counted arcs; when every search succeeds and the two
+// counts agree, every arc has its mirror.
+__global__ void __launch_bounds__(256) mirror_kernel(DGraph g, const int32_t *__restrict__ row_of,
+                                                     int *sev, unsigned long long *counts) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    long long searched = 0, counted = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < g.A; e += stride) {
+        const int i = row_of[e];
+        const int2 a = g.arcs[e];
+        const int j = a.x;
+        if (j == i) continue;
+        const int di = g.off[i + 1] - g.off[i];
+        int lo = g.off[j], hi = g.off[j + 1];
+        const int dj = hi - lo;
+        if (dj < di || (dj == di && j < i)) {
+            ++searched;
+            const int hend = hi;
+            while (lo < hi) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (g.arcs[mid].x < i) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= hend || g.arcs[lo].x != i || g.arcs[lo].y != a.y) raise_sev(sev, kSevSym);
+        } else {
+            ++counted;
+        }
     }
-    if (lo >= hend || g.arcs[lo].x != i || g.arcs[lo].y != a.y) raise_sev(sev, kSevSym);
+    searched = warp_sum(searched);
+    counted = warp_sum(counted);
+    if ((threadIdx.x & 31) == 0) {
+        if (searched) atomicAdd(&counts[0], (unsigned long long)searched);
+        if (counted) atomicAdd(&counts[1], (unsigned long long)counted);
+    }
 }
 
 constexpr int kBigRow = 1024;
@@ -94,29 +134,6 @@ __global__ void big_rows_kernel(DGraph g, const int32_t *__restrict__ keep, int3
                                 int32_t *count) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x)
         if (g.off[i + 1] - g.off[i] >= kBigRow && (!keep || keep[i])) list[atomicAdd(count, 1)] = i;
-}
-
-// one warp per row of fewer than kBigRow arcs
-__global__ void __launch_bounds__(256) symmetry_kernel(DGraph g, int *sev) {
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * 8;
-    for (int64_t i = blockIdx.x * 8 + (threadIdx.x >> 5); i < g.n; i += nw) {
-        const int beg = g.off[i], end = g.off[i + 1];
-        if (end - beg >= kBigRow) continue;
-        for (int e = beg + lane; e < end; e += 32) check_mirror(g, (int)i, g.arcs[e], sev);
-    }
-}
-
-// one 1024-thread block per row of at least kBigRow arcs (from a list)
-__global__ void __launch_bounds__(1024) symmetry_big_kernel(DGraph g, const int32_t *__restrict__ list,
-                                                            const int32_t *__restrict__ count,
-                                                            int *sev) {
-    const int nb = *count;
-    for (int t = blockIdx.x; t < nb; t += gridDim.x) {
-        const int i = list[t];
-        const int beg = g.off[i], end = g.off[i + 1];
-        for (int e = beg + threadIdx.x; e < end; e += 1024) check_mirror(g, i, g.arcs[e], sev);
-    }
 }
 
 // one warp per row: weighted degree k_i and self-loop weight (R1: once)
@@ -351,28 +368,43 @@ lv_status validate_and_build(int64_t n, const int64_t *rowptr, const int32_t *co
     convert_kernel<<<grid_items((int64_t)g.A + n + 1), 256, 0, s>>>(rowptr, col, w, g.n, g.A,
                                                                     g.off, g.arcs);
     LV_LAUNCH_CHECK();
+    unsigned long long *k64 = nullptr;
     if (n > 0) {
-        row_check_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev, k, loop, d2m);
-        LV_LAUNCH_CHECK();
+        LV_TRY(dalloc_n(&k64, (size_t)n, s));
+        LV_CUDA(cudaMemsetAsync(k64, 0, sizeof(unsigned long long) * (size_t)n, s));
+        LV_CUDA(cudaMemsetAsync(loop, 0, sizeof(int32_t) * (size_t)n, s));
     }
-    LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
-    if (scratch_pinned[0] < kSevSym && n > 0) {
-        symmetry_kernel<<<grid_rows(n), 256, 0, s>>>(g, dsev);
+    // counts[0..1]: searching / counted arcs of the symmetry test
+    unsigned long long *counts = nullptr;
+    LV_TRY(dalloc_n(&counts, 2, s));
+    LV_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(unsigned long long), s));
+    if (g.A > 0) {
+        int32_t *row_of = nullptr;
+        LV_TRY(dalloc_n(&row_of, (size_t)g.A, s));
+        row_of_kernel<<<grid_rows(n), 256, 0, s>>>(g, row_of);
         LV_LAUNCH_CHECK();
-        int32_t *big = nullptr;
-        LV_TRY(dalloc_n(&big, (size_t)n / kBigRow + (size_t)g.A / kBigRow + 2, s));
-        LV_CUDA(cudaMemsetAsync(big, 0, sizeof(int32_t), s));
-        big_rows_kernel<<<grid_items(n), 256, 0, s>>>(g, nullptr, big + 1, big);
+        arc_check_kernel<<<grid_items(g.A), 256, 0, s>>>(g, row_of, dsev, k64, loop, d2m);
         LV_LAUNCH_CHECK();
-        symmetry_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, big + 1, big, dsev);
-        LV_LAUNCH_CHECK();
-        dfree(big, s);
+        LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        if (scratch_pinned[0] < kSevSym) {  // columns in range and rows sorted: bisection is safe
+            mirror_kernel<<<grid_items(g.A), 256, 0, s>>>(g, row_of, dsev, counts);
+            LV_LAUNCH_CHECK();
+        }
+        dfree(row_of, s);
     }
-    unsigned long long tm = 0;
+    if (n > 0) {
+        degree_store_kernel<<<grid_items(n), 256, 0, s>>>(g.n, k64, k);
+        LV_LAUNCH_CHECK();
+        dfree(k64, s);
+    }
+    unsigned long long tm = 0, cnt[2] = {0, 0};
     LV_CUDA(cudaMemcpyAsync(scratch_pinned, dsev, sizeof(int), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaMemcpyAsync(&tm, d2m, sizeof(tm), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(cnt, counts, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
+    dfree(counts, s);
+    if (cnt[0] != cnt[1] && scratch_pinned[0] < kSevSym) scratch_pinned[0] = kSevSym;
     st = severity_to_status(scratch_pinned[0]);
     if (st == LV_OK) {
         if (limit_two_m && tm >= (1ull << 31)) st = LV_ERR_OVERFLOW;

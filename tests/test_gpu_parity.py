@@ -239,3 +239,66 @@ def test_compare_partitions_large_device(lv):
     n = len(s)
     assert got["tp"] + got["fp"] + got["fn"] + got["tn"] == n * (n - 1) // 2
     assert got["fn"] == 0  # phase-0 communities nest inside the final ones
+
+
+# ---------------------------------------------------------------- validation
+def _arc(g, i, j):
+    """Index of arc (i, j) in the CSR of g."""
+    seg = g.col[g.rowptr[i]:g.rowptr[i + 1]]
+    k = int(np.searchsorted(seg, j))
+    assert seg[k] == j
+    return int(g.rowptr[i]) + k
+
+
+def _drop(g, e):
+    rp = g.rowptr.copy()
+    rp[int(np.searchsorted(g.rowptr, e, side="right")):] -= 1
+    return rp, np.delete(g.col, e), np.delete(g.w, e)
+
+
+def _validation_cases():
+    """Single-defect CSRs around a hub row (pairs of very unequal rows, both
+    orders of the defect) and a cycle (pairs of equal rows)."""
+    rng = np.random.default_rng(11)
+    edges = [(0, v, int(rng.integers(1, 6))) for v in range(1, 1501)]
+    edges += [(int(a), int(b), 1) for a, b in rng.integers(1, 1501, size=(3000, 2)) if a != b]
+    edges += [(7, 7, 3)]
+    hub = gg.from_edges(1501, edges)
+    cyc = gg.from_edges(50, [(v, (v + 1) % 50, 1 + v % 3) for v in range(50)])
+    cases = [("hub valid", hub.rowptr, hub.col, hub.w), ("cycle valid", cyc.rowptr, cyc.col, cyc.w)]
+    for g, tag, i, j in [(hub, "hub row", 0, 5), (hub, "leaf row", 5, 0), (cyc, "tie up", 4, 3),
+                         (cyc, "tie down", 3, 4)]:
+        e = _arc(g, i, j)
+        cases.append((f"{tag}: arc dropped", *_drop(g, e)))
+        w = g.w.copy()
+        w[e] += 1
+        cases.append((f"{tag}: weight differs", g.rowptr, g.col, w))
+    e, f = _arc(hub, 0, 9), _arc(hub, 9, 0)
+    w = hub.w.copy()
+    w[e] = w[f] = 0
+    cases.append(("zero weight pair", hub.rowptr, hub.col, w))
+    col = hub.col.copy()
+    col[e], col[e + 1] = col[e + 1], col[e]
+    cases.append(("unsorted row", hub.rowptr, col, hub.w))
+    col = hub.col.copy()
+    col[_arc(hub, 5, 0)] = 1501
+    cases.append(("column out of range", hub.rowptr, col, hub.w))
+    col = hub.col.copy()
+    col[e + 1] = col[e]
+    cases.append(("duplicate in row", hub.rowptr, col, hub.w))
+    return cases
+
+
+def test_validation_codes_match_oracle(lv):
+    """lv_graph_create rejects exactly what the oracle rejects, with the same
+    status, for one defect at a time (both arcs of a pair between unequal
+    rows, and between equal rows)."""
+    for name, rp, col, w in _validation_cases():
+        want = oracle.validate(rp, col, w)[0]
+        try:
+            lv.lv_graph_destroy(lv.lv_graph_create(len(rp) - 1, rp, col, w))
+            got = 0
+        except lv.LVError as err:
+            got = err.code
+        assert got == want, name
+        assert (want == 0) == name.endswith("valid"), name
