@@ -70,8 +70,8 @@ typedef struct {
      * A vertex of degree d <= bin_warp_max is swept by the smallest group of
      * G = 1, 2, ..., 32 lanes with d <= G * bin_lane_arcs (else 32 lanes);
      * d <= bin_cta_max by one CTA; larger (hubs) by several CTAs. */
-    int32_t bin_lane_arcs;    /* 1..8, default 4 */
-    int32_t bin_warp_max;     /* 1..256, default 128 */
+    int32_t bin_lane_arcs;    /* 1..8, default 8 */
+    int32_t bin_warp_max;     /* 1..256, default 256 */
     int32_t bin_cta_max;      /* bin_warp_max+1 .. 4096, default 4096 */
     /* 0/1: choose the bins of each uncoloured phase with >= 2^22 arcs by
      * timing one sweep per candidate set (the sweep of an uncoloured phase

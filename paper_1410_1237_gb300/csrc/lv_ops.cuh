@@ -52,7 +52,8 @@ struct Buckets {
 #endif
 constexpr int kHubChunk = LV_HUB_CHUNK;  // arcs (and occupied slots) per block item of a hub
 struct BinLimits {
-    int lane_arcs = 4, warp_max = 128, cta_max = 4096;
+    // the best fixed set on the R-MAT, Chung-Lu and planted-batch workloads
+    int lane_arcs = 8, warp_max = 256, cta_max = 4096;
 };
 lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes,
                           const BinLimits &lim, Buckets *b, int *scratch_pinned, cudaStream_t s);

@@ -26,6 +26,9 @@ lv_status tune_bins(PhaseState &ps, const BinLimits &first, void *zero, size_t z
     bool have = false;
     lv_status st = LV_OK;
     const int ncand = 1 + (int)(sizeof(kCands) / sizeof(kCands[0]));
+    // a sweep first warms L2 and the TLBs, unless its arcs alone (8 B each)
+    // are twice the 129 MB L2: then one timed sweep per candidate suffices
+    const int reps = (int64_t)ps.g.A * 8 >= (int64_t)2 * 129 * 1000 * 1000 ? 1 : 2;
     for (int c = 0; c < ncand && st == LV_OK; ++c) {
         BinLimits lim = first;
         if (c > 0) {
@@ -39,7 +42,7 @@ lv_status tune_bins(PhaseState &ps, const BinLimits &first, void *zero, size_t z
         Buckets b;
         st = bucket_vertices(ps.g, nullptr, 1, lim, &b, pinned, s);
         float ms = 0.f;
-        for (int rep = 0; rep < 2 && st == LV_OK; ++rep) {  // first sweep warms L2 and TLBs
+        for (int rep = 0; rep < reps && st == LV_OK; ++rep) {
             if (cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s) != cudaSuccess ||
                 cudaMemsetAsync(ps.move_count, 0, 3 * sizeof(int32_t), s) != cudaSuccess ||
                 (zero && cudaMemsetAsync(zero, 0, zero_bytes, s) != cudaSuccess) ||
