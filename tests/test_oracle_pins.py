@@ -488,3 +488,39 @@ def test_colour_first_phase_only():
     # phase 0 is the same run in both
     assert np.array_equal(full.phases[0].labels, first.phases[0].labels)
     assert full.phases[0].N_end == first.phases[0].N_end
+
+
+# ------------------------------------------- Sec. 4.3: recursive VF reading
+def _lemma3_mergeable(rp, col, w, two_m):
+    """Single-neighbour vertices i (one neighbour j != i, optional self-loop)
+    whose Lemma 3 lower bound stays positive for any community of j:
+    2m * w(i, j) > k_i * (2m - k_i), the largest a_C(j) being 2m - k_i."""
+    out = []
+    for i in range(len(rp) - 1):
+        c, ww = col[rp[i]:rp[i + 1]], w[rp[i]:rp[i + 1]]
+        other = c != i
+        if other.sum() == 1:
+            k = int(ww.sum())
+            if two_m * int(ww[other][0]) > k * (two_m - k):
+                out.append(i)
+    return out
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(14, 16, seed=2),
+                                  lambda: gg.chunglu(4000, 2.1, 0.7, 16000, 300.0, seed=7),
+                                  lambda: gg.random_graph(300, 0.01, wmax=5, loops=0.1, seed=3)])
+def test_recursive_vf_stops_at_single_degree(make):
+    """Extending VF to single-neighbour vertices (Sec. 4.3's recursive idea)
+    under Lemma 3's own bound merges nothing more on these graphs: after VF
+    every single-neighbour vertex carries a self-loop, and the bound fails
+    unless its degree is a large share of 2m."""
+    g = make()
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, trace=1, max_phases=1)
+    rp, col, w = r.phases[0].graph
+    single = sum(1 for i in range(len(rp) - 1) if (col[rp[i]:rp[i + 1]] != i).sum() == 1)
+    assert single > 0 or len(rp) < 500
+    assert _lemma3_mergeable(rp, col, w, r.two_m) == []
+    # the bound holds for every single-degree vertex (plain VF: vertex 2) and
+    # for a looped one when its pair dominates the graph (vertex 0)
+    h = gg.from_edges(3, [(0, 0, 100), (0, 1, 50), (1, 2, 1)])
+    assert _lemma3_mergeable(h.rowptr, h.col, h.w, int(h.w.sum())) == [0, 2]
