@@ -13,16 +13,20 @@
 // One cooperative launch sweeps every class of an iteration.  Per class:
 //   stage A  block items: hub arc chunks (global tables) and CTA-bin vertices
 //            (shared-memory table); warp items: 32/G vertices of G lanes each,
-//            G = 1..32 chosen per vertex so each lane holds a few arcs
-//   [barrier, stage B: per hub, blocks evaluate chunks of its occupied
-//    slots; the last one to finish combines them and decides]
+//            G = 1..32 chosen per vertex so each lane holds a few arcs.  In a
+//            coloured sweep whose hub chunks each get a block, a hub's chunk
+//            blocks wait for one another (bounded), evaluate the table slots
+//            each claimed, and the last to finish decides the hub's move
+//   [otherwise, with hubs: barrier, stage B: per hub, blocks evaluate chunks
+//    of its occupied slots; the last one to finish combines them and decides]
 //   barrier
 // Coloured phases keep the community state {a_C, |C|} in two buffers.  Class
 // g reads X[g % 2] and writes X[(g + 1) % 2], which before class g holds the
 // state of class g - 1's start: class g replays class g - 1's moves into it
 // and its own movers add their deltas there directly.  Labels are updated in
 // place (a class is an independent set, so no vertex of the class reads the
-// label of another).  One barrier per class suffices (two with hubs).
+// label of another).  One barrier per class suffices (two with hubs whose
+// chunks outnumber the blocks).
 // Uncoloured phases sweep the whole graph from X[0] and leave the moves in a
 // list for the host (the stopping test decides whether they are applied).
 //
