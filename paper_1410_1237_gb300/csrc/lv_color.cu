@@ -320,13 +320,13 @@ __device__ __forceinline__ int next_pow2(int x) {
 
 // hub hash-table size and arc-chunk count at each position of the order
 // (0 for non-hubs)
-__global__ void hub_size_kernel(DGraph g, const int32_t *__restrict__ order, int cta_max,
+__global__ void hub_size_kernel(DGraph g, const int32_t *__restrict__ order, int cta_max, int factor,
                                 int32_t *tsize, int32_t *nchunks) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += gridDim.x * blockDim.x) {
         const int v = order[p];
         const int deg = g.off[v + 1] - g.off[v];
         const bool hub = deg > cta_max;
-        tsize[p] = hub ? next_pow2(2 * deg) : 0;
+        tsize[p] = hub ? next_pow2(factor * deg) : 0;
         nchunks[p] = hub ? (deg + kHubChunk - 1) / kHubChunk : 0;
     }
 }
@@ -427,7 +427,8 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     LV_TRY(dalloc_n(&b->hub_chunk_off, (size_t)n + 1, s));
     LV_TRY(dalloc_n(&b->hub_chunk_at, (size_t)nb + 1, s));
     int32_t *chunk_at = b->hub_chunk_at;
-    hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_off, b->hub_chunk_off);
+    hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, hub_table_factor(color != nullptr),
+                                         b->hub_off, b->hub_chunk_off);
     LV_LAUNCH_CHECK();
     LV_TRY(scan_excl_i32(b->hub_off, b->hub_off, n, s));
     LV_TRY(scan_excl_i32(b->hub_chunk_off, b->hub_chunk_off, n, s));

@@ -51,6 +51,10 @@ struct Buckets {
 #define LV_HUB_CHUNK 1024
 #endif
 constexpr int kHubChunk = LV_HUB_CHUNK;  // arcs (and occupied slots) per block item of a hub
+// a hub's global table has the next power of two >= this many slots per arc:
+// 4 in coloured sweeps (shorter probe chains on the latency-bound path), 2 in
+// one-class sweeps (batches and serving, where memory is budgeted)
+__host__ __device__ constexpr int hub_table_factor(bool coloured) { return coloured ? 4 : 2; }
 struct BinLimits {
     // the best fixed set on the R-MAT, Chung-Lu and planted-batch workloads
     int lane_arcs = 8, warp_max = 256, cta_max = 4096;

@@ -35,8 +35,8 @@
 // Every loop keeps up to 4 independent loads in flight per thread.
 //
 // Hash tables are open-addressing (linear probing) keyed by community label
-// and sized to the next power of two >= 2 * degree, so the load factor is
-// <= 1/2 and every probe sequence ends; a probe count above the table size is
+// and sized to the next power of two >= 2 * degree (4 * degree for hubs in
+// coloured sweeps), so the load factor is <= 1/2 and every probe sequence ends; a probe count above the table size is
 // an internal error (LV_ERR_HASH), never a hang.  Grid barriers wait a bounded
 // time and report LV_ERR_TIMEOUT.
 #include <climits>
@@ -467,7 +467,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const int i = s.order[p];
     if (!live(s, i)) return;  // block-uniform
     const int beg = s.off[i], end = s.off[i + 1];
-    const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+    const unsigned mask = (unsigned)pow2_at_least(hub_table_factor(s.coloured) * (end - beg)) - 1u;
     int2 *tab = s.hub_table + s.hub_off[p];
     const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
     // the hub's own terms, loaded ahead of the arcs (used after the wait)
