@@ -40,7 +40,7 @@ BYTES_PER_VERTEX = 28  # rowptr 8 + C 4 + k 4 + a,|C| of own community 8 + label
 # no capture applies
 MEASURED_TRAFFIC = {
     # sweep_persistent_kernel, rmat20 phase 0 iteration 3 (all 232 classes)
-    "rmat20": {"bytes": 328_256_768 + 16_262_400,
+    "rmat20": {"bytes": 335_230_976 + 17_168_128,
                "scope": "one phase-0 sweep launch (iteration 3, 232 colour classes)"},
     # batched sweep: traffic / algorithmic bytes of a 512-graph capture
     # (1,290.2 MB / 914.1 MB), applied to a phase-0 launch of the full batch
