@@ -20,6 +20,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lv_oracle.c")
 _LIB = os.path.join(_HERE, "liblv_oracle.so")
+# tests that plant mistakes in a copy of the oracle point this at their build
+_LIB_OVERRIDE = os.environ.get("LV_ORACLE_LIB")
 _lib = None
 
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_WEIGHT",
@@ -39,6 +41,8 @@ class OracleError(RuntimeError):
 
 def build(force: bool = False) -> str:
     """Compile ``liblv_oracle.so`` (gcc -O2, single-threaded by design)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared",
@@ -59,8 +63,7 @@ class _Params(ctypes.Structure):
 def _load():
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        L = ctypes.CDLL(build())
         vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
         P = ctypes.POINTER
         L.orc_validate.restype = ctypes.c_int

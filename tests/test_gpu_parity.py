@@ -70,7 +70,8 @@ VARIANTS = [
 
 
 @pytest.mark.parametrize("name", ["two_triangles.txt", "two_k5.txt", "ring3_triangles.txt",
-                                  "k2_singlet.txt", "k4_minlabel.txt", "star_vf.txt"])
+                                  "k2_singlet.txt", "k4_minlabel.txt", "star_vf.txt",
+                                  "zero_gain.txt"])
 @pytest.mark.parametrize("vi", range(len(VARIANTS)))
 def test_golden_graphs(lv, golden, name, vi):
     fx = golden(name)

@@ -1,0 +1,72 @@
+"""The oracle's pins catch typical mistakes.
+
+Each case plants one mistake in a copy of oracle/lv_oracle.c, builds it, and
+runs tests/test_oracle_pins.py against that build in a child process: at
+least one pin must fail.  The unchanged copy must pass them all.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+SRC = os.path.join(ROOT, "oracle", "lv_oracle.c")
+OUT = os.path.join(ROOT, "tests", "_build", "mutants")
+
+MUTANTS = {
+    "none": None,
+    # Eq. 4 without the -k_i a_C term of the target community
+    "dropped gain term": ("const i128 G = ((i128)two_m * sc->e[c] - (i128)ki * a[c]) - s_old;",
+                          "const i128 G = ((i128)two_m * sc->e[c]) - s_old;"),
+    # Sec. 4.1 singlet rule blocking the wrong one of the two moves
+    "flipped singlet rule": ("size[best] == 1 && best > ci) continue;",
+                             "size[best] == 1 && best < ci) continue;"),
+    # equal gains going to the larger label
+    "flipped tie-break": ("(G == bestG && c < best)", "(G == bestG && c > best)"),
+    # vertex following adding w(i,j) once instead of twice (R2)
+    "VF weight": ("extra[j] += 2 * (int64_t)g->w[g->rowptr[i]];",
+                  "extra[j] += (int64_t)g->w[g->rowptr[i]];"),
+    # colouring in increasing instead of decreasing priority (R11)
+    "colouring order": ("if (x->h != y->h) return x->h < y->h ? 1 : -1;",
+                        "if (x->h != y->h) return x->h < y->h ? -1 : 1;"),
+    # a move on a zero gain
+    "zero-gain move": ("if (bestG > 0) {", "if (bestG >= 0 && best != ci) {"),
+    # the self-loop left out of e_in (R1)
+    "self-loop out of e_in": ("if (C[g->col[e]] == C[i]) ein += g->w[e];",
+                              "if (g->col[e] != i && C[g->col[e]] == C[i]) ein += g->w[e];"),
+}
+
+
+def _build(name, change):
+    src = open(SRC).read()
+    if change is not None:
+        old, new = change
+        assert src.count(old) == 1, f"{name}: the line to change is gone"
+        src = src.replace(old, new)
+    os.makedirs(OUT, exist_ok=True)
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)
+    c_path = os.path.join(OUT, f"{tag}.c")
+    so_path = os.path.join(OUT, f"{tag}.so")
+    with open(c_path, "w") as f:
+        f.write(src)
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC",
+                           "-o", so_path, c_path])
+    return so_path
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_planted_mistake(name):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    so = _build(name, MUTANTS[name])
+    env = dict(os.environ, LV_ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "no:cacheprovider"], env=env, cwd=ROOT,
+                       capture_output=True, text=True, timeout=600)
+    if name == "none":
+        assert r.returncode == 0, r.stdout[-2000:]
+    else:
+        assert r.returncode == 1, (r.returncode, r.stdout[-2000:])  # a pin failed, nothing crashed

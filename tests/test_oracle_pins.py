@@ -149,6 +149,18 @@ def test_k2_singlet_rule(golden):
     assert Fraction(r.phases[-1].N_end, r.two_m ** 2) == fx["q"]
 
 
+def test_zero_gain_does_not_move(golden):
+    fx = golden("zero_gain.txt")
+    g = _g(fx)
+    assert oracle.gain(g.rowptr, g.col, g.w, list(range(fx["n"])), 1, 0) == 0
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0, trace=1)
+    p0 = r.phases[0]
+    assert r.two_m == 6
+    assert list(p0.iter_labels[0]) == fx["iter1"]
+    assert Fraction(p0.N_start, p0.two_m ** 2) == fx["q_start"]
+    assert Fraction(r.phases[-1].N_end, r.two_m ** 2) == fx["q"]
+
+
 def test_k4_generalised_min_label(golden):
     fx = golden("k4_minlabel.txt")
     g = _g(fx)
