@@ -1,6 +1,7 @@
 """The oracle's pins catch typical mistakes.
 
-Each case plants one mistake in a copy of oracle/lv_oracle.c, builds it, and
+Each case plants one mistake (one or two edits) in a copy of
+oracle/lv_oracle.c, builds it, and
 runs tests/test_oracle_pins.py against that build in a child process: at
 least one pin must fail.  The unchanged copy must pass them all.
 """
@@ -37,13 +38,34 @@ MUTANTS = {
     # the self-loop left out of e_in (R1)
     "self-loop out of e_in": ("if (C[g->col[e]] == C[i]) ein += g->w[e];",
                               "if (g->col[e] != i && C[g->col[e]] == C[i]) ein += g->w[e];"),
+    # moves applied in place within a class (Gauss-Seidel instead of R6's Jacobi)
+    "in-place moves": [("            sc->mv_v[nmoves] = i;\n            sc->mv_c[nmoves] = best;\n",
+                        "            a[C[i]] -= k[i]; size[C[i]] -= 1; a[best] += k[i]; size[best] += 1;\n"
+                        "            C[i] = best;\n"),
+                       ("    for (int64_t t = 0; t < nmoves; ++t) {\n        const int32_t i = sc->mv_v[t]",
+                        "    for (int64_t t = 0; t < 0; ++t) {\n        const int32_t i = sc->mv_v[t]")],
+    # a coarse self-loop counting each intra edge once instead of per arc (R1)
+    "coarse loop halved": ("            t[e].w = g->w[e];",
+                           "            t[e].w = (t[e].u == t[e].v && u > g->col[e]) ? 0 : g->w[e];"),
+    # coarse vertices numbered in descending instead of ascending label (R14)
+    "descending renumbering": ("        for (int64_t c = 0; c < np; ++c) newid[c] = size[c] > 0 ? (int32_t)nn++ : -1;",
+                               "        for (int64_t c = np - 1; c >= 0; --c) newid[c] = size[c] > 0 ? (int32_t)nn++ : -1;"),
+    # the stop test on the absolute change (R9 reads it signed)
+    "absolute stop test": ("    if (abs_mode) d = abs64(d);", "    d = abs64(d);"),
+    # vertex following removing the larger end of an isolated edge (R3)
+    "VF keeps the smaller end": ("if (deg1[j] && j < i) continue;", "if (deg1[j] && j > i) continue;"),
+    # coloured phases using the fine threshold and uncoloured ones the coarse (R12)
+    "thresholds swapped": ("? prm->theta_high\n", "? prm->theta_low + 0.0 * prm->theta_high\n"),
+    # a self-loop counted twice in k (R1 counts it once)
+    "loop twice in k": ("for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) s += g->w[e];",
+                        "for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e)\n"
+                        "            s += g->col[e] == i ? 2 * (int64_t)g->w[e] : g->w[e];"),
 }
 
 
 def _build(name, change):
     src = open(SRC).read()
-    if change is not None:
-        old, new = change
+    for old, new in ([] if change is None else [change] if isinstance(change, tuple) else change):
         assert src.count(old) == 1, f"{name}: the line to change is gone"
         src = src.replace(old, new)
     os.makedirs(OUT, exist_ok=True)

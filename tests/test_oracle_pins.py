@@ -536,3 +536,82 @@ def test_recursive_vf_stops_at_single_degree(make):
     # for a looped one when its pair dominates the graph (vertex 0)
     h = gg.from_edges(3, [(0, 0, 100), (0, 1, 50), (1, 2, 1)])
     assert _lemma3_mergeable(h.rowptr, h.col, h.w, int(h.w.sum())) == [0, 2]
+
+
+# ------------------------------------ R3, R12, R14: survivor, thresholds, order
+def test_vf_isolated_edge_keeps_the_larger_end():
+    """R3: of an isolated edge the smaller id is removed into the larger.
+    Triangle 0-2-4 and isolated edge 1-3: vertex 1 goes into 3, the survivors
+    0, 2, 3, 4 become 0, 1, 2, 3, and 3 carries the self-loop 2 * w(1, 3)."""
+    g = gg.from_edges(5, [(0, 2, 1), (2, 4, 1), (0, 4, 1), (1, 3, 1)])
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, trace=1)
+    assert list(r.vf_map) == [0, 2, 1, 2, 3]
+    rp, col, w = r.phases[0].graph
+    assert list(rp) == [0, 2, 4, 5, 7]
+    assert list(col) == [1, 3, 0, 3, 2, 0, 1]
+    assert list(w) == [1, 1, 1, 1, 2, 1, 1]
+
+
+def _coarse_by_definition(rp, col, w, labels):
+    """Sec. 4.5: one vertex per non-empty community in ascending label (R14);
+    every arc (u, v, w) becomes (c'(u), c'(v), w) and equal pairs are summed."""
+    _, inv = np.unique(labels, return_inverse=True)
+    u = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    cu, cv = inv[u], inv[col]
+    key = cu.astype(np.int64) * (inv.max() + 1) + cv
+    order = np.argsort(key, kind="stable")
+    k_sorted, w_sorted = key[order], w[order].astype(np.int64)
+    uk, start = np.unique(k_sorted, return_index=True)
+    ws = np.add.reduceat(w_sorted, start)
+    nn = inv.max() + 1
+    rows = uk // nn
+    rp2 = np.zeros(nn + 1, dtype=np.int64)
+    np.add.at(rp2, rows + 1, 1)
+    return np.cumsum(rp2), (uk % nn).astype(np.int32), ws.astype(np.int32)
+
+
+@pytest.mark.parametrize("make", [lambda: gg.planted(1000, 10, 0.1, 0.002, 1, 1, seed=1),
+                                  lambda: gg.random_graph(300, 0.02, wmax=5, loops=0.2, seed=4),
+                                  lambda: gg.rmat(10, 8, seed=5)])
+def test_rebuild_matches_definition(make):
+    """Every phase graph equals the coarse graph of the previous phase's last
+    labels, built here with numpy straight from the definition."""
+    g = make()
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0, trace=1)
+    assert len(r.phases) >= 2
+    for a, b in zip(r.phases, r.phases[1:]):
+        rp, col, w = a.graph
+        want = _coarse_by_definition(rp, col, w, a.iter_labels[-1])
+        got = b.graph
+        for x, y in zip(want, got):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def _stop_rule_holds(r, theta_high, theta_low, cutoff, max_iters=10_000):
+    """R9, R10, R12, R13 checked on the recorded numerators: every phase ends
+    at the first iteration that moves nothing, gains less than theta times
+    |N| of the iteration before (signed, from the second iteration), or hits
+    max_iters; a phase colours iff n_p >= cutoff and no earlier coloured
+    phase gained less than theta_high relative to its start."""
+    colour_stopped = False
+    for p, ph in enumerate(r.phases):
+        its = [t for t in r.iters if t[0] == p]
+        assert ph.colored == (ph.n >= cutoff and not colour_stopped), p
+        theta = theta_high if ph.colored else theta_low
+        prev = None
+        for t, (_, it, moved, N, _) in enumerate(its, start=1):
+            stop = moved == 0 or (prev is not None and N - prev < theta * abs(prev)) or t >= max_iters
+            assert stop == (t == len(its)), (p, t)
+            prev = N
+        if ph.colored and ph.N_end - ph.N_start < theta_high * abs(ph.N_start):
+            colour_stopped = True
+
+
+@pytest.mark.parametrize("make", [lambda: gg.rmat(12, 16, seed=6),
+                                  lambda: gg.planted(3000, 30, 0.02, 0.001, 1, 4, seed=8)])
+def test_stop_rules_on_recorded_numerators(make):
+    g = make()
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=1, color_cutoff=500,
+                   theta_high=1e-2, theta_low=1e-6)
+    assert any(p.colored for p in r.phases)
+    _stop_rule_holds(r, 1e-2, 1e-6, 500)
