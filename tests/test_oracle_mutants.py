@@ -56,6 +56,16 @@ MUTANTS = {
     "VF keeps the smaller end": ("if (deg1[j] && j < i) continue;", "if (deg1[j] && j > i) continue;"),
     # coloured phases using the fine threshold and uncoloured ones the coarse (R12)
     "thresholds swapped": ("? prm->theta_high\n", "? prm->theta_low + 0.0 * prm->theta_high\n"),
+    # the comparison of Sec. 5 counting pairs together only in p as FN and
+    # only in s as FP (R22)
+    "FP and FN swapped": [("else if (same_p) ++fp;", "else if (same_p) ++fn;"),
+                          ("else if (same_s) ++fn;", "else if (same_s) ++fp;")],
+    # symmetry accepting a mirror arc of another weight (Sec. 2)
+    "mirror weight ignored": ("return lo < rowptr[j + 1] && col[lo] == i && w[lo] == wt;",
+                              "return lo < rowptr[j + 1] && col[lo] == i;"),
+    # a repeated column reported as an unsorted row
+    "duplicate as ARG": ("if (col[e] == col[e - 1]) st = worse(st, ORC_ERR_DUPLICATE);",
+                         "if (col[e] == col[e - 1]) st = worse(st, ORC_ERR_ARG);"),
     # a self-loop counted twice in k (R1 counts it once)
     "loop twice in k": ("for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e) s += g->w[e];",
                         "for (int64_t e = g->rowptr[i]; e < g->rowptr[i + 1]; ++e)\n"
