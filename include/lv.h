@@ -228,22 +228,26 @@ lv_status lv_compare_partitions(int64_t n, const int32_t *labels_s, const int32_
 /* Modularity numerator of a caller-given labelling, computed without any
  * device allocation.  (This entry point has no counterpart in the paper; it
  * serves callers that cannot allocate device memory where they need it:
- * code running inside a CUDA graph capture, services that reserve all
- * device memory in a fixed pool at start-up, hosts with a strict
- * pre-computed memory budget.)
+ * services that reserve all device memory in a fixed pool at start-up and
+ * forbid further cudaMalloc calls, hosts with a strict pre-computed memory
+ * budget.)
  *   n, rowptr, col, w  a CSR meeting the lv_graph_create contract, all four
  *                      arrays in DEVICE memory; 1 <= n <= 1,048,576
  *   labels             int32[n] on the device, each in [0, n)
  *   num_hi:num_lo      out (host): N as a 128-bit two's-complement value
  *   den                out (host): (2m)^2, so that Q = N / den (Eq. 3)
- *   cuda_stream        cudaStream_t for the work; the call returns after it
+ *   cuda_stream        cudaStream_t for the work; the call waits for this
+ *                      stream (cudaStreamSynchronize) before it returns
  * Scratch is a fixed 8 MB array of device memory that exists once the library
  * is loaded (on every device the process uses, until exit).  The first call
- * on a device looks up that array's address; make it before capturing a
- * stream into a CUDA graph.  All calls share the array and each one clears
- * what it uses first, so calls whose GPU work overlaps race: serialise them.
+ * on a device looks up that array's address (once per device, thread-safe);
+ * make that first call before any stream capture.  The address is not looked
+ * up again, so it does not survive cudaDeviceReset.  All calls share the
+ * array and each one clears what it uses first, so calls whose GPU work
+ * overlaps race: serialise them.
  * Returns LV_ERR_ARG for n outside [1, 2^20], a label or column out of
- * range, or a NULL pointer; LV_ERR_EMPTY / LV_ERR_OVERFLOW as lv_graph_create. */
+ * range, or a NULL pointer (checked before any GPU work);
+ * LV_ERR_EMPTY / LV_ERR_OVERFLOW as lv_graph_create. */
 lv_status lv_modularity_noalloc(int64_t n, const int64_t *rowptr, const int32_t *col,
                                 const int32_t *w, const int32_t *labels, int64_t *num_hi,
                                 uint64_t *num_lo, int64_t *den, void *cuda_stream);

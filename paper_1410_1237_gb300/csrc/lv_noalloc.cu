@@ -1,14 +1,14 @@
 // lv_noalloc.cu -- modularity of a given labelling without any device allocation.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// modularity value: code running while a CUDA graph is being captured (an
-// allocation there would break or be baked into the capture), services that
-// hand the whole device to a fixed-size memory pool at start-up and forbid
-// further cudaMalloc calls, and hosts that must keep a strict, pre-computed
-// device-memory budget.  lv_modularity_noalloc serves them: its only scratch
-// is a file-scope __device__ array of fixed size that exists from the moment
-// the library is loaded, so the call performs no cudaMalloc, no cudaFree and
-// no allocating library call.
+// modularity value: services that hand the whole device to a fixed-size
+// memory pool at start-up and forbid further cudaMalloc calls (a second
+// allocator would fail or fragment the pool), and hosts that must keep a
+// strict, pre-computed device-memory budget.  lv_modularity_noalloc serves
+// them: its only scratch is a file-scope __device__ array of fixed size that
+// exists from the moment the library is loaded, so the call performs no
+// cudaMalloc, no cudaFree and no allocating library call.  It waits for its
+// stream (cudaStreamSynchronize) before it returns the numerator.
 //
 // Scratch layout (u64): [0, kNoAllocMaxN) community degrees a_c, then the
 // accumulators 2m, sum of intra-community weights, sum of a_c^2 and an error
@@ -17,6 +17,7 @@
 // streams, or different host threads on the same device) race and must be
 // serialised by the caller.
 #include <cstring>
+#include <mutex>
 
 #include "lv_internal.cuh"
 
@@ -28,8 +29,13 @@ enum { kTwoM = 0, kEin = 1, kA2 = 2, kErr = 3 };
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocMaxN + kAcc];
 
-// per-device address of the scratch array, looked up once per device
-unsigned long long *g_scratch_ptr[64];
+// per-device address of the scratch array, looked up once per device (the
+// first call on a device, under that device's once-flag).  The cached address
+// belongs to the device's primary context: after cudaDeviceReset it is stale.
+constexpr int kMaxDevices = 64;
+unsigned long long *g_scratch_ptr[kMaxDevices];
+cudaError_t g_scratch_err[kMaxDevices];
+std::once_flag g_scratch_once[kMaxDevices];
 
 __global__ void noalloc_clear_kernel(unsigned long long *scr, int n) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x)
@@ -97,19 +103,22 @@ extern "C" lv_status lv_modularity_noalloc(int64_t n, const int64_t *rowptr, con
                                            const int32_t *w, const int32_t *labels,
                                            int64_t *num_hi, uint64_t *num_lo, int64_t *den,
                                            void *cuda_stream) {
-    if (n <= 0 || !rowptr || !labels || !num_hi || !num_lo || !den) return LV_ERR_ARG;
+    if (n <= 0 || !rowptr || !col || !w || !labels || !num_hi || !num_lo || !den)
+        return LV_ERR_ARG;
     if (n > kNoAllocMaxN) return LV_ERR_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int dev = 0;
     LV_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return LV_ERR_ARG;
-    if (!g_scratch_ptr[dev]) {
-        // one-time set-up on this device: the host-side name of the array is
-        // not a device address, so look the address up with the device current
+    if (dev < 0 || dev >= kMaxDevices) return LV_ERR_ARG;
+    // one-time set-up on this device: the host-side name of the array is not
+    // a device address, so look the address up with the device current
+    std::call_once(g_scratch_once[dev], [dev] {
         void *p = nullptr;
-        LV_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_scratch_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         g_scratch_ptr[dev] = static_cast<unsigned long long *>(p);
-    }
+    });
+    LV_CUDA(g_scratch_err[dev]);
+    if (!g_scratch_ptr[dev]) return LV_ERR_CUDA;
     unsigned long long *scr = g_scratch_ptr[dev];
     int nsm = 0;
     LV_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

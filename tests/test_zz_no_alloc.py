@@ -1,6 +1,6 @@
 """lv_modularity_noalloc: the modularity entry point for callers that cannot
-allocate device memory (inside a CUDA graph capture, under a fixed device
-memory pool or budget).  Its result must equal what the regular path reports
+allocate device memory (services that hand the device to a fixed memory pool
+at start-up, hosts held to a strict device-memory budget).  Its result must equal what the regular path reports
 through lv_get_modularity for the same labels, on two calls in a row (the
 second call runs on the scratch array the first one left behind).
 
@@ -58,6 +58,17 @@ def test_no_alloc_rejects_oversized_and_bad_labels(env):
     with pytest.raises(lv.LVError) as e:
         lv.lv_modularity_noalloc((1 << 20) + 1, *d, bad)
     assert e.value.code == -1
+    # a NULL column or weight array is refused on the host, before any GPU work
+    import ctypes
+    L = lv.load()
+    hi, lo, den = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_int64()
+    ptr = [x.data_ptr() for x in d]
+    for k in (1, 2):
+        args = list(ptr)
+        args[k] = None
+        rc = L.lv_modularity_noalloc(g.n, *args, bad.data_ptr(), ctypes.byref(hi),
+                                     ctypes.byref(lo), ctypes.byref(den), None)
+        assert rc == -1
     ok = torch.tensor([0, 0, 1, 1], dtype=torch.int32, device=dev)
     num, den = lv.lv_modularity_noalloc(g.n, *d, ok)
     # two edges inside, one across: Q = 4/6 - 2*(3/6)^2 = 1/6 (Eq. 3)
