@@ -112,7 +112,12 @@ def test_arrivals_while_running_join_later_rounds(lv):
     h = lv.lv_server_create(**PARAMS)
     try:
         rb = lv.lv_server_submit(h, big.rowptr, big.col, big.w)
-        time.sleep(0.002)
+        # submit the small requests once the large one is admitted (no fixed
+        # sleep): its solve on the second lane takes far longer than their
+        # admission, which needs only budget and slots
+        t_end = time.monotonic() + 60.0
+        while lv.lv_server_get_stats(h).admitted < 1 and time.monotonic() < t_end:
+            time.sleep(0.001)
         ids = [lv.lv_server_submit(h, g.rowptr, g.col, g.w) for g in small]
         assert lv.lv_server_wait(h, rb, 120.0)
         for rid in ids:
