@@ -48,12 +48,19 @@ namespace {
 
 constexpr int kSwBlock = 512;
 constexpr int kSwWarps = kSwBlock / 32;
-constexpr int kWarpRegion = 2 * kWarpSlots;            // ints per warp (keys + vals)
-constexpr int kSwSmemInts = kSwWarps * kWarpRegion;    // == 2 * kCtaSlots
+// Dynamic shared memory: every table key lives in the first half, every
+// value in the second, whatever the item kind (warp w's group tables use keys
+// [w*kGroupTableInts, (w+1)*kGroupTableInts) and the same range of values; a
+// CTA-bin vertex or a hub chunk uses the block's whole key and value halves).
+// The halves are cleared once at kernel start, and every item leaves the
+// slots it used empty again (key kEmpty, value 0) before the next item, so no
+// item clears or scans a table it did not fill.
+constexpr int kSwSmemInts = 2 * kCtaSlots;
 constexpr int kU = 4;                                  // loads in flight per thread
-static_assert(kSwSmemInts >= 2 * kCtaSlots, "CTA table must fit the block's region");
-static_assert(2 * kGroupTableInts <= kWarpRegion, "group tables must fit the warp region");
-static_assert(2 * kWarpMaxLimit * 2 <= 2 * kGroupTableInts, "warp table must fit");
+constexpr int kCtaArcs = kCtaMaxLimit / kSwBlock;      // arcs per thread of a CTA-bin vertex
+static_assert(kSwWarps * kGroupTableInts == kCtaSlots, "warp tables tile the key half");
+static_assert(2 * kWarpMaxLimit <= kGroupTableInts, "warp table must fit");
+static_assert(kCtaArcs * kSwBlock == kCtaMaxLimit, "CTA-bin arcs split evenly");
 
 struct HubPart {
     long long s;
@@ -168,6 +175,58 @@ __device__ __forceinline__ bool smem_insert(int *key, int *val, unsigned mask, i
     return false;
 }
 
+// as smem_insert; `own` receives the slot when this call created the key
+// (exactly one inserter creates each distinct label's slot), else -1
+template <int ST>
+__device__ __forceinline__ bool smem_insert_own(int *key, int *val, unsigned mask, int c, int w,
+                                                int &own) {
+    unsigned h = hash32(c) & mask;
+    own = -1;
+    for (unsigned probe = 0; probe <= mask; ++probe) {
+        const int cur = ((volatile int *)key)[h * ST];
+        if (cur == c) {
+            atomicAdd(&val[h * ST], w);
+            return true;
+        }
+        if (cur == kEmpty) {
+            const int prev = atomicCAS(&key[h * ST], kEmpty, c);
+            if (prev == kEmpty || prev == c) {
+                if (prev == kEmpty) own = (int)h;
+                atomicAdd(&val[h * ST], w);
+                return true;
+            }
+        }
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+
+// Per-thread arcs of one vertex: up to NA arcs e = first + u * step < end,
+// all loads and label gathers in flight at once, inserted into a
+// shared-memory table; own[u] is the slot arc u's label created (or -1).
+// After the table is complete (a barrier), owner_eval evaluates each owned
+// slot -- every distinct label exactly once over the threads -- with all its
+// community gathers in flight, and clears the slot.
+template <int ST, int NA>
+__device__ __forceinline__ void insert_owned(const Sweep &s, int i, int first, int end, int step,
+                                             int *key, int *val, unsigned mask, int (&own)[NA],
+                                             Acc &acc) {
+    int2 a[NA];
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+        const int e = first + u * step;
+        a[u] = e < end ? s.arcs[e] : make_int2(i, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < NA; ++u) a[u].x = a[u].x != i ? ldC(s, a[u].x) : kEmpty;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+        own[u] = -1;
+        if (a[u].x != kEmpty && !smem_insert_own<ST>(key, val, mask, a[u].x, a[u].y, own[u]))
+            acc.err = 1;
+    }
+}
+
 // insert the arcs e = first, first + step, ... < end of vertex i into a
 // shared-memory table, U arcs (and their label gathers) at a time
 template <int ST, int U = kU>
@@ -218,33 +277,30 @@ __device__ __forceinline__ void best_shfl_xor(Best &b, int o) {
     best_take(b, s, c, z, e);
 }
 
-// evaluate table slots sl = first, first + step, ... <= mask, kU at a time
-template <int ST>
-__device__ __forceinline__ void eval_slots(const Sweep &s, const Cls &cc, const int *key,
-                                           const int *val, int first, unsigned mask, int step,
+// evaluate (and clear) the table slots this thread created (own[u] >= 0):
+// the label is read back from the slot, the weight to the vertex's own
+// community goes to e_old (its slot has exactly one owner)
+template <int ST, int NA>
+__device__ __forceinline__ void owner_eval(const Cls &cc, int *key, int *val, const int (&own)[NA],
                                            int ci, int ki, long long tm, Best &b, int &e_old) {
-    for (int s0 = first; s0 <= (int)mask; s0 += kU * step) {
-        int kk[kU], vv[kU];
-        unsigned long long cm[kU];
+    int lab[NA];
+    unsigned long long cm[NA];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int sl = s0 + u * step;
-            kk[u] = sl <= (int)mask ? key[sl * ST] : kEmpty;
-            vv[u] = sl <= (int)mask ? val[sl * ST] : 0;
+    for (int u = 0; u < NA; ++u) lab[u] = own[u] >= 0 ? key[own[u] * ST] : kEmpty;
+#pragma unroll
+    for (int u = 0; u < NA; ++u)
+        cm[u] = (lab[u] != kEmpty && lab[u] != ci) ? __ldcg(&cc.xr[lab[u]]) : 0ull;
+#pragma unroll
+    for (int u = 0; u < NA; ++u) {
+        if (lab[u] == kEmpty) continue;
+        const int v = val[own[u] * ST];
+        key[own[u] * ST] = kEmpty;
+        val[own[u] * ST] = 0;
+        if (lab[u] == ci) {
+            e_old = v;
+            continue;
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            cm[u] = (kk[u] != kEmpty && kk[u] != ci) ? __ldcg(&cc.xr[kk[u]]) : 0ull;
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (kk[u] == kEmpty) continue;
-            if (kk[u] == ci) {
-                e_old = vv[u];
-                continue;
-            }
-            best_take(b, tm * (long long)vv[u] - (long long)ki * comm_a(cm[u]), kk[u],
-                      comm_size(cm[u]), vv[u]);
-        }
+        best_take(b, tm * (long long)v - (long long)ki * comm_a(cm[u]), lab[u], comm_size(cm[u]), v);
     }
 }
 
@@ -311,13 +367,13 @@ __device__ __forceinline__ void block_best(Best &b, int &e_old, BlockRed &r) {
 // so the lanes of a warp clear and probe distinct banks.
 template <int G>
 __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *verts, int nverts,
-                                 int base, int *region, Acc &acc) {
+                                 int base, int *kreg, int *vreg, Acc &acc) {
     constexpr int NG = 32 / G;
     constexpr int ST = NG;
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
-    int *key = region + lane / G;
-    int *val = region + kGroupTableInts + lane / G;
+    int *key = kreg + lane / G;
+    int *val = vreg + lane / G;
     const unsigned lt = (1u << lane) - 1u;
     const int vi = base + lane / G;
     bool valid = vi < nverts;
@@ -341,19 +397,19 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
         }
         const int h = pow2_at_least(2 * (end - beg));
         mask = (unsigned)((h < 4 ? 4 : h) - 1);
+        if (end - beg > G * kLaneArcsLimit) {  // bins never give a group more
+            acc.err = 1;
+            end = beg;
+        }
     }
-    for (int sl = gl; sl <= (int)mask; sl += G) {
-        key[sl * ST] = kEmpty;
-        val[sl * ST] = 0;
-    }
-    __syncwarp();
-    // up to kLaneArcsLimit arcs per lane: all of a lane's arcs and labels in flight at once
-    insert_arcs<ST, kLaneArcsLimit>(s, i, beg + gl, end, G, key, val, mask, acc);
+    // all of a lane's arcs (at most kLaneArcsLimit) and labels in flight at once
+    int own[kLaneArcsLimit];
+    insert_owned<ST, kLaneArcsLimit>(s, i, beg + gl, end, G, key, val, mask, own, acc);
     __syncwarp();
     Best b;
     best_init(b);
     int e_old = 0;
-    if (valid) eval_slots<ST>(s, cc, key, val, gl, mask, G, ci, ki, tm, b, e_old);
+    owner_eval<ST, kLaneArcsLimit>(cc, key, val, own, ci, ki, tm, b, e_old);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
@@ -385,7 +441,7 @@ __device__ void warp_group_sweep(const Sweep &s, const Cls &cc, const int32_t *v
         acc.ein += ein;
         acc.moved += mv ? 1 : 0;
     }
-    __syncwarp();
+    __syncwarp();  // every owned slot is clear before the next item inserts
 }
 
 // ------------------------------------------------------------ block items
@@ -394,7 +450,8 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
                                    Acc &acc) {
     if (!live(s, i)) return;  // block-uniform
     const long long tm = tm_of(s, i);
-    const int beg = s.off[i], end = s.off[i + 1];
+    const int beg = s.off[i];
+    int end = s.off[i + 1];
     const int ci = ldC(s, i), ki = s.k[i];
     unsigned long long cmi = 0;
     int lp = 0;
@@ -403,19 +460,19 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
         lp = s.loop[i];
     }
     const unsigned mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+    if (end - beg > kCtaMaxLimit) {  // bins never give a CTA more (block-uniform)
+        acc.err = 1;
+        end = beg;
+    }
     int *key = dyn;
     int *val = dyn + kCtaSlots;
-    for (int sl = threadIdx.x; sl <= (int)mask; sl += kSwBlock) {
-        key[sl] = kEmpty;
-        val[sl] = 0;
-    }
-    __syncthreads();
-    insert_arcs<1>(s, i, beg + threadIdx.x, end, kSwBlock, key, val, mask, acc);
+    int own[kCtaArcs];
+    insert_owned<1, kCtaArcs>(s, i, beg + threadIdx.x, end, kSwBlock, key, val, mask, own, acc);
     __syncthreads();
     Best b;
     best_init(b);
     int e_old = 0;
-    eval_slots<1>(s, cc, key, val, threadIdx.x, mask, kSwBlock, ci, ki, tm, b, e_old);
+    owner_eval<1, kCtaArcs>(cc, key, val, own, ci, ki, tm, b, e_old);
     block_best(b, e_old, red);
     if (threadIdx.x == 0) {
         int ein = 0;
@@ -455,6 +512,7 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 // appended to the hub's occupied list (one counter update per warp) for the
 // evaluation after a grid barrier.
 constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
+static_assert(kHubSmemSlots <= kCtaSlots, "hub chunk table fits the key half");
 __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
                             int ki, unsigned long long cmi, int lp, long long tm, BlockRed &red,
                             Acc &acc);
@@ -476,12 +534,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const unsigned long long cmi = __ldcg(&cc.xr[ci]);
     const int start = beg + (chunk - first) * kHubChunk;
     const int stop = min(end, start + kHubChunk);
-    int *key = dyn, *val = dyn + kHubSmemSlots;
-    for (int sl = threadIdx.x; sl < kHubSmemSlots; sl += kSwBlock) {
-        key[sl] = kEmpty;
-        val[sl] = 0;
-    }
-    __syncthreads();
+    int *key = dyn, *val = dyn + kCtaSlots;  // both empty on entry
     insert_arcs<1>(s, i, start + threadIdx.x, stop, kSwBlock, key, val, kHubSmemSlots - 1, acc);
     __syncthreads();
     static_assert(kHubSmemSlots == kU * kSwBlock, "one pass over the chunk's table");
@@ -494,6 +547,8 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
         for (int u = 0; u < kU; ++u) {
             cl[u] = key[threadIdx.x + u * kSwBlock];
             sum[u] = val[threadIdx.x + u * kSwBlock];
+            key[threadIdx.x + u * kSwBlock] = kEmpty;  // each thread clears the slots it read
+            val[threadIdx.x + u * kSwBlock] = 0;
             hslot[u] = hash32(cl[u]) & mask;
             prev[u] = cl[u] != kEmpty ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
         }
@@ -719,7 +774,13 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
     __shared__ int s_item;
     Acc acc;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int *region = dyn + wib * kWarpRegion;
+    int *kreg = dyn + wib * kGroupTableInts;
+    int *vreg = dyn + kCtaSlots + wib * kGroupTableInts;
+    for (int t = threadIdx.x; t < kCtaSlots; t += kSwBlock) {
+        dyn[t] = kEmpty;
+        dyn[kCtaSlots + t] = 0;
+    }
+    __syncthreads();
     const int gthread = blockIdx.x * kSwBlock + threadIdx.x;
     const int nthreads = gridDim.x * kSwBlock;
     unsigned bar_passed = 0;
@@ -825,12 +886,12 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             const unsigned long long tw0 = gtimer();
 #endif
             switch (gb) {
-            case 5: warp_group_sweep<32>(s, cc, s.order + lo, cnt, base, region, acc); break;
-            case 4: warp_group_sweep<16>(s, cc, s.order + lo, cnt, base, region, acc); break;
-            case 3: warp_group_sweep<8>(s, cc, s.order + lo, cnt, base, region, acc); break;
-            case 2: warp_group_sweep<4>(s, cc, s.order + lo, cnt, base, region, acc); break;
-            case 1: warp_group_sweep<2>(s, cc, s.order + lo, cnt, base, region, acc); break;
-            default: warp_group_sweep<1>(s, cc, s.order + lo, cnt, base, region, acc); break;
+            case 5: warp_group_sweep<32>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
+            case 4: warp_group_sweep<16>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
+            case 3: warp_group_sweep<8>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
+            case 2: warp_group_sweep<4>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
+            case 1: warp_group_sweep<2>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
+            default: warp_group_sweep<1>(s, cc, s.order + lo, cnt, base, kreg, vreg, acc); break;
             }
 #ifdef LV_TRACE
             if (lane == 0 && blockIdx.x < 16)
