@@ -3,15 +3,21 @@
 
 One step = one whole run of the method (vertex following, colouring, every
 phase's sweeps, modularity, coarse rebuilds) on one synthetic graph already
-resident in HBM.  The metric is edge visits per second: the arcs scanned by
-all sweep iterations of the run divided by the run's device time.
+resident in HBM.  The default workload is the largest single-GPU one: a
+Chung-Lu power-law graph of 2^24 vertices and about 2.5e8 edges (every
+heuristic on).  ``value`` is edge visits per second of the whole run (the
+arcs scanned by all sweep iterations divided by the run's device time);
+``edge_visits_per_s_sweep`` divides the same arcs by the sweep time alone.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat20]
-  python bench.py --workload planted_batch4096   (4,096 graphs per step: graphs/s,
-                                                  against 4,096 plain runs)
-  python bench.py --workload served_mix200       (Poisson request stream through the
-                                                  server: graphs/s, p50/p99 latency,
-                                                  against sequential plain solves)
+The default line also carries two sub-records measured in the same process:
+``batched`` (4,096 planted-partition graphs of 100-50,000 vertices as one
+batch, against the same graphs through 4,096 plain lv_run calls) and
+``served`` (2,000 requests arriving as a Poisson stream at 200 per second,
+served with continuous batching, against sequential plain solves; p50/p99).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload chunglu24]
+  python bench.py --workload planted_batch4096   (the batch alone as the line)
+  python bench.py --workload served_mix2000      (the request stream alone)
   python bench.py --impl reference ...   (the serial oracle on host cores)
 
 With N > 1 (torchrun) every rank runs an independent replica on its own GPU
@@ -35,26 +41,42 @@ METRIC = "edge visits/s per sweep (whole run, bit-exact labels)"
 UNIT = "edge visits/s"
 BYTES_PER_ARC = 12     # col 4 + w 4 + C[col] 4
 BYTES_PER_VERTEX = 28  # rowptr 8 + C 4 + k 4 + a,|C| of own community 8 + label write 4
+SWEEP_SOURCES = ("lv_sweep.cu", "lv_ops.cuh", "lv_internal.cuh", "lv_engine.cuh")
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of
-# the dominant kernel, from ncu captures of the current kernels; None where
-# no capture applies
-MEASURED_TRAFFIC = {
-    # sweep_persistent_kernel, rmat20 phase 0 iteration 3 (all 232 classes)
-    "rmat20": {"bytes": 335_230_976 + 17_168_128,
-               "scope": "one phase-0 sweep launch (iteration 3, 232 colour classes)"},
-    # batched sweep: traffic / algorithmic bytes of a 512-graph capture
-    # (1,290.2 MB / 914.1 MB), applied to a phase-0 launch of the full batch
-    "planted_batch4096": {"ratio": 1290.2 / 914.1,
-                          "scope": "one phase-0 sweep launch of all 4,096 graphs, scaled by "
-                                   "units from a 512-graph capture"},
-}
+# the dominant kernel, from ncu captures.  Each entry records the digest of
+# the sweep kernel's sources at capture time; when the sources change the
+# entry no longer applies and the line reports traffic as null.
+MEASURED_TRAFFIC: dict = {}
 # bounded oracle samples (host-core baseline): the oracle's whole pipeline
 # on the same graph, cut after these many phases / iterations
 CPU_SAMPLE = {"rmat20": dict(max_phases=1, max_iters=3),
-              "chunglu24": dict(max_phases=1, max_iters=1),
               "planted1k": dict(),
               "rmat16": dict(),
               "chunglu20": dict(max_phases=1, max_iters=3)}
+# workloads too large for a whole oracle iteration within the bench: the
+# oracle's vertex following once, then its sweep of a block of this many
+# phase-0 vertices (ids are shuffled, so a block is a random sample) as one
+# class of an uncoloured first iteration; (bench baseline, reference step)
+CPU_SWEEP_SAMPLE = {"chunglu24": (1 << 22, 1 << 20)}
+
+
+def sweep_source_digest() -> str:
+    """SHA-256 (first 16 hex digits) of the sweep kernel's source files."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1410_1237_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_entry(workload: str):
+    """The ncu traffic record of a workload if it was taken from the current
+    sweep sources, else None."""
+    e = MEASURED_TRAFFIC.get(workload)
+    if e and e.get("sources") == sweep_source_digest():
+        return e
+    return None
 
 
 def dist_env():
@@ -154,16 +176,37 @@ class ClockSampler:
 def cpu_baseline(workload: str, g, prm) -> dict:
     """The oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
+    if workload in CPU_SWEEP_SAMPLE:
+        count = CPU_SWEEP_SAMPLE[workload][0]
+        t0 = time.perf_counter()
+        (rp, cl, w), _ = oracle.vertex_following(g.rowptr, g.col, g.w)
+        t_vf = time.perf_counter() - t0
+        mv, vis, dt = oracle.sweep_sample(rp, cl, w, 0, count)
+        return {"value": vis / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"{workload}: the oracle's sweep of phase-0 vertices [0, {count}) "
+                          f"(of {len(rp) - 1} after its vertex following, {t_vf:.1f} s, not "
+                          f"timed) as one class of an uncoloured first iteration; {vis} edge "
+                          f"visits, {mv} moves, {dt:.2f} s"}
     sample = dict(CPU_SAMPLE.get(workload, dict(max_phases=1, max_iters=2)))
     t0 = time.perf_counter()
-    r = oracle.run(g.rowptr, g.col, g.w, **prm, **sample)
+    r = oracle.run(g.rowptr, g.col, g.w, **{**prm, **sample})
     dt = time.perf_counter() - t0
     visits = sum(r.phases[t[0]].arcs for t in r.iters)
-    desc = "whole run" if not sample else \
-        "vertex following + colouring + " + ", ".join(f"{k}={v}" for k, v in sample.items())
     return {"value": visits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{workload}: {desc}; {len(r.iters)} iterations, {visits} edge visits, "
-                      f"{dt:.2f} s"}
+            "sample": f"{workload}: {sample_desc(sample)}; {len(r.iters)} iterations, "
+                      f"{visits} edge visits, {dt:.2f} s"}
+
+
+def sample_desc(sample: dict) -> str:
+    if not sample:
+        return "whole run"
+    parts = ["vertex following"]
+    if sample.get("coloring", 1):
+        parts.append("colouring")
+    parts += [f"{k}={v}" for k, v in sample.items() if k != "coloring"]
+    if sample.get("coloring", 1) == 0:
+        parts.append("phase 0 uncoloured")
+    return " + ".join(parts)
 
 
 def run_reference(args):
@@ -174,24 +217,36 @@ def run_reference(args):
     import graphgen
     g, prm = graphgen.workload(args.workload)
     import oracle
-    sample = dict(CPU_SAMPLE.get(args.workload, dict(max_phases=1, max_iters=2)))
     times, visits = [], 0
-    for step in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        r = oracle.run(g.rowptr, g.col, g.w, **prm, **sample)
-        dt = time.perf_counter() - t0
-        if step >= args.warmup:
-            times.append(dt)
-            visits = sum(r.phases[t[0]].arcs for t in r.iters)
+    if args.workload in CPU_SWEEP_SAMPLE:
+        count = CPU_SWEEP_SAMPLE[args.workload][1]
+        (rp, cl, w), _ = oracle.vertex_following(g.rowptr, g.col, g.w)
+        for step in range(args.warmup + args.steps):
+            _, vis, dt = oracle.sweep_sample(rp, cl, w, 0, count)
+            if step >= args.warmup:
+                times.append(dt)
+                visits = vis
+        desc = (f"{args.workload}: per step, the oracle's sweep of phase-0 vertices [0, {count}) "
+                f"(after its vertex following, done once) as one class of an uncoloured first "
+                f"iteration; {visits} edge visits per step")
+    else:
+        sample = dict(CPU_SAMPLE.get(args.workload, dict(max_phases=1, max_iters=2)))
+        for step in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            r = oracle.run(g.rowptr, g.col, g.w, **{**prm, **sample})
+            dt = time.perf_counter() - t0
+            if step >= args.warmup:
+                times.append(dt)
+                visits = sum(r.phases[t[0]].arcs for t in r.iters)
+        desc = f"{args.workload}: {sample_desc(sample)} per step"
     tot = sum(times)
     value = visits * len(times) / tot
-    desc = "whole run" if not sample else ", ".join(f"{k}={v}" for k, v in sample.items())
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": {"workload": args.workload, "n": g.n, "arcs": g.arcs},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.workload}: {desc}"},
+                             "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -259,12 +314,13 @@ def run_reference_batch(args):
     return 0
 
 
-def bench_batch(args, lv, torch, dev, pg, rank, world, local):
-    """planted_batch4096: the 4,096-graph batch as one handle (one persistent
-    sweep launch per batched iteration) against the same graphs run by 4,096
-    plain lv_run calls on resident handles."""
+def measure_batch(lv, torch, dev, pg, world, local, steps, warmup, plain=True, e2e=True,
+                  cpu=True, workload="planted_batch4096") -> dict:
+    """The 4,096-graph batch as one handle (one persistent sweep launch per
+    batched iteration) against the same graphs run by 4,096 plain lv_run
+    calls on resident handles.  Returns the measurements as a dict."""
     import numpy as np
-    b = batch_workload(args.workload)
+    b = batch_workload(workload)
     stream = torch.cuda.Stream(dev)
     cs = stream.cuda_stream
     with torch.cuda.stream(stream):
@@ -273,7 +329,7 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
     torch.cuda.synchronize(dev)
     h = lv.lv_batch_create(b.num_graphs, *dt, stream=cs)
     params = lv.make_params(**BATCH_PARAMS, autotune=1, collect_timing=1)
-    for _ in range(args.warmup):  # the first run also measures the bins of each phase
+    for _ in range(warmup):  # the first run also measures the bins of each phase
         lv.lv_batch_run(h, params)
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(local)
@@ -282,8 +338,9 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         pg.barrier()
     torch.cuda.synchronize(dev)
     step_ms, launches, sweep_ms, sweep_bytes, nsweeps = [], 0, 0.0, 0.0, 0
+    sweep_arcs = 0
     st0_arcs = st0_n = 0
-    for _ in range(args.steps):
+    for _ in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -300,24 +357,24 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         for sw in sws:
             if sw.ms > 0:
                 sweep_ms += sw.ms
+                sweep_arcs += sw.arcs
                 sweep_bytes += BYTES_PER_ARC * sw.arcs + BYTES_PER_VERTEX * sw.vertices
                 nsweeps += 1
     torch.cuda.synchronize(dev)
-    total_ms = sum(step_ms)
-    total_ms = max_over_ranks(total_ms, pg, dev)
+    total_ms = max_over_ranks(sum(step_ms), pg, dev)
     clk = clocks.stop()
     st = lv.lv_batch_get_stats(h)
     batch_labels = np.empty(b.n, dtype=np.int32)
     lv.lv_batch_get_labels(h, -1, -1, batch_labels)
     qs = [lv.lv_batch_get_graph_info(h, g).q for g in range(b.num_graphs)]
     lv.lv_batch_destroy(h)
-    value = whole_job_rate(b.num_graphs * args.steps, world, total_ms / 1e3)
+    value = whole_job_rate(b.num_graphs * steps, world, total_ms / 1e3)
     peak, peak_src = measured_peak_gbs()
     achieved = (sweep_bytes / (sweep_ms / 1e3) / 1e9) if sweep_ms > 0 else None
 
     # ---- the same graphs as 4,096 plain runs on resident handles (one pass)
-    plain = None
-    if not args.no_plain:
+    plain_rec = None
+    if plain:
         handles = []
         for g in range(b.num_graphs):
             lo, hi = int(b.gptr[g]), int(b.gptr[g + 1])
@@ -341,24 +398,25 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
         e1.synchronize()
         plain_ms = e0.elapsed_time(e1)
         same = True
-        for g in range(0, b.num_graphs, 41):  # identical labels, sampled
+        for g in range(b.num_graphs):  # identical labels, every graph
             one = np.empty(int(b.gptr[g + 1] - b.gptr[g]), dtype=np.int32)
             lv.lv_get_labels(handles[g], -1, one)
             same = same and bool(np.array_equal(one, batch_labels[b.gptr[g]:b.gptr[g + 1]]))
         for hh in handles:
             lv.lv_graph_destroy(hh)
-        plain = {"value": b.num_graphs / (plain_ms / 1e3), "unit": BATCH_UNIT,
-                 "ms": plain_ms, "launch": "one lv_run per graph, handles resident",
-                 "labels_identical_sampled": same}
+        plain_rec = {"value": b.num_graphs / (plain_ms / 1e3), "unit": BATCH_UNIT,
+                     "ms": plain_ms, "launch": "one lv_run per graph, handles resident",
+                     "labels_identical_all": same}
 
     # ---- end to end from pinned host buffers through the batch API
-    e2e = None
-    if not args.no_e2e:
+    e2e_rec = None
+    if e2e:
         hp = [torch.from_numpy(x).pin_memory() for x in (b.gptr, b.rowptr, b.col, b.w)]
         out = torch.empty(b.n, dtype=torch.int32).pin_memory()
         p2 = lv.make_params(**BATCH_PARAMS)
         times = []
-        for i in range(max(1, args.warmup // 2) + args.steps):
+        nwarm = 1
+        for i in range(nwarm + steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             hh = lv.lv_batch_create(b.num_graphs, *[x.numpy() for x in hp], stream=cs)
@@ -366,39 +424,39 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
             lv.lv_batch_get_labels(hh, -1, -1, out.numpy())
             lv.lv_batch_destroy(hh)
             t1 = time.perf_counter()
-            if i >= max(1, args.warmup // 2):
+            if i >= nwarm:
                 times.append(t1 - t0)
-        tt = sum(times)
-        tt = max_over_ranks(tt, pg, dev)
-        e2e = {"value": whole_job_rate(b.num_graphs * len(times), world, tt), "unit": BATCH_UNIT,
-               "h2d_bytes_per_step": int(sum(x.nbytes for x in (b.gptr, b.rowptr, b.col, b.w))),
-               "d2h_bytes_per_step": int(4 * b.n), "s_per_step": tt / len(times)}
+        tt = max_over_ranks(sum(times), pg, dev)
+        e2e_rec = {"value": whole_job_rate(b.num_graphs * len(times), world, tt),
+                   "unit": BATCH_UNIT,
+                   "h2d_bytes_per_step": int(sum(x.nbytes for x in (b.gptr, b.rowptr, b.col,
+                                                                     b.w))),
+                   "d2h_bytes_per_step": int(4 * b.n), "s_per_step": tt / len(times)}
+    del dt, flush
+    torch.cuda.empty_cache()
 
-    if rank != 0:
-        return 0
-    line = {
-        "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded generator; same batch on every rank)",
-        "config": {"workload": args.workload, "graphs": b.num_graphs, "n": b.n, "arcs": b.arcs,
-                   "params": BATCH_PARAMS, "parallelism": f"replicas x{world}",
+    tr = traffic_entry(workload)
+    alg0 = BYTES_PER_ARC * st0_arcs + BYTES_PER_VERTEX * st0_n
+    rec = {
+        "metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "steps": steps,
+        "warmup": warmup, "ms_per_step": total_ms / steps,
+        "config": {"workload": workload, "graphs": b.num_graphs, "n": b.n, "arcs": b.arcs,
+                   "params": BATCH_PARAMS,
                    "l2": "input larger than L2 and a 256 MB L2 flush before every step",
                    "phases_max": st.num_phases, "batched_sweeps": st.sweep_launches,
                    "sweeps_from_cuda_graph": st.graph_launches,
                    "iterations_all_graphs": st.total_iterations,
                    "edge_visits_per_step": st.edge_visits,
                    "q_min": min(qs), "q_median": statistics.median(qs)},
-        "plain_launches": plain,
-        "speedup_vs_plain": (value / world / plain["value"]) if plain else None,
+        "edge_visits_per_s_sweep": (sweep_arcs / (sweep_ms / 1e3)) if sweep_ms > 0 else None,
+        "plain_launches": plain_rec,
+        "speedup_vs_plain": (value / world / plain_rec["value"]) if plain_rec else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": (MEASURED_TRAFFIC[args.workload]["ratio"] *
-                                 (BYTES_PER_ARC * st0_arcs + BYTES_PER_VERTEX * st0_n))
-                     if st0_arcs else None,
-                     "traffic_scope": MEASURED_TRAFFIC[args.workload]["scope"],
-                     "algorithmic_bytes_phase0_launch": BYTES_PER_ARC * st0_arcs +
-                     BYTES_PER_VERTEX * st0_n,
+                     "traffic": (tr["ratio"] * alg0) if (tr and st0_arcs) else None,
+                     "traffic_scope": tr["scope"] if tr else
+                     "null: no ncu capture of the current sweep sources",
+                     "algorithmic_bytes_phase0_launch": alg0,
                      "kernel": "batched sweep (persistent launch over all iterating graphs)",
                      "bytes_per_unit": f"{BYTES_PER_ARC} B/arc + {BYTES_PER_VERTEX} B/vertex "
                                        "of the swept graphs",
@@ -406,12 +464,30 @@ def bench_batch(args, lv, torch, dev, pg, rank, world, local):
                      "sweeps_timed": nsweeps},
         "clocks": clk,
         "gpu_launches": launches,
-        "e2e": e2e,
+        "e2e": e2e_rec,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if cpu and world == 1:
         v, desc = oracle_graphs_per_s(b)
-        line["cpu_baseline"] = {"value": v, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
-                                "sample": desc}
+        rec["cpu_baseline"] = {"value": v, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
+                               "sample": desc}
+    return rec
+
+
+def bench_batch(args, lv, torch, dev, pg, rank, world, local):
+    """--workload planted_batch4096: the batch as the line."""
+    rec = measure_batch(lv, torch, dev, pg, world, local, args.steps, args.warmup,
+                        plain=not args.no_plain, e2e=not args.no_e2e,
+                        cpu=not args.no_cpu_baseline, workload=args.workload)
+    if rank != 0:
+        return 0
+    line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"),
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded generator; same batch on every rank)"}
+    rec.pop("steps"), rec.pop("warmup")
+    rec["config"]["parallelism"] = f"replicas x{world}"
+    line.update(rec)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -420,13 +496,15 @@ SERVED_METRIC = "served graphs/s under Poisson arrivals (whole run per request, 
 SERVED_PARAMS = dict(vertex_following=1, coloring=1, color_cutoff=100_000, theta_low=1e-6,
                      theta_high=1e-2)  # every heuristic on
 SERVED_BUDGET = 120 << 30
+SERVED_WORKLOADS = {"served_mix2000": 2000, "served_mix200": 200}
 
 
 def served_workload(name: str):
     import graphgen
-    if name != "served_mix200":
+    if name not in SERVED_WORKLOADS:
         raise SystemExit(f"unknown served workload {name}")
-    return graphgen.served_stream(num_requests=200, rate=200.0, seed=5)
+    return graphgen.served_stream(num_requests=SERVED_WORKLOADS[name], rate=200.0, seed=5,
+                                  workers=min(8, os.cpu_count() or 1))
 
 
 def pct(xs, q):
@@ -462,27 +540,34 @@ def serve_once(lv, reqs):
     return out, st
 
 
+def oracle_served_sample(reqs, budget_s: float) -> tuple[float, str]:
+    """The oracle on the smallest requests of the stream until about
+    budget_s seconds of CPU work (whole run each)."""
+    import oracle
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i][1].arcs)
+    t_tot, done = 0.0, 0
+    for i in order:
+        g = reqs[i][1]
+        t0 = time.perf_counter()
+        oracle.run(g.rowptr, g.col, g.w, **SERVED_PARAMS)
+        t_tot += time.perf_counter() - t0
+        done += 1
+        if t_tot >= budget_s:
+            break
+    return done / t_tot, (f"the {done} smallest of {len(reqs)} requests, whole run each, "
+                          f"{t_tot:.2f} s")
+
+
 def run_reference_served(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
     reqs = served_workload(args.workload)
-    order = sorted(range(len(reqs)), key=lambda i: reqs[i][1].arcs)  # smallest first: bounded
     vals, desc = [], ""
     for step in range(args.warmup + args.steps):
-        t_tot, done = 0.0, 0
-        for i in order:
-            g = reqs[i][1]
-            t0 = time.perf_counter()
-            oracle.run(g.rowptr, g.col, g.w, **SERVED_PARAMS)
-            t_tot += time.perf_counter() - t0
-            done += 1
-            if t_tot >= 6.0:
-                break
-        desc = f"the {done} smallest of {len(reqs)} requests, whole run each, {t_tot:.2f} s"
+        v, desc = oracle_served_sample(reqs, 6.0)
         if step >= args.warmup:
-            vals.append(done / t_tot)
+            vals.append(v)
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": SERVED_METRIC, "value": value, "unit": "graphs/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
@@ -497,13 +582,14 @@ def run_reference_served(args):
     return 0
 
 
-def bench_served(args, lv, torch, dev, pg, rank, world, local):
-    """served_mix200: 200 requests (R-MAT scale 10-20 and planted graphs of
-    1e3-1e6 vertices) arriving as a Poisson stream at 200 req/s, served with
-    continuous batching, against the same stream solved one request at a time
-    by plain lv_run calls in arrival order."""
+def measure_served(lv, torch, dev, pg, world, local, steps, warmup, cpu=True,
+                   workload="served_mix2000") -> dict:
+    """The request stream (R-MAT scale 10-20 and planted graphs of 1e3-1e6
+    vertices, Poisson arrivals at 200 req/s) served with continuous batching,
+    against the same stream solved one request at a time by plain lv_run
+    calls in arrival order.  Returns the measurements as a dict."""
     import numpy as np
-    reqs = served_workload(args.workload)
+    reqs = served_workload(workload)
     N = len(reqs)
     in_bytes = int(sum(g.rowptr.nbytes + g.col.nbytes + g.w.nbytes for _, g in reqs))
     out_bytes = int(sum(4 * g.n for _, g in reqs))
@@ -513,14 +599,14 @@ def bench_served(args, lv, torch, dev, pg, rank, world, local):
     if pg:
         pg.barrier()
     lat, spans, launches, rounds, sweeps, peak_g = [], [], 0, 0, 0, 0
-    results = None
-    for step in range(args.warmup + args.steps):
+    results, worker_ms = None, {}
+    for step in range(warmup + steps):
         out, st = serve_once(lv, reqs)
         infos = [i for _, i in out]
         if any(i.status != 0 for i in infos):
             raise SystemExit("a served request failed")
         span = (max(i.t_done_ms for i in infos) - min(i.t_submit_ms for i in infos)) / 1e3
-        if step >= args.warmup:
+        if step >= warmup:
             spans.append(span)
             lat += [i.t_done_ms - i.t_submit_ms for i in infos]
             launches += st.kernel_launches
@@ -530,7 +616,7 @@ def bench_served(args, lv, torch, dev, pg, rank, world, local):
                          "results": st.ms_results}
             results = out
     clk = clocks.stop()
-    total_s = max_over_ranks(sum(spans), pg, dev if dev.type == "cuda" else dev)
+    total_s = max_over_ranks(sum(spans), pg, dev)
     value = whole_job_rate(N * len(spans), world, total_s)
 
     # ---- the same stream solved one request at a time (FIFO, plain lv_run)
@@ -551,25 +637,23 @@ def bench_served(args, lv, torch, dev, pg, rank, world, local):
         finish = max(finish, a) + sv
         seq_lat.append(1e3 * (finish - a))
     seq_span = finish - reqs[0][0]
-    if rank != 0:
-        return 0
-    line = {
-        "metric": SERVED_METRIC, "value": value, "unit": "graphs/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(spans) / len(spans),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded Poisson request stream; same stream on every rank)",
-        "config": {"workload": args.workload, "requests": N, "rate_req_s": 200.0,
+    seq_value = N / seq_span
+    rec = {
+        "metric": SERVED_METRIC, "value": value, "unit": "graphs/s", "steps": steps,
+        "warmup": warmup, "ms_per_step": 1e3 * sum(spans) / len(spans),
+        "config": {"workload": workload, "requests": N, "rate_req_s": 200.0,
                    "params": SERVED_PARAMS, "mem_budget_bytes": SERVED_BUDGET,
-                   "parallelism": f"replicas x{world}", "arcs_total": int(sum(g.arcs for _, g in reqs)),
+                   "arcs_total": int(sum(g.arcs for _, g in reqs)),
                    "l2": "inputs larger than L2 (whole stream per step)",
-                   "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
                    "rounds": rounds, "batched_sweeps": sweeps, "peak_resident_requests": peak_g,
                    "worker_ms_last_step": worker_ms},
-        "sequential_plain": {"value": N / seq_span, "unit": "graphs/s",
-                             "latency_ms_p50": pct(seq_lat, 50), "latency_ms_p99": pct(seq_lat, 99),
+        "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
+        "sequential_plain": {"value": seq_value, "unit": "graphs/s",
+                             "latency_ms_p50": pct(seq_lat, 50),
+                             "latency_ms_p99": pct(seq_lat, 99),
                              "service_s_total": sum(service),
                              "labels_identical_all": same},
-        "speedup_vs_sequential": value / world / (N / seq_span),
+        "speedup_vs_sequential": value / world / seq_value,
         "roofline": None,
         "clocks": clk,
         "gpu_launches": launches,
@@ -577,22 +661,27 @@ def bench_served(args, lv, torch, dev, pg, rank, world, local):
                 "d2h_bytes_per_step": out_bytes,
                 "note": "the served value is end to end: host CSRs in, host labels out"},
     }
-    if not args.no_cpu_baseline and world == 1:
-        import oracle
-        order = sorted(range(N), key=lambda i: reqs[i][1].arcs)
-        t_tot, done = 0.0, 0
-        for i in order:
-            g = reqs[i][1]
-            t0 = time.perf_counter()
-            oracle.run(g.rowptr, g.col, g.w, **SERVED_PARAMS)
-            t_tot += time.perf_counter() - t0
-            done += 1
-            if t_tot >= 10.0:
-                break
-        line["cpu_baseline"] = {"value": done / t_tot, "unit": "graphs/s", "cores": 1,
-                                "kind": "oracle",
-                                "sample": f"the {done} smallest of {N} requests, whole run each, "
-                                          f"{t_tot:.2f} s"}
+    if cpu and world == 1:
+        v, desc = oracle_served_sample(reqs, 10.0)
+        rec["cpu_baseline"] = {"value": v, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                               "sample": desc}
+    return rec
+
+
+def bench_served(args, lv, torch, dev, pg, rank, world, local):
+    """--workload served_mix2000: the request stream as the line."""
+    rec = measure_served(lv, torch, dev, pg, world, local, args.steps, args.warmup,
+                         cpu=not args.no_cpu_baseline, workload=args.workload)
+    if rank != 0:
+        return 0
+    line = {"metric": rec.pop("metric"), "value": rec.pop("value"), "unit": rec.pop("unit"),
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": rec.pop("ms_per_step"), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded Poisson request stream; same stream on every rank)"}
+    rec.pop("steps"), rec.pop("warmup")
+    rec["config"]["parallelism"] = f"replicas x{world}"
+    line.update(rec)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -602,11 +691,17 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="rmat20")
+    ap.add_argument("--workload", default="chunglu24")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave the batched sub-record out of a single-graph line")
+    ap.add_argument("--no-served", action="store_true",
+                    help="leave the served sub-record out of a single-graph line")
+    ap.add_argument("--sub-steps", type=int, default=3,
+                    help="timed steps of the batched sub-record (after 2 warm-up steps)")
     args = ap.parse_args()
     batch = args.workload.startswith("planted_batch")
     served = args.workload.startswith("served_")
@@ -615,7 +710,6 @@ def main():
             return run_reference_served(args)
         return run_reference_batch(args) if batch else run_reference(args)
 
-    import numpy as np
     import torch
 
     import graphgen
@@ -662,6 +756,7 @@ def main():
         pg.barrier()
     torch.cuda.synchronize(dev)
     step_ms, visits, launches, sweep_ms, sweep_bytes, sweeps = [], 0, 0, 0.0, 0.0, 0
+    sweep_arcs = 0
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -680,6 +775,7 @@ def main():
             if it.ms > 0:
                 ph = infos[it.phase]
                 sweep_ms += it.ms
+                sweep_arcs += it.arcs
                 sweep_bytes += BYTES_PER_ARC * ph.arcs + BYTES_PER_VERTEX * ph.n
                 sweeps += 1
     torch.cuda.synchronize(dev)
@@ -689,7 +785,10 @@ def main():
     q = lv.lv_get_modularity(h, -1)[0]
     phases = lv.lv_num_phases(h)
     stats = lv.lv_get_stats(h)
+    infos = [lv.lv_get_phase_info(h, p) for p in range(phases)]
     lv.lv_graph_destroy(h)
+    del d_rowptr, d_col, d_w, flush
+    torch.cuda.empty_cache()
 
     value = whole_job_rate(visits * args.steps, world, total_ms / 1e3)
     peak, peak_src = measured_peak_gbs()
@@ -717,11 +816,9 @@ def main():
         e2e = {"value": whole_job_rate(visits * len(times), world, tt), "unit": UNIT,
                "h2d_bytes_per_step": int(g.rowptr.nbytes + g.col.nbytes + g.w.nbytes),
                "d2h_bytes_per_step": int(4 * g.n), "s_per_step": tt / len(times)}
+        del hp, out
 
-    if rank != 0:
-        if pg:
-            pg.destroy_process_group()
-        return 0
+    tr = traffic_entry(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -732,11 +829,18 @@ def main():
                    "l2": "input larger than L2 and a 256 MB L2 flush before every step",
                    "s_to_final_q": total_ms / args.steps / 1e3, "final_q": q,
                    "phases": phases, "iterations": stats.total_iterations,
-                   "edge_visits_per_step": visits},
+                   "edge_visits_per_step": visits,
+                   "stage_ms_last_step": {"vf": stats.ms_vf, "color": stats.ms_color,
+                                          "iterate": stats.ms_iterate,
+                                          "rebuild": stats.ms_rebuild},
+                   "phase_q": [i.q for i in infos]},
+        "s_to_final_q": total_ms / args.steps / 1e3,
+        "edge_visits_per_s_sweep": (sweep_arcs / (sweep_ms / 1e3)) if sweep_ms > 0 else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": MEASURED_TRAFFIC.get(args.workload, {}).get("bytes"),
-                     "traffic_scope": MEASURED_TRAFFIC.get(args.workload, {}).get("scope"),
+                     "traffic": tr["bytes"] if tr else None,
+                     "traffic_scope": tr["scope"] if tr else
+                     "null: no ncu capture of the current sweep sources",
                      "kernel": "sweep_persistent_kernel (one launch per iteration, all colour "
                                "classes)",
                      "bytes_per_unit": f"{BYTES_PER_ARC} B/arc + {BYTES_PER_VERTEX} B/vertex",
@@ -746,9 +850,19 @@ def main():
         "gpu_launches": launches,
         "e2e": e2e,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and rank == 0:
         line["cpu_baseline"] = cpu_baseline(args.workload, g, prm)
-    print(json.dumps(line), flush=True)
+    del g
+    # sub-records of the batched and served forms (one GPU: replicas add nothing)
+    if world == 1 and not args.no_batched:
+        line["batched"] = measure_batch(lv, torch, dev, pg, world, local, args.sub_steps, 2,
+                                        plain=not args.no_plain, e2e=False,
+                                        cpu=not args.no_cpu_baseline)
+    if world == 1 and not args.no_served:
+        line["served"] = measure_served(lv, torch, dev, pg, world, local, 1, 0,
+                                        cpu=not args.no_cpu_baseline)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
     return 0

@@ -52,6 +52,7 @@ def _load():
         lib.gg_stats.argtypes = [vp] + [ctypes.POINTER(i64)] * 3
         lib.gg_copy.argtypes = [vp, vp, vp, vp]
         lib.gg_free.argtypes = [vp]
+        lib.gg_set_threads.argtypes = [i32]
         _lib = lib
     return _lib
 
@@ -280,14 +281,15 @@ def _planted_degrees(n: int, b: int, intra_deg: float, inter_deg: float, wmax: i
     return planted(n, b, p_in, p_out, 1, wmax, seed=seed)
 
 
-def served_stream(num_requests: int = 200, rate: float = 200.0, seed: int = 5,
-                  rmat_scales=(10, 20), rmat_ef=(8, 16), planted_n=(1_000, 1_000_000)):
-    """Request stream for serving: Poisson arrivals at ``rate`` per second;
-    each request is, with equal odds, an R-MAT graph (scale and edge factor
-    uniform integers in the given ranges, (a,b,c) = (0.57, 0.19, 0.19)) or a
-    planted-partition graph (n log-uniform in ``planted_n``, 2..200 blocks,
-    mean intra-block degree 12, inter-block 2, weights 1..8).  Returns a list
-    of (arrival seconds, Graph); request i uses seed (seed << 20) + i."""
+def served_specs(num_requests: int = 200, rate: float = 200.0, seed: int = 5,
+                 rmat_scales=(10, 20), rmat_ef=(8, 16), planted_n=(1_000, 1_000_000)):
+    """Recipe of the request stream for serving: Poisson arrivals at ``rate``
+    per second; each request is, with equal odds, an R-MAT graph (scale and
+    edge factor uniform integers in the given ranges, (a,b,c) = (0.57, 0.19,
+    0.19)) or a planted-partition graph (n log-uniform in ``planted_n``,
+    2..200 blocks, mean intra-block degree 12, inter-block 2, weights 1..8).
+    Returns a list of (arrival seconds, kind, parameters, seed); request i
+    uses seed (seed << 20) + i."""
     rng = np.random.default_rng(seed)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=num_requests))
     out = []
@@ -296,10 +298,48 @@ def served_stream(num_requests: int = 200, rate: float = 200.0, seed: int = 5,
         if rng.random() < 0.5:
             sc = int(rng.integers(rmat_scales[0], rmat_scales[1] + 1))
             ef = int(rng.integers(rmat_ef[0], rmat_ef[1] + 1))
-            g = rmat(sc, ef, seed=s)
+            out.append((float(arrivals[i]), "rmat", (sc, ef), s))
         else:
             n = int(np.exp(rng.uniform(np.log(planted_n[0]), np.log(planted_n[1]))))
             b = int(rng.integers(2, 201))
-            g = _planted_degrees(n, b, 12.0, 2.0, 8, s)
-        out.append((float(arrivals[i]), g))
+            out.append((float(arrivals[i]), "planted", (n, b), s))
     return out
+
+
+def served_request(spec) -> Graph:
+    """The graph of one request of :func:`served_specs`."""
+    _, kind, prm, s = spec
+    if kind == "rmat":
+        return rmat(prm[0], prm[1], seed=s)
+    return _planted_degrees(prm[0], prm[1], 12.0, 2.0, 8, s)
+
+
+def served_stream(num_requests: int = 200, rate: float = 200.0, seed: int = 5,
+                  rmat_scales=(10, 20), rmat_ef=(8, 16), planted_n=(1_000, 1_000_000),
+                  workers: int = 0):
+    """The request stream of :func:`served_specs` as a list of (arrival
+    seconds, Graph).  ``workers`` > 1 generates that many requests side by
+    side (each with a share of the cores); the graphs are the same."""
+    specs = served_specs(num_requests, rate, seed, rmat_scales, rmat_ef, planted_n)
+    if workers <= 1:
+        return [(sp[0], served_request(sp)) for sp in specs]
+    import concurrent.futures as cf
+    lib = _load()
+    share = max(1, (os.cpu_count() or 1) // workers)
+
+    def one(sp):
+        lib.gg_set_threads(share)
+        return served_request(sp)
+
+    # largest first, so the long R-MAT requests do not end up last
+    order = sorted(range(len(specs)), key=lambda i: -_spec_cost(specs[i]))
+    graphs = [None] * len(specs)
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        for i, g in zip(order, ex.map(one, [specs[i] for i in order])):
+            graphs[i] = g
+    return [(sp[0], g) for sp, g in zip(specs, graphs)]
+
+
+def _spec_cost(spec) -> float:
+    _, kind, prm, _ = spec
+    return float(prm[1] << prm[0]) if kind == "rmat" else 14.0 * prm[0]

@@ -80,9 +80,30 @@ typedef struct {
 
 enum { MERGE_SUM = 0, MERGE_MAX = 1 };
 
-static int cmp_u64(const void *a, const void *b) {
-    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
-    return (x > y) - (x < y);
+/* Ascending sort of 64-bit keys: insertion sort for short runs, otherwise
+ * quicksort with a three-way partition (rows of R-MAT hubs repeat keys
+ * often) recursing into the smaller side, so the stack stays O(log n). */
+static void sort_u64(uint64_t *x, int64_t n) {
+    while (n > 24) {
+        const uint64_t p0 = x[0], p1 = x[n / 2], p2 = x[n - 1];
+        const uint64_t piv = p0 < p1 ? (p1 < p2 ? p1 : (p0 < p2 ? p2 : p0))
+                                     : (p0 < p2 ? p0 : (p1 < p2 ? p2 : p1));
+        int64_t lt = 0, i = 0, gt = n; /* [0,lt) < piv, [lt,i) == piv, [gt,n) > piv */
+        while (i < gt) {
+            const uint64_t v = x[i];
+            if (v < piv) { x[i] = x[lt]; x[lt] = v; ++lt; ++i; }
+            else if (v > piv) { --gt; x[i] = x[gt]; x[gt] = v; }
+            else ++i;
+        }
+        if (lt < n - gt) { sort_u64(x, lt); x += gt; n -= gt; }
+        else { sort_u64(x + gt, n - gt); n = lt; }
+    }
+    for (int64_t i = 1; i < n; ++i) {
+        const uint64_t v = x[i];
+        int64_t j = i;
+        while (j > 0 && x[j - 1] > v) { x[j] = x[j - 1]; --j; }
+        x[j] = v;
+    }
 }
 
 /* Assemble a symmetric CSR from undirected edges.  Edges with u < 0 are
@@ -133,7 +154,7 @@ static gg_graph *build_csr(int64_t n, const gg_edge *e, int64_t ne, int mode) {
     for (int64_t i = 0; i < n; ++i) {
         uint64_t *r = packed + off[i];
         int64_t d = off[i + 1] - off[i];
-        if (d > 1) qsort(r, (size_t)d, sizeof(uint64_t), cmp_u64);
+        if (d > 1) sort_u64(r, d);
         int64_t o = 0;
         for (int64_t k = 0; k < d; ++k) {
             uint32_t c = (uint32_t)(r[k] >> 32), wk = (uint32_t)r[k];
@@ -168,6 +189,17 @@ static gg_graph *build_csr(int64_t n, const gg_edge *e, int64_t ne, int mode) {
     free(off);
     free(cnt);
     return g;
+}
+
+/* Threads of the OpenMP regions that the calling thread starts (0 = the
+ * default).  Lets several host threads generate graphs side by side without
+ * oversubscribing the cores; the output never depends on it. */
+void gg_set_threads(int32_t t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
 }
 
 /* ------------------------------------------------------------ accessors */
@@ -290,12 +322,10 @@ gg_graph *gg_rmat(int32_t scale, int64_t draws, double a, double b, double c, ui
         for (int64_t d = ch * CH; d < (ch + 1) * CH && d < draws; ++d) {
             uint32_t u = 0, v = 0;
             for (int l = 0; l < scale; ++l) {
-                double x = xo_unif(&r);
-                uint32_t bu, bv;
-                if (x < a) { bu = 0; bv = 0; }
-                else if (x < ab) { bu = 0; bv = 1; }
-                else if (x < abc) { bu = 1; bv = 0; }
-                else { bu = 1; bv = 1; }
+                /* quadrant a = (0,0), b = (0,1), c = (1,0), d = (1,1) */
+                const double x = xo_unif(&r);
+                const uint32_t bu = x >= ab;
+                const uint32_t bv = (uint32_t)((x >= a) & (x < ab)) | (uint32_t)(x >= abc);
                 u = (u << 1) | bu;
                 v = (v << 1) | bv;
             }

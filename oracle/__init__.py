@@ -106,6 +106,9 @@ def _load():
         L.orc_num_iters.argtypes = [vp]
         L.orc_iters.argtypes = [vp, vp, vp, vp, vp]
         L.orc_free.argtypes = [vp]
+        L.orc_sweep_sample.restype = ctypes.c_int
+        L.orc_sweep_sample.argtypes = [i64, vp, vp, vp, i64, i64, P(i64), P(i64),
+                                       P(ctypes.c_double)]
         L.orc_compare.restype = ctypes.c_int
         L.orc_compare.argtypes = [i64, vp, vp, vp]
         _lib = L
@@ -196,6 +199,21 @@ def vertex_following(rowptr, col, w):
     out = _graph_out(h)
     L.orc_graph_free(h)
     return out, m
+
+
+def sweep_sample(rowptr, col, w, first: int, count: int) -> tuple[int, int, float]:
+    """Timing sample for the host-core baseline: the oracle's sweep of
+    vertices [first, first + count) as one class of an uncoloured first
+    iteration from the singleton partition.  Returns (moves, arcs scanned,
+    seconds of the sweep alone)."""
+    rowptr, col, w = _csr(rowptr, col, w)
+    mv, vis, sec = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    st = _load().orc_sweep_sample(len(rowptr) - 1, rowptr.ctypes.data, col.ctypes.data,
+                                  w.ctypes.data, first, count, ctypes.byref(mv),
+                                  ctypes.byref(vis), ctypes.byref(sec))
+    if st:
+        raise OracleError(st)
+    return mv.value, vis.value, sec.value
 
 
 def rebuild(rowptr, col, w, labels):

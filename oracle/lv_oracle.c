@@ -484,6 +484,50 @@ static int64_t sweep_class(const orc_graph *g, const int32_t *S, int64_t ns, int
     return nmoves;
 }
 
+/* Timing sample (for the bench's host-core baseline only): from the
+ * singleton partition of the given graph, the oracle's own sweep_class over
+ * the `count` vertices first, first+1, ... as one class of an uncoloured
+ * first iteration.  Reports the moves, the arcs those vertices scan and the
+ * wall time of the sweep alone (set-up excluded).  No other oracle result
+ * depends on this entry point. */
+int orc_sweep_sample(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *w,
+                     int64_t first, int64_t count, int64_t *moves, int64_t *visits,
+                     double *seconds) {
+    if (n <= 0 || first < 0 || count < 0 || first + count > n) return ORC_ERR_ARG;
+    orc_graph G = {n, rowptr[n], (int64_t *)rowptr, (int32_t *)col, (int32_t *)w};
+    int64_t *k = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *a = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *size = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int32_t *C = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *S = (int32_t *)malloc((size_t)(count ? count : 1) * sizeof(int32_t));
+    sweep_scratch sc;
+    sc.e = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    sc.seen = (char *)calloc((size_t)n, 1);
+    sc.touched = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    sc.mv_v = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    sc.mv_c = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!k || !a || !size || !C || !S || !sc.e || !sc.seen || !sc.touched || !sc.mv_v ||
+        !sc.mv_c) {
+        free(k); free(a); free(size); free(C); free(S);
+        free(sc.e); free(sc.seen); free(sc.touched); free(sc.mv_v); free(sc.mv_c);
+        return ORC_ERR_OOM;
+    }
+    const int64_t two_m = degrees(&G, k);
+    for (int64_t i = 0; i < n; ++i) { C[i] = (int32_t)i; a[i] = k[i]; size[i] = 1; }
+    int64_t vis = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        S[t] = (int32_t)(first + t);
+        vis += rowptr[first + t + 1] - rowptr[first + t];
+    }
+    const double t0 = now_s();
+    *moves = sweep_class(&G, S, count, C, a, size, k, two_m, &sc);
+    *seconds = now_s() - t0;
+    *visits = vis;
+    free(k); free(a); free(size); free(C); free(S);
+    free(sc.e); free(sc.seen); free(sc.touched); free(sc.mv_v); free(sc.mv_c);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------- rebuild */
 /* Coarse graph of Sec. 4.4 step 4 / Sec. 4.5 (i)-(iii): vertex c' per
  * non-empty community (renumbered in ascending old label), and for every

@@ -55,3 +55,13 @@ def test_rmat20_workload_sizes():
     assert (g.n, len(g.col)) == (1_048_576, 31_402_876)
     assert int(deg.max()) == 64_659 and int((deg == 0).sum()) == 402_622
     assert prm["coloring"] == 1 and prm["vertex_following"] == 1
+
+
+def test_served_stream_same_with_parallel_workers():
+    """Generating the request stream side by side gives the same requests."""
+    a = gg.served_stream(24, 200.0, 5, rmat_scales=(8, 12), planted_n=(500, 20_000))
+    b = gg.served_stream(24, 200.0, 5, rmat_scales=(8, 12), planted_n=(500, 20_000), workers=4)
+    assert [x for x, _ in a] == [x for x, _ in b]
+    for (_, g), (_, h) in zip(a, b):
+        assert np.array_equal(g.rowptr, h.rowptr) and np.array_equal(g.col, h.col)
+        assert np.array_equal(g.w, h.w)

@@ -615,3 +615,15 @@ def test_stop_rules_on_recorded_numerators(make):
                    theta_high=1e-2, theta_low=1e-6)
     assert any(p.colored for p in r.phases)
     _stop_rule_holds(r, 1e-2, 1e-6, 500)
+
+
+def test_sweep_sample_is_the_first_iteration():
+    """The oracle's timing sample over every vertex is the first uncoloured
+    iteration of its own run (same moves, every arc scanned once)."""
+    g = gg.rmat(12, 16, seed=2)
+    mv, vis, sec = oracle.sweep_sample(g.rowptr, g.col, g.w, 0, g.n)
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=0, coloring=0, max_iters=1,
+                   max_phases=1)
+    assert mv == r.iters[0][2] and vis == g.arcs and sec >= 0.0
+    mv2, vis2, _ = oracle.sweep_sample(g.rowptr, g.col, g.w, 100, 50)
+    assert vis2 == int(g.rowptr[150] - g.rowptr[100]) and 0 <= mv2 <= 50
