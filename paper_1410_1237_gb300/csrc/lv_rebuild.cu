@@ -54,6 +54,14 @@ constexpr int kGrpWarpSlots = 512;    // its table (power of two, 2x the arcs)
 constexpr int kGrpBlockArcs = 1024;   // at most this many: one block (larger: the sort)
 constexpr int kGrpBlockSlots = 2048;
 constexpr int kGrpBlockThreads = 512;
+// larger communities up to kGrpBigArcs arcs: one block walks the members'
+// rows into a table of kGrpBigSlots; a community with more than
+// kGrpBigDistinct distinct neighbouring communities, or more arcs (one block
+// would be the critical path of the whole rebuild), takes the sort instead
+constexpr int kGrpBigSlots = 4096;
+constexpr int kGrpBigDistinct = kGrpBigSlots / 2;
+constexpr int kGrpBigThreads = 512;
+constexpr int kGrpBigArcs = 1 << 16;
 
 __global__ void group_starts_kernel(int n, const uint32_t *__restrict__ cm_sorted, int n_next,
                                     int32_t *gs) {
@@ -228,6 +236,119 @@ __global__ void __launch_bounds__(kGrpBlockThreads) group_block_kernel(
     }
 }
 
+// communities with kGrpBlockArcs < arcs <= kGrpBigArcs, one block each: warps take
+// member rows, lanes their arcs; each arc's neighbouring community is summed
+// in a shared-memory table.  When the distinct neighbours stay within
+// kGrpBigDistinct they are sorted ascending (bitonic, in shared memory) and
+// written to the community's slice of tmp; otherwise fail[c] = 1 and the
+// community goes to the sort of its arcs.
+__global__ void __launch_bounds__(kGrpBigThreads) group_big_kernel(
+    DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ gs,
+    const int32_t *__restrict__ ga, const uint32_t *__restrict__ vo,
+    const uint32_t *__restrict__ cm, int2 *tmp, int32_t *cnt, int32_t *fail) {
+    // the table (keys, then values) and, once its entries are in registers,
+    // the sort buffer of up to kGrpBigDistinct packed (key, value) pairs
+    __shared__ unsigned long long KV[kGrpBigSlots];
+    __shared__ int s_d, s_over;
+    int *K = reinterpret_cast<int *>(KV), *V = K + kGrpBigSlots;
+    unsigned long long *S = KV;
+    static_assert(2 * kGrpBigSlots * sizeof(int) == sizeof(KV) && kGrpBigDistinct <= kGrpBigSlots,
+                  "table and sort buffer share the array");
+    constexpr int kWarps = kGrpBigThreads / 32;
+    constexpr int kPer = kGrpBigSlots / kGrpBigThreads;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
+        const int c = list[li];
+        const int a0 = ga[c], m0 = gs[c], m1 = gs[c + 1];
+        if (ga[c + 1] - a0 > kGrpBigArcs) {  // block-uniform
+            if (threadIdx.x == 0) fail[c] = 1;
+            continue;
+        }
+        for (int sl = threadIdx.x; sl < kGrpBigSlots; sl += kGrpBigThreads) {
+            K[sl] = kEmpty;
+            V[sl] = 0;
+        }
+        if (threadIdx.x == 0) {
+            s_d = 0;
+            s_over = 0;
+        }
+        __syncthreads();
+        for (int m = m0 + w; m < m1; m += kWarps) {
+            if (((volatile int *)&s_over)[0]) break;  // warp-uniform (one read per row)
+            const int u = (int)vo[m];
+            const int beg = g.off[u], end = g.off[u + 1];
+            for (int e = beg + lane; e < end; e += 32) {
+                const int2 a = g.arcs[e];
+                const int cv = (int)cm[a.x];
+                unsigned h = hash32(cv) & (kGrpBigSlots - 1);
+                bool done = false;
+                for (int probe = 0; probe < kGrpBigSlots && !done; ++probe) {
+                    const int prev = atomicCAS(&K[h], kEmpty, cv);
+                    if (prev == kEmpty || prev == cv) {
+                        atomicAdd(&V[h], a.y);
+                        if (prev == kEmpty && atomicAdd(&s_d, 1) >= kGrpBigDistinct)
+                            s_over = 1;
+                        done = true;
+                    }
+                    h = (h + 1) & (kGrpBigSlots - 1);
+                }
+                if (!done) s_over = 1;
+            }
+        }
+        __syncthreads();
+        if (s_over) {  // block-uniform
+            if (threadIdx.x == 0) fail[c] = 1;
+            __syncthreads();
+            continue;
+        }
+        const int d = s_d;
+        int kr[kPer], vr[kPer];
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            kr[t] = K[t * kGrpBigThreads + threadIdx.x];
+            vr[t] = V[t * kGrpBigThreads + threadIdx.x];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_d = 0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < kPer; ++t)
+            if (kr[t] != kEmpty) {
+                const int at = atomicAdd(&s_d, 1);  // the sort below fixes the order
+                S[at] = ((unsigned long long)(unsigned)kr[t] << 32) | (unsigned)vr[t];
+            }
+        int P = 1;
+        while (P < d) P <<= 1;
+        for (int x = d + threadIdx.x; x < P; x += kGrpBigThreads) S[x] = ~0ull;
+        __syncthreads();
+        for (int k = 2; k <= P; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int x = threadIdx.x; x < P; x += kGrpBigThreads) {
+                    const int y = x ^ j;
+                    if (y > x) {
+                        const unsigned long long sx = S[x], sy = S[y];
+                        if ((sx > sy) == ((x & k) == 0)) {
+                            S[x] = sy;
+                            S[y] = sx;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int x = threadIdx.x; x < d; x += kGrpBigThreads)
+            tmp[a0 + x] = make_int2((int)(S[x] >> 32), (int)(unsigned)S[x]);
+        if (threadIdx.x == 0) cnt[c] = d;
+        __syncthreads();
+    }
+}
+
+// arcs of the communities that failed the block path (0 for the others)
+__global__ void fail_arcs_kernel(int n_next, const int32_t *__restrict__ ga,
+                                 const int32_t *__restrict__ fail, int32_t *fail_arcs) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_next; c += gridDim.x * blockDim.x)
+        fail_arcs[c] = fail[c] ? ga[c + 1] - ga[c] : 0;
+}
+
 // communities with more arcs: their arcs as (c << b | c(v), w), one thread
 // per arc (the community by a search of the list's arc starts lstart)
 __global__ void __launch_bounds__(256) group_keys_kernel(
@@ -396,7 +517,6 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     LV_LAUNCH_CHECK();
     LV_TRY(scan_excl_i32(f_mid, pmid, n_next, s));
     LV_TRY(scan_excl_i32(f_big, pbig, n_next, s));
-    LV_TRY(scan_excl_i32(big_arcs, lpos, n_next, s));
     int32_t *list_mid = lists, *list_big = lists + n_next + 1;
     list_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, f_mid, pmid, list_mid);
     LV_LAUNCH_CHECK();
@@ -404,9 +524,9 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     LV_LAUNCH_CHECK();
     LV_CUDA(cudaMemcpyAsync(pinned, pmid + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaMemcpyAsync(pinned + 1, pbig + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaMemcpyAsync(pinned + 2, lpos + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     LV_CUDA(cudaStreamSynchronize(s));
-    const int n_mid = pinned[0], n_big = pinned[1], AL = pinned[2];
+    const int n_mid = pinned[0];
+    int n_big = pinned[1], AL = 0;
     // small and medium communities
     group_warp_kernel<<<grid_for(n_next, kGrpWarps, g_num_sms * 16), kGrpWarps * 32, 0, s>>>(
         g, n_next, gs, ga, apos, vo, cm, tmp, cnt, err);
@@ -416,7 +536,27 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
             g, n_mid, list_mid, gs, ga, apos, vo, cm, tmp, cnt, err);
         LV_LAUNCH_CHECK();
     }
-    // large communities: sort of their arcs by (community, neighbour)
+    // large communities: one block each while their distinct neighbours fit
+    // its table; the others sort their arcs by (community, neighbour)
+    if (n_big > 0) {
+        int32_t *fail = f_big;  // reused: one flag per community
+        LV_CUDA(cudaMemsetAsync(fail, 0, sizeof(int32_t) * ((size_t)n_next + 1), s));
+        group_big_kernel<<<std::min(n_big, g_num_sms * 4), kGrpBigThreads, 0, s>>>(
+            g, n_big, list_big, gs, ga, vo, cm, tmp, cnt, fail);
+        LV_LAUNCH_CHECK();
+        fail_arcs_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, ga, fail, big_arcs);
+        LV_LAUNCH_CHECK();
+        LV_TRY(scan_excl_i32(fail, pbig, n_next, s));
+        LV_TRY(scan_excl_i32(big_arcs, lpos, n_next, s));
+        list_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, fail, pbig, list_big);
+        LV_LAUNCH_CHECK();
+        LV_CUDA(cudaMemcpyAsync(pinned, pbig + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaMemcpyAsync(pinned + 1, lpos + n_next, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        n_big = pinned[0];
+        AL = pinned[1];
+    }
     if (n_big > 0) {
         uint64_t *keys, *keys_alt;
         uint32_t *vals, *vals_alt;
