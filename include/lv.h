@@ -90,6 +90,19 @@ typedef struct {
      * printed in Alg. 1, instead of the signed net gain (default 0; the
      * absolute form can cycle between two labellings until max_iters). */
     int32_t abs_threshold;
+    /* 0/1: after vertex following, merge single-neighbour vertices (one
+     * neighbour j plus an optional self-loop l) into their neighbour, round
+     * after round, while Lemma 3's bound (Eq. eqnClaimIItemp, taken at the
+     * largest community degree C(j) can have) guarantees the move: k_i^2 >
+     * 2m l_i with k_i = w(i,j) + l_i.  The extension sketched at the end of
+     * Sec. 4.3 (default 0; single-graph runs and the server's second lane;
+     * lv_batch_run returns LV_ERR_ARG). */
+    int32_t vf_recursive;
+    /* Colouring priority (Sec. 4.2 leaves the colouring order to the
+     * implementation): 0 = largest number of neighbours first, ties by the
+     * seeded hash, then by id (default: fewer colour classes, so fewer
+     * class steps per iteration); 1 = the seeded hash alone, then id. */
+    int32_t color_order;
 } lv_params;
 
 /* Per-phase record.  N values are exact modularity numerators: Q = N/(2m)^2. */

@@ -30,7 +30,8 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_NOT_SYMMETRIC", -3: "ERR_WEIGHT",
 
 DEFAULTS = dict(vertex_following=1, coloring=1, theta_low=1e-6, theta_high=1e-2,
                 color_cutoff=100_000, max_iters=10_000, max_phases=64, color_seed=0x5EED,
-                trace=0, color_phases=0, abs_threshold=0)
+                trace=0, color_phases=0, abs_threshold=0, vf_recursive=0,
+                color_order=0)
 
 
 class OracleError(RuntimeError):
@@ -57,7 +58,8 @@ class _Params(ctypes.Structure):
                 ("color_cutoff", ctypes.c_int64), ("max_iters", ctypes.c_int32),
                 ("max_phases", ctypes.c_int32), ("color_seed", ctypes.c_uint64),
                 ("trace", ctypes.c_int32), ("color_phases", ctypes.c_int32),
-                ("abs_threshold", ctypes.c_int32)]
+                ("abs_threshold", ctypes.c_int32), ("vf_recursive", ctypes.c_int32),
+                ("color_order", ctypes.c_int32)]
 
 
 def _load():
@@ -73,7 +75,7 @@ def _load():
         L.orc_gain.restype = ctypes.c_int
         L.orc_gain.argtypes = [i64, vp, vp, vp, vp, i32, i32, P(i64), P(u64)]
         L.orc_color.restype = i32
-        L.orc_color.argtypes = [i64, vp, vp, u64, vp]
+        L.orc_color.argtypes = [i64, vp, vp, u64, i32, vp]
         L.orc_rebuild.restype = ctypes.c_int
         L.orc_rebuild.argtypes = [i64, vp, vp, vp, vp, P(vp)]
         L.orc_vertex_following.restype = ctypes.c_int
@@ -178,12 +180,14 @@ def gain(rowptr, col, w, labels, i: int, c: int) -> int:
     return _i128(hi.value, lo.value)
 
 
-def color(rowptr, col, seed: int) -> tuple[int, np.ndarray]:
-    """Greedy distance-1 colouring in decreasing hash priority (R11)."""
+def color(rowptr, col, seed: int, order: int = 0) -> tuple[int, np.ndarray]:
+    """Greedy distance-1 colouring in decreasing priority (R11): (degree,
+    hash, id) for order 0, (hash, id) for order 1."""
     rowptr, col, _ = _csr(rowptr, col, None)
     n = len(rowptr) - 1
     out = np.empty(n, dtype=np.int32)
-    K = _load().orc_color(n, rowptr.ctypes.data, col.ctypes.data, seed, out.ctypes.data)
+    K = _load().orc_color(n, rowptr.ctypes.data, col.ctypes.data, seed, order,
+                          out.ctypes.data)
     return int(K), out
 
 
@@ -306,7 +310,8 @@ def run(rowptr, col, w, **params) -> Result:
     p = _Params(int(prm["vertex_following"]), int(prm["coloring"]), float(prm["theta_low"]),
                 float(prm["theta_high"]), int(prm["color_cutoff"]), int(prm["max_iters"]),
                 int(prm["max_phases"]), int(prm["color_seed"]), int(prm["trace"]),
-                int(prm["color_phases"]), int(prm["abs_threshold"]))
+                int(prm["color_phases"]), int(prm["abs_threshold"]), int(prm["vf_recursive"]),
+                int(prm["color_order"]))
     h = ctypes.c_void_p()
     st = L.orc_run(n, rowptr.ctypes.data, col.ctypes.data, w.ctypes.data, ctypes.byref(p),
                    ctypes.byref(h))

@@ -36,14 +36,15 @@
  *   R9  the loop stops when the net gain is below the threshold relative
  *       to the previous value: (double)(N_C - N_P) < theta * (double)|N_P|
  *       on exact numerators (signed: a negative gain stops it).
- *   R11 colouring = greedy distance-1 colouring in decreasing hash priority
- *       (the fixed point of Jones-Plassmann with that priority).
+ *   R11 colouring = greedy distance-1 colouring in decreasing priority
+ *       (degree, hash, id) -- the fixed point of Jones-Plassmann with that
+ *       priority; optionally (hash, id) alone.
  *   R12 colour phases use theta_high; once a coloured phase gains less than
  *       theta_high colouring stops for good; uncoloured phases use theta_low.
  *   R13 phases stop when nothing merged or an uncoloured phase gains less
  *       than theta_low relative to its singleton start (same signed test).
  *
- * Parity unpinned: the colouring priority hash (R11) and the guards
+ * Parity unpinned: the colouring priority (R11) and the guards
  * max_iters / max_phases are choices of these readings; no printed example
  * fixes them.  The threshold and phase-control semantics (R9, R12, R13) are
  * readings too; the tests check the recorded numerators of whole runs
@@ -83,6 +84,11 @@ typedef struct {
                                  first phase, the variant of the Sec. 5 experiments) */
     int32_t abs_threshold;    /* 1: every threshold test uses |N_C - N_P| (the form printed
                                  in Alg. 1) instead of the signed net gain of R9 */
+    int32_t vf_recursive;     /* 1: after vertex following, merge single-neighbour vertices
+                                 round by round while Lemma 3's bound guarantees the move
+                                 (R23; the closing paragraph of Sec. 4.3) */
+    int32_t color_order;      /* colouring priority (R11): 0 = largest degree first, hash
+                                 tie-break; 1 = hash only */
 } orc_params;
 
 typedef struct {
@@ -373,17 +379,20 @@ static orc_graph *vertex_following(const orc_graph *g, int32_t *map) {
 }
 
 /* ----------------------------------------------------------- colouring */
-/* Priority of Jones-Plassmann colouring: pi(v) = (h(v xor seed), v),
- * compared lexicographically, h = the SplitMix64 output mixing function
- * (Steele, Lea, Flood 2014).  R11. */
+/* Priority of the colouring (R11): pi(v) = (d(v), h(v xor seed), v),
+ * compared lexicographically, where d(v) is the number of neighbours of v
+ * other than v itself (largest degree first, Welsh and Powell 1967) and h is
+ * the SplitMix64 output mixing function (Steele, Lea, Flood 2014).  With
+ * order = 1 the degree is left out: pi(v) = (h(v xor seed), v). */
 static uint64_t prio_hash(uint64_t x) {
     x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
     x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
     return x ^ (x >> 31);
 }
-typedef struct { uint64_t h; int32_t v; } prio_t;
+typedef struct { int64_t d; uint64_t h; int32_t v; } prio_t;
 static int cmp_prio_desc(const void *a, const void *b) {
     const prio_t *x = (const prio_t *)a, *y = (const prio_t *)b;
+    if (x->d != y->d) return x->d < y->d ? 1 : -1;
     if (x->h != y->h) return x->h < y->h ? 1 : -1;
     return (x->v < y->v) - (x->v > y->v);
 }
@@ -391,10 +400,13 @@ static int cmp_prio_desc(const void *a, const void *b) {
 /* Greedy distance-1 colouring visiting vertices in decreasing priority; each
  * takes the smallest colour not used by an already coloured neighbour.
  * Self-loops are ignored.  Returns the number of colours. */
-static int32_t greedy_color(const orc_graph *g, uint64_t seed, int32_t *color) {
+static int32_t greedy_color(const orc_graph *g, uint64_t seed, int order, int32_t *color) {
     const int64_t n = g->n;
     prio_t *ord = (prio_t *)malloc((size_t)(n ? n : 1) * sizeof(prio_t));
     for (int64_t v = 0; v < n; ++v) {
+        int64_t d = 0;
+        for (int64_t e = g->rowptr[v]; e < g->rowptr[v + 1]; ++e) d += g->col[e] != v;
+        ord[v].d = order == 1 ? 0 : d;
         ord[v].h = prio_hash((uint64_t)v ^ seed);
         ord[v].v = (int32_t)v;
         color[v] = -1;
@@ -420,9 +432,9 @@ static int32_t greedy_color(const orc_graph *g, uint64_t seed, int32_t *color) {
 }
 
 int32_t orc_color(int64_t n, const int64_t *rowptr, const int32_t *col, uint64_t seed,
-                  int32_t *color) {
+                  int32_t order, int32_t *color) {
     orc_graph g = {n, rowptr[n], (int64_t *)rowptr, (int32_t *)col, NULL};
-    return greedy_color(&g, seed, color);
+    return greedy_color(&g, seed, order, color);
 }
 
 /* ------------------------------------------------------------- sweep */
@@ -570,6 +582,68 @@ static orc_graph *rebuild(const orc_graph *g, const int32_t *C, const int32_t *n
     return h;
 }
 
+/* ------------------------------------- recursive single-neighbour VF */
+/* The extension sketched at the end of Sec. 4.3 (R23).  A single-neighbour
+ * vertex i has exactly one neighbour j != i and an optional self-loop of
+ * weight l.  With k_i = w(i,j) + l, the lower bound of Eq. (eqnClaimIItemp)
+ * on the gain of moving i into C(j), taken at the largest community degree
+ * C(j) can have without i (a_C(j) <= 2m - k_i), is
+ *     w(i,j)/m - 2 k_i (2m - k_i) / (2m)^2,
+ * which is positive iff 2m w(i,j) > k_i (2m - k_i), i.e. iff
+ * k_i^2 > 2m l.  A vertex passing this test joins C(j) whatever the rest of
+ * the partition is, so it is merged into j before the phases start, as
+ * plain vertex following does with single-degree vertices (l = 0 always
+ * passes).  Rounds: every vertex of the current graph is tested at once; of
+ * two single-neighbour vertices adjacent to each other only the smaller id
+ * merges (R3); the merged graph is the coarse graph of that partition (a
+ * survivor's loop becomes its old loop + the merged loops + 2 w(i,j), R1,
+ * R2) with survivors renumbered ascending; rounds repeat until no vertex
+ * passes.  Takes ownership of G; map (n_orig entries) is composed. */
+static orc_graph *vf_recursive_rounds(orc_graph *G, int32_t *map, int64_t n_orig) {
+    int64_t two_m = 0;
+    for (int64_t e = 0; e < G->arcs; ++e) two_m += G->w[e];
+    for (;;) {
+        const int64_t n = G->n;
+        int32_t *target = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+        int64_t merges = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            target[i] = -1;
+            int64_t nb = 0, loop = 0, wij = 0;
+            int32_t j = -1;
+            for (int64_t e = G->rowptr[i]; e < G->rowptr[i + 1]; ++e) {
+                if (G->col[e] == i) loop += G->w[e];
+                else { nb++; j = G->col[e]; wij = G->w[e]; }
+            }
+            if (nb != 1) continue;
+            const int64_t k = wij + loop;
+            if ((i128)k * k > (i128)two_m * loop) target[i] = j;
+        }
+        int32_t *C = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t j = target[i];
+            /* of two single-neighbour vertices passing towards each other,
+             * the smaller merges into the larger */
+            const int merge = j >= 0 && !(target[j] == (int32_t)i && j < i);
+            C[i] = merge ? j : (int32_t)i;
+            merges += merge;
+        }
+        free(target);
+        if (merges == 0) {
+            free(C);
+            return G;
+        }
+        int32_t *newid = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+        int64_t nn = 0;
+        for (int64_t i = 0; i < n; ++i) newid[i] = C[i] == i ? (int32_t)nn++ : -1;
+        orc_graph *H = rebuild(G, C, newid, nn);
+        for (int64_t v = 0; v < n_orig; ++v) map[v] = newid[C[map[v]]];
+        free(C);
+        free(newid);
+        graph_free(G);
+        G = H;
+    }
+}
+
 int orc_rebuild(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t *w,
                 const int32_t *labels, orc_graph **out) {
     orc_graph g = {n, rowptr[n], (int64_t *)rowptr, (int32_t *)col, (int32_t *)w};
@@ -656,6 +730,7 @@ int orc_run(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t 
         G = graph_copy_in(n, rowptr, col, w);
         for (int64_t v = 0; v < n; ++v) map[v] = (int32_t)v;
     }
+    if (prm->vertex_following && prm->vf_recursive) G = vf_recursive_rounds(G, map, n);
     r->vf_map = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
     memcpy(r->vf_map, map, (size_t)n * sizeof(int32_t));
     r->vf_n = G->n;
@@ -681,7 +756,7 @@ int orc_run(int64_t n, const int64_t *rowptr, const int32_t *col, const int32_t 
         int32_t *color = NULL;
         if (colour_on) {
             color = (int32_t *)malloc((size_t)(np ? np : 1) * sizeof(int32_t));
-            K = greedy_color(G, prm->color_seed + (uint64_t)p, color);
+            K = greedy_color(G, prm->color_seed + (uint64_t)p, prm->color_order, color);
             cls_off = (int64_t *)calloc((size_t)K + 1, sizeof(int64_t));
             for (int64_t v = 0; v < np; ++v) cls_off[color[v] + 1]++;
             for (int32_t c = 0; c < K; ++c) cls_off[c + 1] += cls_off[c];

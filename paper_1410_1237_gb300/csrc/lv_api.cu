@@ -339,7 +339,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit)
         return LV_ERR_ARG;
     if (P.max_iters < 1 || P.max_phases < 1 || !(P.theta_low >= -1e300) ||
-        !(P.theta_high >= 0.0))
+        !(P.theta_high >= 0.0) || P.color_order < 0 || P.color_order > 1)
         return LV_ERR_ARG;
     h->timer.on = P.collect_timing != 0;
     const unsigned long long launches0 = g_kernel_launches;
@@ -356,6 +356,15 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     if (P.vertex_following) {
         DGraph G2;
         LV_TRY(vertex_following(G, h->loop_in, &G2, h->vf_map, h->pinned, s));
+        if (P.vf_recursive) {
+            int32_t vf_rounds = 0;
+            const lv_status st_vf = vf_recursive(&G2, h->two_m, h->vf_map, n_orig, h->pinned,
+                                                 &vf_rounds, s);
+            if (st_vf != LV_OK) {
+                free_graph(G2, s);
+                return st_vf;
+            }
+        }
         G = G2;
         own_g = true;
         LV_TRY(dalloc_n(&k_own, (size_t)G.n, s));
@@ -416,7 +425,8 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         int32_t K = 1;
         int32_t rounds = 0;
         if (colour_on)
-            LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, color, &K, &rounds, h->pinned, s));
+            LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, P.color_order == 0, color, &K, &rounds,
+                            h->pinned, s));
         info.color_rounds = rounds;
         info.num_colors = colour_on ? K : 0;
         BinLimits plim = lim;

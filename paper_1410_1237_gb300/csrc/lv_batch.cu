@@ -341,6 +341,7 @@ lv_status lv_batch_run(lv_batch *b, const lv_params *p) {
     lv_params P;
     if (p) P = *p;
     else lv_params_default(&P);
+    if (P.vf_recursive) return LV_ERR_ARG;  // single-graph runs only
     b->clear_results();
     const lv_status st = batch_run_impl(b, P);
     if (st != LV_OK) {

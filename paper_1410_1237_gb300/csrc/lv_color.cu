@@ -1,7 +1,10 @@
 // lv_color.cu -- distance-1 colouring (Sec. 4.2) and the per-phase vertex order.
 //
-// Colouring: Jones-Plassmann with a hash priority pi(v) = (h(v ^ seed), v).
-// Every vertex counts its higher-priority neighbours; a vertex whose count
+// Colouring: Jones-Plassmann with the priority pi(v) = (d(v), h(v ^ seed), v)
+// -- d(v) the neighbours of v other than v, largest first, then a hash -- or
+// (h(v ^ seed), v) alone.  A first pass marks, per arc, whether the
+// neighbour has the higher priority (one bit per arc, read beside the arc in
+// every round).  Every vertex counts its higher-priority neighbours; a vertex whose count
 // reaches zero takes the smallest colour not used by those neighbours, then
 // decrements the counts of its lower-priority neighbours.  The result equals
 // greedy colouring in decreasing priority order, whatever the timing, because
@@ -11,7 +14,9 @@
 // separated by a bounded grid barrier.  Ready vertices are handled by size:
 // small (< 256 arcs) one warp each; big (< 4,096 arcs) one block each; huge
 // ones are split over the blocks left over, which mark a shared global colour
-// bitmap; the last of them to finish computes the colour.
+// bitmap; the last of them to finish computes the colour; tiny ones (at
+// most 32 arcs, so a colour below 33) take 8 lanes each, 4 to a warp, and
+// find their colour in a 64-bit mask held in registers.
 //
 // Vertex order: a stable radix sort of (colour, degree bin) keys, so each
 // colour class is split into the group / warp / CTA / hub bins of the sweep,
@@ -30,22 +35,32 @@ constexpr int kJpBig = 256;          // arcs: from here a vertex uses a whole bl
 constexpr int kJpHuge = 4096;        // arcs: from here a vertex is split over blocks
 constexpr int kMexWindow = 1024;     // colours examined per pass of the mex search
 constexpr int kJpSmallU = 8;         // 32-arc chunks in flight per warp: a small vertex in one pass
+constexpr int kJpTiny = 32;          // arcs: up to here a vertex uses 8 lanes (4 per warp)
+constexpr int kJpTinyLanes = 8;
+constexpr int kJpTinyPerWarp = 32 / kJpTinyLanes;
+constexpr int kJpKinds = 4;          // small, big, huge, tiny
 
-// device state; the ring of list lengths has 3 slots of {small, big, huge}.
+// device state; the ring of list lengths has 3 slots of {small, big, huge, tiny}.
 // A list entry is {v, off[v], off[v + 1], 0}: whoever queues a vertex has
 // its row bounds already, so the round that colours it starts at its arcs.
 struct JpState {
     int32_t *cnt;          // higher-priority neighbours not yet processed
     int32_t *color;
-    int4 *list[3][2];      // [kind][round parity]
-    int32_t *counts;       // [3 ring slots][3 kinds]
+    int4 *list[kJpKinds][2];  // [kind][round parity]
+    int32_t *counts;       // [3 ring slots][kJpKinds kinds]
     int32_t *max_color;
     unsigned *huge_bm;     // 32-word first-window bitmap per slot of the huge list
     int32_t *huge_done;    // finished parts per slot of the huge list
     GridBarrier *bar;      // flag 1: a wait expired; flag 2: more rounds than vertices
     int32_t *rounds;
+    const unsigned *hb;    // bit e: arc e leads to a higher-priority neighbour
     TraceBuf tb;
 };
+
+// is the neighbour of arc e of higher priority than the row's vertex
+__device__ __forceinline__ bool higher_arc(const JpState &st, int e) {
+    return (__ldg(&st.hb[e >> 5]) >> (e & 31)) & 1u;
+}
 
 // append u (arcs [beg, end)) to the next round's list of its kind;
 // warp-aggregated
@@ -56,10 +71,10 @@ __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next,
     int kind = 0;
     if (ready) {
         const int d = end - beg;
-        kind = d >= kJpHuge ? 2 : (d >= kJpBig ? 1 : 0);
+        kind = d >= kJpHuge ? 2 : (d >= kJpBig ? 1 : (d <= kJpTiny ? 3 : 0));
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < kJpKinds; ++k) {
         const bool mine = ready && kind == k;
         const unsigned bm = __ballot_sync(0xffffffffu, mine);
         if (bm) {
@@ -79,9 +94,8 @@ __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next,
 // disjoint, so one pass serves both.  The row bounds of a lower-priority
 // neighbour are loaded beside its decrement, for the queue entry.
 template <int kU>  // chunks of 32 arcs in flight per warp
-__device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState &st, int v,
-                        unsigned long long hv, int e0, int e1, int wrank, int nw, unsigned *bm,
-                        int32_t *cnt_next, int nxt_list) {
+__device__ void jp_pass(const DGraph &g, const JpState &st, int v, int e0, int e1, int wrank,
+                        int nw, unsigned *bm, int32_t *cnt_next, int nxt_list) {
     const int lane = threadIdx.x & 31;
     const int stride = nw * 32;
     for (int b0 = e0 + wrank * 32; b0 < e1; b0 += kU * stride) {
@@ -91,11 +105,8 @@ __device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState 
         for (int u = 0; u < kU; ++u) {
             const int e = b0 + u * stride + lane;
             uu[u] = e < e1 ? g.arcs[e].x : v;
+            higher[u] = e < e1 && higher_arc(st, e);
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            higher[u] = uu[u] != v &&
-                        prio_greater(prio_hash((unsigned long long)uu[u] ^ seed), uu[u], hv, v);
         int res[kU], ob[kU], oe[kU];
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -122,8 +133,8 @@ __device__ void jp_pass(const DGraph &g, unsigned long long seed, const JpState 
 // l; windows above the first are searched by mark-only passes of this warp
 // over v's whole row (needs >= kMexWindow colours among v's higher-priority
 // neighbours).
-__device__ int warp_mex(const DGraph &g, unsigned long long seed, const JpState &st, int v,
-                        unsigned long long hv, unsigned word0, unsigned *scratch32) {
+__device__ int warp_mex(const DGraph &g, const JpState &st, int v, unsigned word0,
+                        unsigned *scratch32) {
     const int lane = threadIdx.x & 31;
     unsigned word = word0;
     const int beg = g.off[v], end = g.off[v + 1];
@@ -139,7 +150,7 @@ __device__ int warp_mex(const DGraph &g, unsigned long long seed, const JpState 
         __syncwarp();
         for (int e = beg + lane; e < end; e += 32) {
             const int u = g.arcs[e].x;
-            if (u != v && prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v)) {
+            if (u != v && higher_arc(st, e)) {
                 const int c = __ldcg(&st.color[u]) - nb;
                 if (c >= 0 && c < kMexWindow) atomicOr(&scratch32[c >> 5], 1u << (c & 31));
             }
@@ -155,19 +166,107 @@ __device__ __forceinline__ void set_color(const JpState &st, int v, int mex) {
     atomicMax(st.max_color, mex);
 }
 
-__global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long long seed, JpState st) {
+// Tiny vertices (at most kJpTiny arcs), 32 / LANES per warp with LANES
+// lanes each: every lane holds up to kJpTiny / LANES arcs, all loads in
+// flight at once.  A tiny vertex has at most 32 higher-priority neighbours,
+// so its colour is below 33: the colours of those neighbours go into a
+// 64-bit mask in registers, OR-reduced over the group, and the colour is its
+// lowest clear bit.  Lower-priority neighbours are released as in jp_pass.
+// Every lane of the warp calls this (t >= n marks an empty group).
+template <int LANES>
+__device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *list, int t, int n,
+                             int32_t *cnt_next, int nxt_list) {
+    constexpr int kA = kJpTiny / LANES;
+    const int lane = threadIdx.x & 31, gl = lane & (LANES - 1);
+    const bool has = t < n;
+    const int4 it = has ? __ldcg(&list[t]) : make_int4(-1, 0, 0, 0);
+    const int v = it.x;
+    int uu[kA];
+    bool higher[kA];
+#pragma unroll
+    for (int a = 0; a < kA; ++a) {
+        const int e = it.y + gl + a * LANES;
+        const bool in = has && e < it.z;
+        uu[a] = in ? g.arcs[e].x : v;
+        higher[a] = in && higher_arc(st, e);
+    }
+    int res[kA], ob[kA], oe[kA];
+#pragma unroll
+    for (int a = 0; a < kA; ++a) {
+        ob[a] = oe[a] = 0;
+        if (uu[a] == v) res[a] = 0;
+        else if (higher[a]) res[a] = __ldcg(&st.color[uu[a]]);
+        else {
+            res[a] = atomicSub(&st.cnt[uu[a]], 1);
+            ob[a] = g.off[uu[a]];
+            oe[a] = g.off[uu[a] + 1];
+        }
+    }
+    unsigned long long mask = 0ull;
+#pragma unroll
+    for (int a = 0; a < kA; ++a) {
+        if (uu[a] != v && higher[a] && res[a] < 64) mask |= 1ull << res[a];
+        push_ready(st, cnt_next, nxt_list, uu[a] != v && !higher[a] && res[a] == 1, uu[a], ob[a],
+                   oe[a]);
+    }
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
+    const int mex = __ffsll((long long)~mask) - 1;
+    if (has && gl == 0) __stcg(&st.color[v], mex);
+    const int top = __reduce_max_sync(0xffffffffu, (has && gl == 0) ? mex : -1);
+    if (lane == 0 && top >= 0) atomicMax(st.max_color, top);
+}
+
+// d(v) = neighbours of v other than v itself (rows are sorted, so the
+// self-loop is found by bisection)
+__global__ void nbdeg_kernel(DGraph g, int32_t *d) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += gridDim.x * blockDim.x) {
+        int lo = g.off[v], hi = g.off[v + 1];
+        const int len = hi - lo;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (g.arcs[mid].x < v) lo = mid + 1; else hi = mid;
+        }
+        d[v] = len - (lo < g.off[v + 1] && g.arcs[lo].x == v ? 1 : 0);
+    }
+}
+
+// Priority pi(v) = (d(v), h(v ^ seed), v) compared lexicographically (R11;
+// d = nullptr leaves the degree out).  One warp per vertex: the bit of every
+// arc whose neighbour has the higher priority (hb, cleared before), the
+// count of such neighbours, and the vertices that have none are queued for
+// round 0.
+__global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long long seed,
+                                                      const int32_t *__restrict__ d, unsigned *hb,
+                                                      JpState st) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t vv = blockIdx.x * 8 + (threadIdx.x >> 5); vv < g.n; vv += nw) {
         const int v = (int)vv;
         const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
+        const int dv = d ? d[v] : 0;
         const int beg = g.off[v], end = g.off[v + 1];
         int c = 0;
-        for (int e = beg + lane; e < end; e += 32) {
-            const int u = g.arcs[e].x;
-            if (u != v && prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v)) ++c;
+        for (int e0 = beg; e0 < end; e0 += 32) {
+            const int e = e0 + lane;
+            bool hi = false;
+            if (e < end) {
+                const int u = g.arcs[e].x;
+                if (u != v) {
+                    const int du = d ? d[u] : 0;
+                    hi = du > dv ||
+                         (du == dv &&
+                          prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v));
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hi);
+            c += __popc(m);
+            if (lane == 0 && m) {  // the 32 arcs from e0 span two words at most
+                const int sh = e0 & 31;
+                atomicOr(&hb[e0 >> 5], m << sh);
+                if (sh && (m >> (32 - sh))) atomicOr(&hb[(e0 >> 5) + 1], m >> (32 - sh));
+            }
         }
-        c = warp_sum(c);
         if (lane == 0) {
             st.cnt[v] = c;
             st.color[v] = -1;
@@ -188,35 +287,37 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
 // A grid barrier ends the round; the vertices released in round r are
 // coloured in round r + 1, after the colours they depend on have been
 // written.
-__global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsigned long long seed,
-                                                                 JpState st) {
+__global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpState st) {
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
     __shared__ int s_last_part;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned bar_passed = 0;
     int n_small = __ldcg(&st.counts[0]), n_big = __ldcg(&st.counts[1]),
-        n_huge = __ldcg(&st.counts[2]);
+        n_huge = __ldcg(&st.counts[2]), n_tiny = __ldcg(&st.counts[3]);
     for (int r = 0;; ++r) {
         const int nxt = (r + 1) % 3, clr = (r + 2) % 3;
-        if (blockIdx.x == 0 && threadIdx.x < 3) st.counts[3 * clr + threadIdx.x] = 0;
+        if (blockIdx.x == 0 && threadIdx.x < kJpKinds) st.counts[kJpKinds * clr + threadIdx.x] = 0;
         const int in_list = r & 1, out_list = (r + 1) & 1;
-        int32_t *cnt_next = st.counts + 3 * nxt;
+        int32_t *cnt_next = st.counts + kJpKinds * nxt;
         const unsigned long long tr0 = LV_TRACE_ON ? gtimer() : 0;
         const int small_units = (n_small + kJpWarps - 1) / kJpWarps;
-        const int P = n_huge > 0 ? max(1, ((int)gridDim.x - n_big - small_units) / n_huge) : 0;
+        constexpr int tiny_per_unit = kJpWarps * kJpTinyPerWarp;
+        const int tiny_units = (n_tiny + tiny_per_unit - 1) / tiny_per_unit;
+        const int P = n_huge > 0
+                          ? max(1, ((int)gridDim.x - n_big - small_units - tiny_units) / n_huge)
+                          : 0;
         const int huge_units = n_huge * P;
-        const int units = huge_units + n_big + small_units;
+        const int units = huge_units + n_big + small_units + tiny_units;
         for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
             if (unit < huge_units) {
                 const int t = unit % n_huge, part = unit / n_huge;
                 const int4 it = __ldcg(&st.list[2][in_list][t]);
                 const int v = it.x;
-                const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
                 const int L = (it.z - it.y + P - 1) / P;
                 const int e0 = it.y + part * L, e1 = min(it.z, e0 + L);
                 unsigned *gbm = st.huge_bm + (size_t)t * 32;
-                jp_pass<4>(g, seed, st, v, hv, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
+                jp_pass<4>(g, st, v, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
                 __threadfence();
                 __syncthreads();
                 if (threadIdx.x == 0) s_last_part = atomicAdd(&st.huge_done[t], 1) == P - 1;
@@ -225,7 +326,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
                     __threadfence();
                     const unsigned w0 = __ldcg(&gbm[lane]);
                     __stcg(&gbm[lane], 0u);
-                    const int mex = warp_mex(g, seed, st, v, hv, w0, bm_warp[0]);
+                    const int mex = warp_mex(g, st, v, w0, bm_warp[0]);
                     if (lane == 0) {
                         set_color(st, v, mex);
                         st.huge_done[t] = 0;
@@ -235,30 +336,33 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
             } else if (unit < huge_units + n_big) {
                 const int4 it = __ldcg(&st.list[1][in_list][unit - huge_units]);
                 const int v = it.x;
-                const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
                 if (threadIdx.x < 32) bm_cta[threadIdx.x] = 0u;
                 __syncthreads();
-                jp_pass<4>(g, seed, st, v, hv, it.y, it.z, wib, kJpWarps, bm_cta, cnt_next, out_list);
+                jp_pass<4>(g, st, v, it.y, it.z, wib, kJpWarps, bm_cta, cnt_next, out_list);
                 __syncthreads();
                 if (wib == 0) {
-                    const int mex = warp_mex(g, seed, st, v, hv, bm_cta[lane], bm_warp[0]);
+                    const int mex = warp_mex(g, st, v, bm_cta[lane], bm_warp[0]);
                     if (lane == 0) set_color(st, v, mex);
                 }
                 __syncthreads();
+            } else if (unit >= huge_units + n_big + small_units) {
+                const int u0 = (unit - huge_units - n_big - small_units) * tiny_per_unit;
+                jp_tiny_warp<kJpTinyLanes>(g, st, st.list[3][in_list],
+                                           u0 + wib * kJpTinyPerWarp + lane / kJpTinyLanes,
+                                           n_tiny, cnt_next, out_list);
             } else {
                 const int t = (unit - huge_units - n_big) * kJpWarps + wib;
                 if (t < n_small) {
                     const int4 it = __ldcg(&st.list[0][in_list][t]);
                     const int v = it.x;
-                    const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
                     unsigned *bm = bm_warp[wib];
                     bm[lane] = 0u;
                     __syncwarp();
-                    jp_pass<kJpSmallU>(g, seed, st, v, hv, it.y, it.z, 0, 1, bm, cnt_next, out_list);
+                    jp_pass<kJpSmallU>(g, st, v, it.y, it.z, 0, 1, bm, cnt_next, out_list);
                     __syncwarp();
                     const unsigned w0 = bm[lane];
                     __syncwarp();
-                    const int mex = warp_mex(g, seed, st, v, hv, w0, bm);
+                    const int mex = warp_mex(g, st, v, w0, bm);
                     if (lane == 0) set_color(st, v, mex);
                     __syncwarp();
                 }
@@ -270,11 +374,13 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, unsig
         if (!grid_sync(st.bar, bar_passed)) return;
         if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
             trace4(st.tb, 0x200000000ull | (unsigned)r,
-                   ((unsigned long long)n_small << 32) | (unsigned)(n_big + n_huge), gtimer(), 0);
+                   ((unsigned long long)(n_small + n_tiny) << 32) | (unsigned)(n_big + n_huge),
+                   gtimer(), 0);
         n_small = __ldcg(&cnt_next[0]);
         n_big = __ldcg(&cnt_next[1]);
         n_huge = __ldcg(&cnt_next[2]);
-        if (n_small + n_big + n_huge == 0) {
+        n_tiny = __ldcg(&cnt_next[3]);
+        if (n_small + n_big + n_huge + n_tiny == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *st.rounds = r + 1;
             return;
         }
@@ -345,29 +451,43 @@ __global__ void gather_at_kernel(const int32_t *__restrict__ vals, const int32_t
 
 }  // namespace
 
-lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_colors,
-                   int32_t *rounds, int *pinned, cudaStream_t s) {
+lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *color,
+                   int32_t *num_colors, int32_t *rounds, int *pinned, cudaStream_t s) {
     const int n = g.n;
     JpState st;
     st.color = color;
     st.tb = trace_buffer();
+    // higher-priority bit of every arc, and the degrees of the priority
+    const size_t words = (size_t)g.A / 32 + 2;
+    unsigned *hb = nullptr;
+    int32_t *d = nullptr;
+    LV_TRY(dalloc_n(&hb, words, s));
+    LV_CUDA(cudaMemsetAsync(hb, 0, sizeof(unsigned) * words, s));
+    if (degree_first) {
+        LV_TRY(dalloc_n(&d, (size_t)n, s));
+        nbdeg_kernel<<<grid_for(n, 256, g_num_sms * 16), 256, 0, s>>>(g, d);
+        LV_LAUNCH_CHECK();
+    }
+    st.hb = hb;
     LV_TRY(dalloc_n(&st.cnt, (size_t)n, s));
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < kJpKinds; ++k)
         for (int p = 0; p < 2; ++p) LV_TRY(dalloc_n(&st.list[k][p], (size_t)n, s));
     const size_t max_huge = (size_t)g.A / kJpHuge + 1;  // each has >= kJpHuge arcs
     LV_TRY(dalloc_n(&st.huge_bm, 32 * max_huge, s));
     LV_CUDA(cudaMemsetAsync(st.huge_bm, 0, sizeof(unsigned) * 32 * max_huge, s));
     LV_TRY(dalloc_n(&st.huge_done, max_huge, s));
     LV_CUDA(cudaMemsetAsync(st.huge_done, 0, sizeof(int32_t) * max_huge, s));
-    // counts[9], max_color, barrier (2 words, 8-byte aligned), rounds
+    // counts[3 * kJpKinds = 12], max_color, barrier (2 words at byte 56,
+    // 8-byte aligned), rounds
+    static_assert(3 * kJpKinds == 12, "state layout");
     int32_t *small_state = nullptr;
-    LV_TRY(dalloc_n(&small_state, 16, s));
-    LV_CUDA(cudaMemsetAsync(small_state, 0, 16 * sizeof(int32_t), s));
+    LV_TRY(dalloc_n(&small_state, 20, s));
+    LV_CUDA(cudaMemsetAsync(small_state, 0, 20 * sizeof(int32_t), s));
     st.counts = small_state;
-    st.max_color = small_state + 9;
-    st.bar = reinterpret_cast<GridBarrier *>(small_state + 10);
-    st.rounds = small_state + 12;
-    jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, st);
+    st.max_color = small_state + 13;
+    st.bar = reinterpret_cast<GridBarrier *>(small_state + 14);
+    st.rounds = small_state + 16;
+    jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, d, hb, st);
     LV_LAUNCH_CHECK();
     static int blocks_per_sm = 0;
     if (!blocks_per_sm) {
@@ -375,14 +495,14 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
                                                               kJpBlock, 0));
         if (blocks_per_sm < 1) return LV_ERR_CUDA;
     }
-    unsigned long long seed_arg = seed;
     DGraph garg = g;
-    void *args[] = {&garg, &seed_arg, &st};
+    void *args[] = {&garg, &st};
     // one block per SM: a second one per SM only adds barrier arrivals
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms),
                                         dim3(kJpBlock), args, 0, s));
     LV_LAUNCH_CHECK();
-    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 9, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaMemcpyAsync(pinned, small_state + 13, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            s));
     LV_CUDA(cudaStreamSynchronize(s));
     GridBarrier bar;
     std::memcpy(&bar, pinned + 1, sizeof bar);
@@ -391,11 +511,13 @@ lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_
     *num_colors = pinned[0] + 1;
     *rounds = pinned[3];
     dfree(st.cnt, s);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < kJpKinds; ++k)
         for (int p = 0; p < 2; ++p) dfree(st.list[k][p], s);
     dfree(st.huge_bm, s);
     dfree(st.huge_done, s);
     dfree(small_state, s);
+    dfree(hb, s);
+    dfree(d, s);
     return LV_OK;
 }
 

@@ -319,6 +319,45 @@ __global__ void iota_kernel(int32_t n, int32_t *out) {
         out[v] = v;
 }
 
+// ------------------------------------------- recursive single-neighbour VF
+// Target of each vertex in one round of the recursive merge: a vertex with
+// exactly one neighbour j != i (row of one arc, or two arcs one of which is
+// its self-loop l) passes when k_i^2 > 2m l with k_i = w(i,j) + l -- the
+// bound of Lemma 3's Eq. (eqnClaimIItemp) taken at a_C(j) = 2m - k_i, exact
+// in 64-bit integers (k_i <= 2m < 2^31).  Otherwise the target is -1.
+__global__ void sn_target_kernel(DGraph g, long long two_m, int32_t *target) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += gridDim.x * blockDim.x) {
+        const int b = g.off[i], len = g.off[i + 1] - b;
+        int t = -1;
+        if (len == 1 || len == 2) {
+            const int2 a0 = g.arcs[b];
+            const int2 a1 = len == 2 ? g.arcs[b + 1] : make_int2(i, 0);
+            // rows hold no duplicates: a row of two arcs is single-neighbour
+            // only when one of them is the self-loop
+            const bool one = len == 1 ? a0.x != i : (a0.x == i) != (a1.x == i);
+            if (one) {
+                const int2 nb = a0.x != i ? a0 : a1;
+                const long long l = a0.x == i ? a0.y : (len == 2 && a1.x == i ? a1.y : 0);
+                const long long k = (long long)nb.y + l;
+                if (k * k > two_m * l) t = nb.x;
+            }
+        }
+        target[i] = t;
+    }
+}
+
+// C[i] = the vertex i merges into (itself if it stays); of two vertices
+// passing towards each other the smaller merges (R3); keep[i] = survivor
+__global__ void sn_resolve_kernel(int n, const int32_t *__restrict__ target, int32_t *C,
+                                  int32_t *keep) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = target[i];
+        const bool merge = t >= 0 && !(target[t] == i && t < i);
+        C[i] = merge ? t : i;
+        keep[i] = merge ? 0 : 1;
+    }
+}
+
 }  // namespace
 
 static int grid_rows(int64_t rows) { return grid_for(rows, 8, g_num_sms * 16); }
@@ -495,6 +534,44 @@ lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, in
     dfree(rowlen, s);
     *out = h;
     return LV_OK;
+}
+
+lv_status vf_recursive(DGraph *G, int64_t two_m, int32_t *map, int32_t n_orig, int *pinned,
+                       int32_t *rounds, cudaStream_t s) {
+    *rounds = 0;
+    for (;;) {
+        const int n = G->n;
+        int32_t *target = nullptr, *C = nullptr, *newid = nullptr, *scratch = nullptr;
+        LV_TRY(dalloc_n(&target, (size_t)n, s));
+        LV_TRY(dalloc_n(&C, (size_t)n, s));
+        LV_TRY(dalloc_n(&newid, (size_t)n + 1, s));
+        sn_target_kernel<<<grid_items(n), 256, 0, s>>>(*G, (long long)two_m, target);
+        LV_LAUNCH_CHECK();
+        sn_resolve_kernel<<<grid_items(n), 256, 0, s>>>(n, target, C, newid);
+        LV_LAUNCH_CHECK();
+        LV_TRY(scan_excl_i32(newid, newid, n, s));
+        LV_CUDA(cudaMemcpyAsync(pinned, newid + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        const int32_t n_next = pinned[0];
+        lv_status st = LV_OK;
+        if (n_next < n) {
+            DGraph H;
+            st = coarsen(*G, C, newid, n_next, &H, pinned, s);
+            if (st == LV_OK) st = dalloc_n(&scratch, (size_t)n_orig, s);
+            if (st == LV_OK) st = compose_labels(n_orig, map, C, newid, scratch, s);
+            if (st == LV_OK) {
+                free_graph(*G, s);
+                *G = H;
+                ++*rounds;
+            }
+        }
+        dfree(target, s);
+        dfree(C, s);
+        dfree(newid, s);
+        dfree(scratch, s);
+        if (st != LV_OK) return st;
+        if (n_next == n) return LV_OK;
+    }
 }
 
 void free_graph(DGraph &g, cudaStream_t s) {

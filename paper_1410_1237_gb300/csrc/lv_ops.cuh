@@ -22,11 +22,19 @@ lv_status iota(int32_t n, int32_t *out, cudaStream_t s);
 lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, int32_t *map,
                            int *scratch_pinned, cudaStream_t s);
 void free_graph(DGraph &g, cudaStream_t s);
+// Recursive single-neighbour merge after vertex following (R23, the closing
+// paragraph of Sec. 4.3): rounds that merge every single-neighbour vertex
+// passing Lemma 3's bound (k_i^2 > 2m l_i) into its neighbour, until none
+// passes.  Replaces *G (owned) by the merged graph and composes map
+// (n_orig entries); *rounds = merging rounds.
+lv_status vf_recursive(DGraph *G, int64_t two_m, int32_t *map, int32_t n_orig, int *pinned,
+                       int32_t *rounds, cudaStream_t s);
 
 // lv_color.cu ------------------------------------------------------------
-// Jones-Plassmann distance-1 colouring with priority (h(v ^ seed), v).
-lv_status jp_color(const DGraph &g, uint64_t seed, int32_t *color, int32_t *num_colors,
-                   int32_t *rounds, int *scratch_pinned, cudaStream_t s);
+// Jones-Plassmann distance-1 colouring with priority (d(v), h(v ^ seed), v),
+// d(v) = neighbours other than v (degree_first), else (h(v ^ seed), v).
+lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *color,
+                   int32_t *num_colors, int32_t *rounds, int *scratch_pinned, cudaStream_t s);
 
 // Vertex order of a phase: vertices grouped by (colour class, degree bin),
 // ascending id inside a group.  order[n], bucket_off[(classes*(kBins+1))+1]

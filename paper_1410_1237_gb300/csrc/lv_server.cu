@@ -415,10 +415,12 @@ void complete_locked(lv_server *S, Request &r, double t) {
     else ++S->stats.failed;
 }
 
-// lane 1 takes large requests and those that would colour a phase
+// lane 1 takes large requests, those that would colour a phase, and every
+// request when recursive vertex following is on (single-graph runs only)
 bool plain_lane(const lv_server *S, const Request &r) {
     return (int64_t)r.col.size() >= kLaneSplitArcs ||
-           (S->cfg.params.coloring && r.n >= S->cfg.params.color_cutoff);
+           (S->cfg.params.coloring && r.n >= S->cfg.params.color_cutoff) ||
+           S->cfg.params.vf_recursive;
 }
 
 // Lane 1: one request at a time through the single-graph entry points.

@@ -42,7 +42,8 @@ class lv_params(ctypes.Structure):
                 ("bin_lane_arcs", ctypes.c_int32), ("bin_warp_max", ctypes.c_int32),
                 ("bin_cta_max", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("graph_capture", ctypes.c_int32), ("color_phases", ctypes.c_int32),
-                ("abs_threshold", ctypes.c_int32)]
+                ("abs_threshold", ctypes.c_int32), ("vf_recursive", ctypes.c_int32),
+                ("color_order", ctypes.c_int32)]
 
 
 class lv_phase_info(ctypes.Structure):

@@ -303,3 +303,51 @@ def test_validation_codes_match_oracle(lv):
             got = err.code
         assert got == want, name
         assert (want == 0) == name.endswith("valid"), name
+
+
+# ------------------------------------- recursive single-neighbour VF (R23)
+def _recursive_vf_graphs():
+    from test_oracle_pins import _pendant_graph
+    out = [gg.from_edges(3, [(0, 0, 100), (0, 1, 50), (1, 2, 1)]),
+           gg.from_edges(4, [(0, 1, 8), (1, 2, 8), (2, 3, 1)]),
+           gg.from_edges(6, [(0, 2), (2, 3), (0, 3), (3, 4), (2, 4), (1, 5, 50), (1, 1, 3),
+                             (5, 5, 3)])]
+    out += [_pendant_graph(s)[0] for s in range(6)]
+    return out
+
+
+@pytest.mark.parametrize("idx", range(9))
+def test_variant_recursive_vf_merging_graphs(lv, idx):
+    g = _recursive_vf_graphs()[idx]
+    compare(lv, g, vertex_following=1, vf_recursive=1, coloring=0)
+
+
+@pytest.mark.parametrize("wl", ["planted1k", "rmat16"])
+def test_variant_recursive_vf_workloads(lv, wl):
+    g, prm = gg.workload(wl)
+    compare(lv, g, graphs=False, vf_recursive=1, **prm)
+
+
+def test_recursive_vf_random_looped(lv):
+    # a looped random graph with heavy pendant edges: several vertices merge
+    rng = np.random.default_rng(9)
+    edges = [(i, (i + 1) % 40, 1) for i in range(40)]
+    for t in range(30):
+        edges.append((40 + t, int(rng.integers(0, 40)), int(rng.integers(1, 60))))
+        edges.append((40 + t, 40 + t, int(rng.integers(1, 4))))
+    g = gg.from_edges(70, edges)
+    ref = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, vf_recursive=1, coloring=0)
+    assert ref.vf_n < 70
+    compare(lv, g, vertex_following=1, vf_recursive=1, coloring=0)
+
+
+def test_recursive_vf_is_single_graph_only(lv):
+    g = gg.from_edges(3, [(0, 1), (1, 2)])
+    gptr = np.array([0, 3], dtype=np.int64)
+    h = lv.lv_batch_create(1, gptr, g.rowptr, g.col, g.w)
+    try:
+        with pytest.raises(lv.LVError) as e:
+            lv.lv_batch_run(h, lv.make_params(vf_recursive=1))
+        assert e.value.code == -1
+    finally:
+        lv.lv_batch_destroy(h)

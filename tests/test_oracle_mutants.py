@@ -33,6 +33,11 @@ MUTANTS = {
     # colouring in increasing instead of decreasing priority (R11)
     "colouring order": ("if (x->h != y->h) return x->h < y->h ? 1 : -1;",
                         "if (x->h != y->h) return x->h < y->h ? -1 : 1;"),
+    # smallest degree first instead of largest (R11)
+    "colouring degree order": ("if (x->d != y->d) return x->d < y->d ? 1 : -1;",
+                               "if (x->d != y->d) return x->d < y->d ? -1 : 1;"),
+    # the colouring degree counting the self-loop as a neighbour (R11)
+    "colouring degree with loop": ("d += g->col[e] != v;", "d += 1;"),
     # a move on a zero gain
     "zero-gain move": ("if (bestG > 0) {", "if (bestG >= 0 && best != ci) {"),
     # the self-loop left out of e_in (R1)
@@ -54,6 +59,11 @@ MUTANTS = {
     "absolute stop test": ("    if (abs_mode) d = abs64(d);", "    d = abs64(d);"),
     # vertex following removing the larger end of an isolated edge (R3)
     "VF keeps the smaller end": ("if (deg1[j] && j < i) continue;", "if (deg1[j] && j > i) continue;"),
+    # recursive VF testing the bound without the self-loop in k_i (R23)
+    "recursive VF loop out of k": ("const int64_t k = wij + loop;", "const int64_t k = wij;"),
+    # recursive VF keeping the smaller of a facing pair (R3 applied to R23)
+    "recursive VF pair rule": ("!(target[j] == (int32_t)i && j < i)",
+                               "!(target[j] == (int32_t)i && j > i)"),
     # coloured phases using the fine threshold and uncoloured ones the coarse (R12)
     "thresholds swapped": ("? prm->theta_high\n", "? prm->theta_low + 0.0 * prm->theta_high\n"),
     # the comparison of Sec. 5 counting pairs together only in p as FN and

@@ -309,15 +309,19 @@ def test_bruteforce_upper_bound(seed):
 
 
 # ------------------------------------------------------------- invariants
-def _independent_greedy_colouring(g, seed):
-    # Plain restatement in Python: decreasing (h(v^seed), v), smallest free colour.
+def _independent_greedy_colouring(g, seed, order=0):
+    # Plain restatement in Python: decreasing (neighbours other than v,
+    # h(v^seed), v) -- or (h(v^seed), v) for order 1 -- smallest free colour.
     M = (1 << 64) - 1
 
     def h(x):
         x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M
         x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M
         return x ^ (x >> 31)
-    order = sorted(range(g.n), key=lambda v: (h(v ^ seed), v), reverse=True)
+
+    def d(v):
+        return 0 if order == 1 else sum(1 for u in g.col[g.rowptr[v]:g.rowptr[v + 1]] if u != v)
+    order = sorted(range(g.n), key=lambda v: (d(v), h(v ^ seed), v), reverse=True)
     col = [-1] * g.n
     for v in order:
         used = {col[u] for u in g.col[g.rowptr[v]:g.rowptr[v + 1]] if u != v and col[u] >= 0}
@@ -329,10 +333,11 @@ def _independent_greedy_colouring(g, seed):
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_colouring_matches_independent_greedy(seed):
+@pytest.mark.parametrize("order", [0, 1])
+def test_colouring_matches_independent_greedy(seed, order):
     g = gg.rmat(9, 8, seed=seed)
-    K, c = oracle.color(g.rowptr, g.col, 77 + seed)
-    ref = _independent_greedy_colouring(g, 77 + seed)
+    K, c = oracle.color(g.rowptr, g.col, 77 + seed, order)
+    ref = _independent_greedy_colouring(g, 77 + seed, order)
     assert list(c) == ref and K == max(ref) + 1
     src = np.repeat(np.arange(g.n), np.diff(g.rowptr))
     off = src != g.col
@@ -627,3 +632,117 @@ def test_sweep_sample_is_the_first_iteration():
     assert mv == r.iters[0][2] and vis == g.arcs and sec >= 0.0
     mv2, vis2, _ = oracle.sweep_sample(g.rowptr, g.col, g.w, 100, 50)
     assert vis2 == int(g.rowptr[150] - g.rowptr[100]) and 0 <= mv2 <= 50
+
+
+# ------------------------- Sec. 4.3 closing paragraph: recursive VF (R23)
+def test_recursive_vf_fixtures():
+    """Hand-derived merges of the recursive single-neighbour rounds.
+
+    Looped pair: edges (0,0,100), (0,1,50), (1,2,1), 2m = 202.  Plain VF
+    removes vertex 2 into 1 (loop 2).  Then vertex 0 (loop 100, w 50, k 150)
+    passes k^2 = 22500 > 2m l = 20200, and vertex 1 (loop 2, w 50, k 52)
+    passes 2704 > 404: two single-neighbour vertices facing each other, so
+    the smaller (0) merges into 1 and one vertex is left.
+
+    Weighted path (0,1,8), (1,2,8), (2,3,1), 2m = 34: plain VF removes 0
+    into 1 (loop 16) and 3 into 2 (loop 2); then 1 (k 24: 576 > 544) and 2
+    (k 10: 100 > 68) pass towards each other and 1 merges into 2.
+
+    Unweighted path of 6 vertices: after plain VF the ends carry loop 2 with
+    w 1 (k 3: 9 > 2m l = 20 fails), so nothing more merges."""
+    g = gg.from_edges(3, [(0, 0, 100), (0, 1, 50), (1, 2, 1)])
+    a = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0)
+    b = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1)
+    assert a.vf_n == 2 and list(a.vf_map) == [0, 1, 1]
+    assert b.vf_n == 1 and list(b.vf_map) == [0, 0, 0]
+    g = gg.from_edges(4, [(0, 1, 8), (1, 2, 8), (2, 3, 1)])
+    b = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1,
+                   trace=1)
+    assert b.vf_n == 1 and list(b.vf_map) == [0, 0, 0, 0]
+    rp, col, w = b.phases[0].graph
+    assert list(rp) == [0, 1] and list(col) == [0] and list(w) == [34]
+    g = gg.from_edges(6, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5)])
+    a = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0)
+    b = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1)
+    assert b.vf_n == a.vf_n == 4 and list(b.vf_map) == list(a.vf_map)
+    # a looped pair 1-5 (w 50, loops 3) beside a 0-2-3-4 block, 2m = 116:
+    # both pass (53^2 = 2809 > 348), so 1 merges into 5 (R3) and the
+    # survivors 0, 2, 3, 4, 5 become 0..4
+    g = gg.from_edges(6, [(0, 2), (2, 3), (0, 3), (3, 4), (2, 4), (1, 5, 50), (1, 1, 3),
+                          (5, 5, 3)])
+    b = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1)
+    assert list(b.vf_map) == [0, 4, 1, 2, 3, 4]
+
+
+def _pendant_graph(seed):
+    """A core where every vertex keeps >= 2 core neighbours, plus looped
+    pendants (one core neighbour each), so plain VF merges nothing and the
+    first recursive round decides every pendant on its own."""
+    rng = np.random.default_rng(seed)
+    nc, npd = 8, 5
+    edges = [(i, (i + 1) % nc, int(rng.integers(1, 6))) for i in range(nc)]
+    for i in range(nc):
+        for j in range(i + 2, nc):
+            if rng.random() < 0.3 and not (i == 0 and j == nc - 1):
+                edges.append((i, j, int(rng.integers(1, 6))))
+    pend = []
+    for t in range(npd):
+        p, j = nc + t, int(rng.integers(0, nc))
+        edges.append((p, j, int(rng.integers(1, 31))))
+        edges.append((p, p, int(rng.integers(1, 7))))
+        pend.append((p, j))
+    return gg.from_edges(nc + npd, edges), pend
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_recursive_vf_is_lemma3_guarantee(seed):
+    """A pendant merges iff Lemma 3's guarantee holds for it: when merged,
+    its exact gain (Eq. 4) towards C(j) is positive for random partitions
+    with it alone; when kept, the partition {i} | everything else (where
+    a_C(j) = 2m - k_i, the bound's worst case) gives a gain <= 0."""
+    g, pend = _pendant_graph(seed)
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1,
+                   max_phases=1, max_iters=1)
+    rng = np.random.default_rng(100 + seed)
+    n = g.n
+    for p, j in pend:
+        merged = r.vf_map[p] == r.vf_map[j]
+        if merged:
+            for _ in range(30):
+                lab = rng.integers(0, 4, size=n).astype(np.int32)
+                lab[p] = 4  # alone
+                assert oracle.gain(g.rowptr, g.col, g.w, lab, p, int(lab[j])) > 0
+        else:
+            lab = np.zeros(n, dtype=np.int32)
+            lab[p] = 1
+            assert oracle.gain(g.rowptr, g.col, g.w, lab, p, 0) <= 0
+
+
+def test_recursive_vf_cases_cover_both_outcomes():
+    """The seeds above include pendants that merge and pendants that stay."""
+    seen = 0
+    for seed in range(12):
+        g, pend = _pendant_graph(seed)
+        r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1,
+                       max_phases=1, max_iters=1)
+        for p, j in pend:
+            seen |= 1 if r.vf_map[p] == r.vf_map[j] else 2
+    assert seen == 3
+
+
+@pytest.mark.parametrize("make", [lambda: _pendant_graph(3)[0],
+                                  lambda: gg.random_graph(200, 0.02, wmax=9, loops=0.3, seed=8),
+                                  lambda: gg.from_edges(4, [(0, 1, 8), (1, 2, 8), (2, 3, 1)])])
+def test_recursive_vf_is_an_exact_coarsening(make):
+    """Like plain VF (R1, R2): Q of any partition of the merged graph equals
+    Q of the expanded partition on the input graph."""
+    g = make()
+    r = oracle.run(g.rowptr, g.col, g.w, vertex_following=1, coloring=0, vf_recursive=1,
+                   trace=1, max_phases=1, max_iters=1)
+    rp, col, w = r.phases[0].graph
+    rng = np.random.default_rng(1)
+    for _ in range(10):
+        lab = rng.integers(0, max(1, (len(rp) - 1) // 2), size=len(rp) - 1).astype(np.int32)
+        N1, t1 = oracle.modularity_num(rp, col, w, lab)
+        N0, t0 = oracle.modularity_num(g.rowptr, g.col, g.w, lab[r.vf_map])
+        assert (N1, t1) == (N0, t0)

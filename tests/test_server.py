@@ -200,3 +200,21 @@ def test_all_heuristics_with_colouring(lv):
             check(lv, h, rid, g, w)
     finally:
         lv.lv_server_destroy(h)
+
+
+def test_recursive_vf_requests_take_the_single_graph_lane(lv):
+    """With recursive vertex following on, every request is solved by the
+    single-graph driver (second lane) and equals lv_run alone."""
+    prm = dict(vertex_following=1, coloring=0, vf_recursive=1)
+    graphs = [gg.from_edges(3, [(0, 0, 100), (0, 1, 50), (1, 2, 1)]),
+              gg.from_edges(4, [(0, 1, 8), (1, 2, 8), (2, 3, 1)])] + request_mix(5, 6)
+    want = [alone(lv, g, **prm) for g in graphs]
+    h = lv.lv_server_create(**prm)
+    try:
+        ids = [lv.lv_server_submit(h, g.rowptr, g.col, g.w) for g in graphs]
+        for rid in ids:
+            assert lv.lv_server_wait(h, rid, 120.0)
+        for rid, g, w in zip(ids, graphs, want):
+            check(lv, h, rid, g, w)
+    finally:
+        lv.lv_server_destroy(h)
