@@ -46,7 +46,22 @@ SWEEP_SOURCES = ("lv_sweep.cu", "lv_ops.cuh", "lv_internal.cuh", "lv_engine.cuh"
 # the dominant kernel, from ncu captures.  Each entry records the digest of
 # the sweep kernel's sources at capture time; when the sources change the
 # entry no longer applies and the line reports traffic as null.
-MEASURED_TRAFFIC: dict = {}
+MEASURED_TRAFFIC: dict = {
+    # sweep_persistent_kernel on chunglu20 (2^20-vertex member of the Chung-Lu
+    # family), phase-0 iteration 2: 354,168,064 + 36,743,936 B against
+    # 369,528,704 algorithmic (12 x 29,082,750 arcs + 28 x 733,418 vertices);
+    # applied to a phase-0 launch of the 2^24-vertex graph by that ratio
+    "chunglu24": {"sources": "996b16eaa8776618", "ratio": 390_912_000 / 369_528_704,
+                  "scope": "one phase-0 sweep launch, scaled by units from a capture of a "
+                           "2^20-vertex Chung-Lu phase-0 launch (ratio 1.058)"},
+    # the batched sweep on 512 planted graphs, phase-0 sweep 7 (324 graphs
+    # iterating): 265,677,568 + 16,336,128 B against 230,483,328 algorithmic
+    # (12 x 16,401,407 arcs + 28 x 1,202,373 vertices)
+    "planted_batch4096": {"sources": "996b16eaa8776618",
+                          "ratio": 282_013_696 / 230_483_328,
+                          "scope": "one phase-0 sweep launch of all 4,096 graphs, scaled by "
+                                   "units from a 512-graph capture (ratio 1.22)"},
+}
 # bounded oracle samples (host-core baseline): the oracle's whole pipeline
 # on the same graph, cut after these many phases / iterations
 CPU_SAMPLE = {"rmat20": dict(max_phases=1, max_iters=3),
@@ -819,6 +834,10 @@ def main():
         del hp, out
 
     tr = traffic_entry(args.workload)
+    alg0 = BYTES_PER_ARC * infos[0].arcs + BYTES_PER_VERTEX * infos[0].n if infos else 0
+    traffic = None
+    if tr:
+        traffic = tr["bytes"] if "bytes" in tr else tr["ratio"] * alg0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -838,9 +857,10 @@ def main():
         "edge_visits_per_s_sweep": (sweep_arcs / (sweep_ms / 1e3)) if sweep_ms > 0 else None,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": tr["bytes"] if tr else None,
+                     "traffic": traffic,
                      "traffic_scope": tr["scope"] if tr else
                      "null: no ncu capture of the current sweep sources",
+                     "algorithmic_bytes_phase0_launch": alg0,
                      "kernel": "sweep_persistent_kernel (one launch per iteration, all colour "
                                "classes)",
                      "bytes_per_unit": f"{BYTES_PER_ARC} B/arc + {BYTES_PER_VERTEX} B/vertex",

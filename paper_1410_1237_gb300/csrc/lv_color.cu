@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
         if (!grid_sync(st.bar, bar_passed)) return;
         if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
             trace4(st.tb, 0x200000000ull | (unsigned)r,
-                   ((unsigned long long)(n_small + n_tiny) << 32) | (unsigned)(n_big + n_huge),
-                   gtimer(), 0);
+                   ((unsigned long long)n_small << 32) | (unsigned)n_tiny, gtimer(),
+                   ((unsigned long long)n_big << 32) | (unsigned)n_huge);
         n_small = __ldcg(&cnt_next[0]);
         n_big = __ldcg(&cnt_next[1]);
         n_huge = __ldcg(&cnt_next[2]);
