@@ -382,6 +382,8 @@ def measure_batch(lv, torch, dev, pg, world, local, steps, warmup, plain=True, e
     batch_labels = np.empty(b.n, dtype=np.int32)
     lv.lv_batch_get_labels(h, -1, -1, batch_labels)
     qs = [lv.lv_batch_get_graph_info(h, g).q for g in range(b.num_graphs)]
+    tuning = {r: t for r in range(st.num_phases)
+              if (t := lv.lv_batch_get_tuning(h, r)) is not None}
     lv.lv_batch_destroy(h)
     value = whole_job_rate(b.num_graphs * steps, world, total_ms / 1e3)
     peak, peak_src = measured_peak_gbs()
@@ -462,7 +464,8 @@ def measure_batch(lv, torch, dev, pg, world, local, steps, warmup, plain=True, e
                    "sweeps_from_cuda_graph": st.graph_launches,
                    "iterations_all_graphs": st.total_iterations,
                    "edge_visits_per_step": st.edge_visits,
-                   "q_min": min(qs), "q_median": statistics.median(qs)},
+                   "q_min": min(qs), "q_median": statistics.median(qs),
+                   "autotuned_sweep_shape_by_round": tuning},
         "edge_visits_per_s_sweep": (sweep_arcs / (sweep_ms / 1e3)) if sweep_ms > 0 else None,
         "plain_launches": plain_rec,
         "speedup_vs_plain": (value / world / plain_rec["value"]) if plain_rec else None,

@@ -103,6 +103,12 @@ typedef struct {
      * seeded hash, then by id (default: fewer colour classes, so fewer
      * class steps per iteration); 1 = the seeded hash alone, then id. */
     int32_t color_order;
+    /* Sweep launch shape (0 = default; results never depend on them; the
+     * autotuner may choose others for uncoloured phases): persistent sweep
+     * blocks per SM, 1 or 2 (default: as many as fit, 2), and hub hash-table
+     * slots per arc, 2, 4 or 8 (default 4 in coloured phases, 2 otherwise). */
+    int32_t sweep_blocks_per_sm;
+    int32_t hub_slots_per_arc;
 } lv_params;
 
 /* Per-phase record.  N values are exact modularity numerators: Q = N/(2m)^2. */
@@ -206,6 +212,13 @@ lv_status lv_get_iteration_stats(const lv_graph *g, lv_iter_stat *out, int64_t c
 
 /* Whole-run totals of the last run. */
 lv_status lv_get_stats(const lv_graph *g, lv_stats *out);
+
+/* The sweep configuration the autotuner chose for phase `phase` (runs with
+ * autotune = 1; kept in the handle across runs): out = int32[5] host array
+ * {lane_arcs, warp_max, cta_max, sweep blocks per SM (0 = as many as fit),
+ * hub table slots per arc (0 = the default: 4 coloured, 2 otherwise)}.
+ * LV_ERR_STATE when that phase was not tuned (coloured, or < 2^22 arcs). */
+lv_status lv_get_tuning(const lv_graph *g, int32_t phase, int32_t *out);
 
 /* Map of vertex following: int32[n] giving each original vertex's vertex in
  * the phase-0 graph (identity when vertex following is off). */
@@ -356,6 +369,11 @@ lv_status lv_batch_get_phase_info(const lv_batch *b, int32_t graph, int32_t phas
  * vf_n = vertices of the union after vertex following; sweep_launches =
  * batched sweeps; times (collect_timing) and kernel launches of the run. */
 lv_status lv_batch_get_stats(const lv_batch *b, lv_stats *out);
+
+/* The sweep configuration the autotuner chose for batched phase round
+ * `round` (autotune = 1; as lv_get_tuning).  LV_ERR_STATE when that round
+ * was not tuned. */
+lv_status lv_batch_get_tuning(const lv_batch *b, int32_t round, int32_t *out);
 
 /* Batched sweep records of the last run: count, then copy up to `count`. */
 lv_status lv_batch_get_num_sweeps(const lv_batch *b, int64_t *count);

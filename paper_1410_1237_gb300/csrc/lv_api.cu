@@ -335,8 +335,11 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     if (P.bin_lane_arcs) lim.lane_arcs = P.bin_lane_arcs;
     if (P.bin_warp_max) lim.warp_max = P.bin_warp_max;
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
+    lim.blocks_per_sm = P.sweep_blocks_per_sm;
+    lim.hub_factor = P.hub_slots_per_arc;
     if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
-        lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit)
+        lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit ||
+        !valid_shape(lim))
         return LV_ERR_ARG;
     if (P.max_iters < 1 || P.max_phases < 1 || !(P.theta_low >= -1e300) ||
         !(P.theta_high >= 0.0) || P.color_order < 0 || P.color_order > 1)
@@ -690,6 +693,18 @@ lv_status lv_get_stats(const lv_graph *g, lv_stats *out) {
     if (!g || !out) return LV_ERR_ARG;
     if (!g->have_run) return LV_ERR_STATE;
     *out = g->stats;
+    return LV_OK;
+}
+
+lv_status lv_get_tuning(const lv_graph *g, int32_t phase, int32_t *out) {
+    if (!g || !out) return LV_ERR_ARG;
+    if (phase < 0 || phase >= (int32_t)g->tuned.size() || !g->tuned_ok[phase]) return LV_ERR_STATE;
+    const BinLimits &t = g->tuned[phase];
+    out[0] = t.lane_arcs;
+    out[1] = t.warp_max;
+    out[2] = t.cta_max;
+    out[3] = t.blocks_per_sm;
+    out[4] = t.hub_factor;
     return LV_OK;
 }
 

@@ -228,8 +228,11 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
     if (P.bin_lane_arcs) lim.lane_arcs = P.bin_lane_arcs;
     if (P.bin_warp_max) lim.warp_max = P.bin_warp_max;
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
+    lim.blocks_per_sm = P.sweep_blocks_per_sm;
+    lim.hub_factor = P.hub_slots_per_arc;
     if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
-        lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit)
+        lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit ||
+        !valid_shape(lim))
         return LV_ERR_ARG;
     if (P.max_iters < 1 || P.max_phases < 1 || !(P.theta_low >= -1e300) ||
         !(P.theta_high >= 0.0))
@@ -424,6 +427,19 @@ lv_status lv_batch_get_stats(const lv_batch *b, lv_stats *out) {
     if (!b || !out) return LV_ERR_ARG;
     if (!b->have_run) return LV_ERR_STATE;
     *out = b->stats;
+    return LV_OK;
+}
+
+lv_status lv_batch_get_tuning(const lv_batch *b, int32_t round, int32_t *out) {
+    if (!b || !out) return LV_ERR_ARG;
+    if (round < 0 || round >= (int32_t)b->tuned.size() || !b->tuned_ok[round])
+        return LV_ERR_STATE;
+    const BinLimits &t = b->tuned[round];
+    out[0] = t.lane_arcs;
+    out[1] = t.warp_max;
+    out[2] = t.cta_max;
+    out[3] = t.blocks_per_sm;
+    out[4] = t.hub_factor;
     return LV_OK;
 }
 

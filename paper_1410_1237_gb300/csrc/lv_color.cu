@@ -62,10 +62,26 @@ __device__ __forceinline__ bool higher_arc(const JpState &st, int e) {
     return (__ldg(&st.hb[e >> 5]) >> (e & 31)) & 1u;
 }
 
+// Block-local staging of the next round's ready vertices: pushes reserve
+// room with shared-memory atomics, and the block appends each kind's staged
+// entries to the global list with one global atomic per kind when it
+// flushes (mid-round when a kind is half full, and before the round's
+// barrier).  A push that does not fit goes straight to the global list.
+// Without it, every warp's push was a global atomic on the same four
+// counters, which serialised the rounds that release 10^5 vertices.
+constexpr int kJpStage = 512;  // entries per kind
+constexpr int kJpStageMinReady = 8192;  // ready vertices from which a round stages
+struct JpStage {
+    int cnt[kJpKinds];
+    int base[kJpKinds];
+    int4 q[kJpKinds][kJpStage];
+};
+
 // append u (arcs [beg, end)) to the next round's list of its kind;
-// warp-aggregated
+// warp-aggregated, through the block's stage when one is given
 __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next, int nxt_list,
-                                           bool ready, int u, int beg, int end) {
+                                           bool ready, int u, int beg, int end,
+                                           JpStage *stg = nullptr) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     int kind = 0;
@@ -78,8 +94,25 @@ __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next,
         const bool mine = ready && kind == k;
         const unsigned bm = __ballot_sync(0xffffffffu, mine);
         if (bm) {
-            int pos = 0;
-            if (lane == 0) pos = atomicAdd(&cnt_next[k], __popc(bm));
+            const int c = __popc(bm);
+            int pos = -1;
+            if (lane == 0 && stg) {  // reserve in the stage only if all c fit
+                int old = ((volatile int *)stg->cnt)[k];
+                while (old + c <= kJpStage) {
+                    const int prev = atomicCAS(&stg->cnt[k], old, old + c);
+                    if (prev == old) {
+                        pos = old;
+                        break;
+                    }
+                    old = prev;
+                }
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (pos >= 0) {
+                if (mine) stg->q[k][pos + __popc(bm & lt)] = make_int4(u, beg, end, 0);
+                continue;
+            }
+            if (lane == 0) pos = atomicAdd(&cnt_next[k], c);
             pos = __shfl_sync(0xffffffffu, pos, 0);
             if (mine) st.list[k][nxt_list][pos + __popc(bm & lt)] = make_int4(u, beg, end, 0);
         }
@@ -95,7 +128,7 @@ __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next,
 // neighbour are loaded beside its decrement, for the queue entry.
 template <int kU>  // chunks of 32 arcs in flight per warp
 __device__ void jp_pass(const DGraph &g, const JpState &st, int v, int e0, int e1, int wrank,
-                        int nw, unsigned *bm, int32_t *cnt_next, int nxt_list) {
+                        int nw, unsigned *bm, int32_t *cnt_next, int nxt_list, JpStage *stg) {
     const int lane = threadIdx.x & 31;
     const int stride = nw * 32;
     for (int b0 = e0 + wrank * 32; b0 < e1; b0 += kU * stride) {
@@ -124,7 +157,7 @@ __device__ void jp_pass(const DGraph &g, const JpState &st, int v, int e0, int e
             if (uu[u] != v && higher[u] && res[u] < kMexWindow)
                 atomicOr(&bm[res[u] >> 5], 1u << (res[u] & 31));
             push_ready(st, cnt_next, nxt_list, uu[u] != v && !higher[u] && res[u] == 1, uu[u], ob[u],
-                       oe[u]);
+                       oe[u], stg);
         }
     }
 }
@@ -175,7 +208,7 @@ __device__ __forceinline__ void set_color(const JpState &st, int v, int mex) {
 // Every lane of the warp calls this (t >= n marks an empty group).
 template <int LANES>
 __device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *list, int t, int n,
-                             int32_t *cnt_next, int nxt_list) {
+                             int32_t *cnt_next, int nxt_list, JpStage *stg) {
     constexpr int kA = kJpTiny / LANES;
     const int lane = threadIdx.x & 31, gl = lane & (LANES - 1);
     const bool has = t < n;
@@ -207,7 +240,7 @@ __device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *lis
     for (int a = 0; a < kA; ++a) {
         if (uu[a] != v && higher[a] && res[a] < 64) mask |= 1ull << res[a];
         push_ready(st, cnt_next, nxt_list, uu[a] != v && !higher[a] && res[a] == 1, uu[a], ob[a],
-                   oe[a]);
+                   oe[a], stg);
     }
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
@@ -275,6 +308,33 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
     }
 }
 
+// Appends the block's staged entries to the global lists (one global
+// atomic per kind) and empties the stage.  Called by the whole block at a
+// block-uniform point; `more` = pushes follow before the next grid barrier
+// (which otherwise orders the emptied stage before the next round's pushes).
+__device__ void jp_flush(const JpState &st, JpStage *stg, int32_t *cnt_next, int nxt_list,
+                         bool more) {
+    __syncthreads();
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < kJpKinds; ++k) any |= stg->cnt[k] > 0;
+    if (!any) return;  // block-uniform: every thread read the same counts
+    __syncthreads();   // every thread has read the counts before they change
+    if (threadIdx.x < kJpKinds) {
+        const int c = stg->cnt[threadIdx.x];
+        stg->base[threadIdx.x] = c ? atomicAdd(&cnt_next[threadIdx.x], c) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kJpKinds; ++k) {
+        const int c = stg->cnt[k], b = stg->base[k];
+        for (int t = threadIdx.x; t < c; t += blockDim.x) st.list[k][nxt_list][b + t] = stg->q[k][t];
+    }
+    __syncthreads();
+    if (threadIdx.x < kJpKinds) stg->cnt[threadIdx.x] = 0;
+    if (more) __syncthreads();
+}
+
 // All rounds of Jones-Plassmann in one cooperative launch.  Round r colours
 // the vertices queued in round r - 1, in units of one block each:
 //   huge  split over P blocks each, which mark a global bitmap and release
@@ -288,6 +348,10 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
 // coloured in round r + 1, after the colours they depend on have been
 // written.
 __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpState st) {
+    extern __shared__ int4 jp_dyn[];
+    JpStage *stg = reinterpret_cast<JpStage *>(jp_dyn);
+    if (threadIdx.x < kJpKinds) stg->cnt[threadIdx.x] = 0;
+    __syncthreads();
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
     __shared__ int s_last_part;
@@ -309,6 +373,9 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                           : 0;
         const int huge_units = n_huge * P;
         const int units = huge_units + n_big + small_units + tiny_units;
+        // heavy rounds stage their pushes in the block; light ones (the long
+        // tail of the priority DAG) push straight to the global lists
+        JpStage *rs = n_small + n_tiny + n_big >= kJpStageMinReady ? stg : nullptr;
         for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
             if (unit < huge_units) {
                 const int t = unit % n_huge, part = unit / n_huge;
@@ -317,7 +384,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                 const int L = (it.z - it.y + P - 1) / P;
                 const int e0 = it.y + part * L, e1 = min(it.z, e0 + L);
                 unsigned *gbm = st.huge_bm + (size_t)t * 32;
-                jp_pass<4>(g, st, v, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list);
+                jp_pass<4>(g, st, v, e0, e1, wib, kJpWarps, gbm, cnt_next, out_list, rs);
                 __threadfence();
                 __syncthreads();
                 if (threadIdx.x == 0) s_last_part = atomicAdd(&st.huge_done[t], 1) == P - 1;
@@ -338,7 +405,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                 const int v = it.x;
                 if (threadIdx.x < 32) bm_cta[threadIdx.x] = 0u;
                 __syncthreads();
-                jp_pass<4>(g, st, v, it.y, it.z, wib, kJpWarps, bm_cta, cnt_next, out_list);
+                jp_pass<4>(g, st, v, it.y, it.z, wib, kJpWarps, bm_cta, cnt_next, out_list, rs);
                 __syncthreads();
                 if (wib == 0) {
                     const int mex = warp_mex(g, st, v, bm_cta[lane], bm_warp[0]);
@@ -349,7 +416,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                 const int u0 = (unit - huge_units - n_big - small_units) * tiny_per_unit;
                 jp_tiny_warp<kJpTinyLanes>(g, st, st.list[3][in_list],
                                            u0 + wib * kJpTinyPerWarp + lane / kJpTinyLanes,
-                                           n_tiny, cnt_next, out_list);
+                                           n_tiny, cnt_next, out_list, rs);
             } else {
                 const int t = (unit - huge_units - n_big) * kJpWarps + wib;
                 if (t < n_small) {
@@ -358,7 +425,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                     unsigned *bm = bm_warp[wib];
                     bm[lane] = 0u;
                     __syncwarp();
-                    jp_pass<kJpSmallU>(g, st, v, it.y, it.z, 0, 1, bm, cnt_next, out_list);
+                    jp_pass<kJpSmallU>(g, st, v, it.y, it.z, 0, 1, bm, cnt_next, out_list, rs);
                     __syncwarp();
                     const unsigned w0 = bm[lane];
                     __syncwarp();
@@ -367,7 +434,15 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                     __syncwarp();
                 }
             }
+            if (rs && unit + (int)gridDim.x < units) {  // block-uniform: more units follow
+                __syncthreads();
+                bool half = false;
+#pragma unroll
+                for (int k = 0; k < kJpKinds; ++k) half |= stg->cnt[k] > kJpStage / 2;
+                if (half) jp_flush(st, stg, cnt_next, out_list, true);
+            }
         }
+        if (rs) jp_flush(st, stg, cnt_next, out_list, false);  // the round's last entries
         const unsigned long long tr1 = LV_TRACE_ON ? gtimer() : 0;
         if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 8)
             trace4(st.tb, 0x100000000ull | (unsigned)r, (unsigned long long)blockIdx.x, tr0, tr1);
@@ -490,16 +565,19 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
     jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, d, hb, st);
     LV_LAUNCH_CHECK();
     static int blocks_per_sm = 0;
+    const int stage_bytes = (int)sizeof(JpStage);
     if (!blocks_per_sm) {
+        LV_CUDA(cudaFuncSetAttribute(jp_persistent_kernel,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, stage_bytes));
         LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, jp_persistent_kernel,
-                                                              kJpBlock, 0));
+                                                              kJpBlock, stage_bytes));
         if (blocks_per_sm < 1) return LV_ERR_CUDA;
     }
     DGraph garg = g;
     void *args[] = {&garg, &st};
     // one block per SM: a second one per SM only adds barrier arrivals
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms),
-                                        dim3(kJpBlock), args, 0, s));
+                                        dim3(kJpBlock), args, stage_bytes, s));
     LV_LAUNCH_CHECK();
     LV_CUDA(cudaMemcpyAsync(pinned, small_state + 13, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                             s));
@@ -549,7 +627,9 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     LV_TRY(dalloc_n(&b->hub_chunk_off, (size_t)n + 1, s));
     LV_TRY(dalloc_n(&b->hub_chunk_at, (size_t)nb + 1, s));
     int32_t *chunk_at = b->hub_chunk_at;
-    hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, hub_table_factor(color != nullptr),
+    b->hub_factor = lim.hub_factor > 0 ? lim.hub_factor : hub_table_factor(color != nullptr);
+    b->blocks_per_sm = lim.blocks_per_sm;
+    hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_factor,
                                          b->hub_off, b->hub_chunk_off);
     LV_LAUNCH_CHECK();
     LV_TRY(scan_excl_i32(b->hub_off, b->hub_off, n, s));

@@ -54,6 +54,8 @@ struct Buckets {
     int32_t *hub_done = nullptr;       // device, n: finished decide chunks per position
     int32_t *host_off = nullptr;     // host copy of bucket_off
     int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
+    int hub_factor = 2;              // hub table slots per arc (next power of two)
+    int blocks_per_sm = 0;           // sweep blocks per SM (0 = as many as fit)
 };
 #ifndef LV_HUB_CHUNK
 #define LV_HUB_CHUNK 1024
@@ -66,7 +68,16 @@ __host__ __device__ constexpr int hub_table_factor(bool coloured) { return colou
 struct BinLimits {
     // the best fixed set on the R-MAT, Chung-Lu and planted-batch workloads
     int lane_arcs = 8, warp_max = 256, cta_max = 4096;
+    // hub table slots per arc (0 = hub_table_factor of the mode) and sweep
+    // blocks per SM (0 = as many as fit); the autotuner may set both
+    int hub_factor = 0, blocks_per_sm = 0;
 };
+// sweep blocks per SM 0..2 and hub table slots per arc 0 (the mode's default),
+// 2, 4 or 8
+inline bool valid_shape(const BinLimits &l) {
+    return l.blocks_per_sm >= 0 && l.blocks_per_sm <= 2 &&
+           (l.hub_factor == 0 || l.hub_factor == 2 || l.hub_factor == 4 || l.hub_factor == 8);
+}
 lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes,
                           const BinLimits &lim, Buckets *b, int *scratch_pinned, cudaStream_t s);
 void free_buckets(Buckets &b, cudaStream_t s);

@@ -690,8 +690,11 @@ lv_status lv_server_create(lv_server **out, const lv_server_config *cfg, void *c
     if (P.bin_lane_arcs) lim.lane_arcs = P.bin_lane_arcs;
     if (P.bin_warp_max) lim.warp_max = P.bin_warp_max;
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
+    lim.blocks_per_sm = P.sweep_blocks_per_sm;
+    lim.hub_factor = P.hub_slots_per_arc;
     if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
         lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit ||
+        !valid_shape(lim) ||
         P.max_iters < 1 || P.max_phases < 1 || !(P.theta_low >= -1e300) || cfg->max_graphs < 0 ||
         cfg->mem_budget_bytes < 0)
         return LV_ERR_ARG;

@@ -39,6 +39,7 @@
 // coloured sweeps), so the load factor is <= 1/2 and every probe sequence ends; a probe count above the table size is
 // an internal error (LV_ERR_HASH), never a hang.  Grid barriers wait a bounded
 // time and report LV_ERR_TIMEOUT.
+#include <algorithm>
 #include <climits>
 
 #include "lv_ops.cuh"
@@ -94,6 +95,7 @@ struct Sweep {
     int n_act;
     long long g0;  // classes swept in this phase before this launch
     int coloured;
+    int hub_factor;  // hub table slots per arc (next power of two)
     int n;
     long long two_m;
     GridBarrier *bar;
@@ -525,7 +527,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const int i = s.order[p];
     if (!live(s, i)) return;  // block-uniform
     const int beg = s.off[i], end = s.off[i + 1];
-    const unsigned mask = (unsigned)pow2_at_least(hub_table_factor(s.coloured) * (end - beg)) - 1u;
+    const unsigned mask = (unsigned)pow2_at_least(s.hub_factor * (end - beg)) - 1u;
     int2 *tab = s.hub_table + s.hub_off[p];
     const int first = s.hub_chunk_off[p], nch = s.hub_chunk_off[p + 1] - first;
     // the hub's own terms, loaded ahead of the arcs (used after the wait)
@@ -1045,6 +1047,7 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.n_act = ps.n_act;
     a.g0 = ps.g_total;
     a.coloured = ps.coloured ? 1 : 0;
+    a.hub_factor = b.hub_factor;
     a.n = ps.g.n;
     a.two_m = ps.two_m;
     a.bar = ps.bar;
@@ -1058,7 +1061,9 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     // cooperative launch (all blocks co-resident, as the grid barrier needs);
     // the launch-attribute form is also valid inside a stream capture
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_num_sms * g_sweep_blocks_per_sm);
+    const int bps = b.blocks_per_sm > 0 ? std::min(b.blocks_per_sm, g_sweep_blocks_per_sm)
+                                        : g_sweep_blocks_per_sm;
+    cfg.gridDim = dim3(g_num_sms * bps);
     cfg.blockDim = dim3(kSwBlock);
     cfg.dynamicSmemBytes = kSwSmemInts * sizeof(int);
     cfg.stream = s;

@@ -16,6 +16,7 @@ import numpy as np
 from . import _build
 
 LV_OK = 0
+LV_ERR_STATE = -10
 STATUS_NAMES = {0: "LV_OK", -1: "LV_ERR_ARG", -2: "LV_ERR_NOT_SYMMETRIC", -3: "LV_ERR_WEIGHT",
                 -4: "LV_ERR_DUPLICATE", -5: "LV_ERR_OVERFLOW", -6: "LV_ERR_EMPTY",
                 -7: "LV_ERR_CUDA", -8: "LV_ERR_OOM", -9: "LV_ERR_TIMEOUT", -10: "LV_ERR_STATE",
@@ -43,7 +44,8 @@ class lv_params(ctypes.Structure):
                 ("bin_cta_max", ctypes.c_int32), ("autotune", ctypes.c_int32),
                 ("graph_capture", ctypes.c_int32), ("color_phases", ctypes.c_int32),
                 ("abs_threshold", ctypes.c_int32), ("vf_recursive", ctypes.c_int32),
-                ("color_order", ctypes.c_int32)]
+                ("color_order", ctypes.c_int32), ("sweep_blocks_per_sm", ctypes.c_int32),
+                ("hub_slots_per_arc", ctypes.c_int32)]
 
 
 class lv_phase_info(ctypes.Structure):
@@ -131,6 +133,8 @@ SIGNATURES = {
     "lv_get_num_iterations": (ctypes.c_int, [_vp, _P(ctypes.c_int64)]),
     "lv_get_iteration_stats": (ctypes.c_int, [_vp, _vp, ctypes.c_int64]),
     "lv_get_stats": (ctypes.c_int, [_vp, _P(lv_stats)]),
+    "lv_get_tuning": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
+    "lv_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.c_int32, _vp]),
     "lv_get_vf_map": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
     "lv_get_phase_graph": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_int64),
                                           _P(ctypes.c_int64), _vp, _vp, _vp, ctypes.c_int]),
@@ -279,6 +283,28 @@ def lv_get_stats(h: int) -> lv_stats:
     out = lv_stats()
     _check(load().lv_get_stats(h, ctypes.byref(out)), "lv_get_stats")
     return out
+
+
+TUNING_FIELDS = ("lane_arcs", "warp_max", "cta_max", "blocks_per_sm", "hub_slots_per_arc")
+
+
+def _tuning(fn, h: int, index: int):
+    out = np.zeros(5, dtype=np.int32)
+    code = fn(h, index, out.ctypes.data)
+    if code == LV_ERR_STATE:
+        return None
+    _check(code, fn.__name__)
+    return dict(zip(TUNING_FIELDS, (int(x) for x in out)))
+
+
+def lv_get_tuning(h: int, phase: int):
+    """The autotuner's choice for a phase as a dict, or None if not tuned."""
+    return _tuning(load().lv_get_tuning, h, phase)
+
+
+def lv_batch_get_tuning(h: int, rnd: int):
+    """The autotuner's choice for a batched phase round, or None."""
+    return _tuning(load().lv_batch_get_tuning, h, rnd)
 
 
 def lv_get_vf_map(h: int, out) -> None:

@@ -271,6 +271,10 @@ def test_autotune_and_graph_capture_keep_results(lv):
             if key == "tuned":
                 for g in (0, 17, 39):
                     check_graph(lv, h, b, g)
+                t = lv.lv_batch_get_tuning(h, 0)  # the first round is large enough
+                assert t is not None and t["blocks_per_sm"] in (0, 1)
+                assert t["hub_slots_per_arc"] in (0, 4) and 1 <= t["lane_arcs"] <= 8
+                assert lv.lv_batch_get_tuning(h, 1000) is None
         finally:
             lv.lv_batch_destroy(h)
     assert np.array_equal(runs["plain"][0], runs["tuned"][0])
@@ -291,8 +295,43 @@ def test_autotune_single_graph(lv):
             for x, y in zip(res.phases, a.phases):
                 assert (x.N_end, x.iterations) == (y.N_end, y.iterations)
                 assert np.array_equal(x.labels, y.labels)
+        assert lv.lv_get_tuning(h, 0) is not None
     finally:
         lv.lv_graph_destroy(h)
+
+
+@pytest.mark.parametrize("shape", [dict(sweep_blocks_per_sm=1), dict(hub_slots_per_arc=4),
+                                   dict(hub_slots_per_arc=8, sweep_blocks_per_sm=2),
+                                   dict(hub_slots_per_arc=2)])
+def test_autotune_shape_knobs_keep_results(lv, shape):
+    """Every launch shape the autotuner can choose (sweep blocks per SM, hub
+    table slots per arc) gives the same labels, coloured and uncoloured,
+    single graph and batch."""
+    g, prm = gg.workload("rmat16")
+    a = lv.run(g.rowptr, g.col, g.w, **prm)
+    r = lv.run(g.rowptr, g.col, g.w, **prm, **shape)
+    for x, y in zip(r.phases, a.phases):
+        assert (x.N_end, x.iterations) == (y.N_end, y.iterations)
+        assert np.array_equal(x.labels, y.labels)
+    b = gg.planted_batch(num_graphs=12, nmin=500, nmax=20_000, seed=21)
+    runs = []
+    for extra in ({}, shape):
+        h = run_batch(lv, b, **extra)
+        try:
+            lab = np.empty(b.n, dtype=np.int32)
+            lv.lv_batch_get_labels(h, -1, -1, lab)
+            runs.append(lab)
+        finally:
+            lv.lv_batch_destroy(h)
+    assert np.array_equal(runs[0], runs[1])
+
+
+def test_shape_knobs_validated(lv):
+    g = gg.rmat(8, 8, seed=1)
+    for bad in (dict(sweep_blocks_per_sm=3), dict(hub_slots_per_arc=3)):
+        with pytest.raises(lv.LVError) as e:
+            lv.run(g.rowptr, g.col, g.w, **bad)
+        assert e.value.code == -1
 
 
 def test_batch_variants(lv, golden):
