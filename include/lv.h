@@ -109,6 +109,12 @@ typedef struct {
      * slots per arc, 2, 4 or 8 (default 4 in coloured phases, 2 otherwise). */
     int32_t sweep_blocks_per_sm;
     int32_t hub_slots_per_arc;
+    /* Most SMs the persistent kernels (sweep, colouring) of a single-graph
+     * run use: 0 = all.  A phase graph of A arcs uses about A / 65,536 SMs
+     * (at least 16) within that bound: fewer blocks make cheaper grid
+     * barriers on small graphs, and solves of small graphs on different
+     * streams run side by side (the server's single-graph lane uses it). */
+    int32_t persistent_sms;
 } lv_params;
 
 /* Per-phase record.  N values are exact modularity numerators: Q = N/(2m)^2. */

@@ -20,6 +20,7 @@
 //
 // Stopping tests use the signed net gain: (N_C - N_P) < theta |N_P|, on the
 // exact numerators converted to double once.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -337,6 +338,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
     lim.blocks_per_sm = P.sweep_blocks_per_sm;
     lim.hub_factor = P.hub_slots_per_arc;
+    lim.sms = P.persistent_sms;
     if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
         lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit ||
         !valid_shape(lim))
@@ -410,6 +412,10 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
     int32_t coloured_phases = 0;
     lv_status st = LV_OK;
     for (int32_t p = 0; p < P.max_phases; ++p) {
+        // persistent kernels of a small phase graph run on fewer SMs: fewer
+        // barrier arrivals and claims, and the graph's work still fills them
+        const int phase_sms = P.persistent_sms > 0 ? std::min(P.persistent_sms, auto_sms(G.A))
+                                                   : auto_sms(G.A);
         PhaseRec rec;
         std::memset(&rec.info, 0, sizeof rec.info);
         lv_phase_info &info = rec.info;
@@ -429,10 +435,11 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
         int32_t rounds = 0;
         if (colour_on)
             LV_TRY(jp_color(G, P.color_seed + (uint64_t)p, P.color_order == 0, color, &K, &rounds,
-                            h->pinned, s));
+                            h->pinned, s, phase_sms));
         info.color_rounds = rounds;
         info.num_colors = colour_on ? K : 0;
         BinLimits plim = lim;
+        plim.sms = phase_sms;
         if (P.autotune && !colour_on && (int64_t)G.A >= kTuneMinArcs) {
             if ((int32_t)h->tuned.size() <= p || !h->tuned_ok[p]) {
                 // time candidate bins on the phase's initial state (a scratch
@@ -463,6 +470,7 @@ lv_status run_impl(lv_graph *h, const lv_params &P) {
                 h->tuned_ok[p] = 1;
             }
             plim = h->tuned[p];
+            plim.sms = phase_sms;
         }
         Buckets b;
         LV_TRY(bucket_vertices(G, colour_on ? color : nullptr, K, plim, &b, h->pinned, s));

@@ -230,6 +230,7 @@ lv_status batch_run_impl(lv_batch *h, const lv_params &P) {
     if (P.bin_cta_max) lim.cta_max = P.bin_cta_max;
     lim.blocks_per_sm = P.sweep_blocks_per_sm;
     lim.hub_factor = P.hub_slots_per_arc;
+    lim.sms = P.persistent_sms;
     if (lim.lane_arcs < 1 || lim.lane_arcs > kLaneArcsLimit || lim.warp_max < 1 ||
         lim.warp_max > kWarpMaxLimit || lim.cta_max <= lim.warp_max || lim.cta_max > kCtaMaxLimit ||
         !valid_shape(lim))

@@ -527,7 +527,7 @@ __global__ void gather_at_kernel(const int32_t *__restrict__ vals, const int32_t
 }  // namespace
 
 lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *color,
-                   int32_t *num_colors, int32_t *rounds, int *pinned, cudaStream_t s) {
+                   int32_t *num_colors, int32_t *rounds, int *pinned, cudaStream_t s, int sms) {
     const int n = g.n;
     JpState st;
     st.color = color;
@@ -576,7 +576,8 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
     DGraph garg = g;
     void *args[] = {&garg, &st};
     // one block per SM: a second one per SM only adds barrier arrivals
-    LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(g_num_sms),
+    const int grid = sms > 0 && sms < g_num_sms ? sms : g_num_sms;
+    LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(grid),
                                         dim3(kJpBlock), args, stage_bytes, s));
     LV_LAUNCH_CHECK();
     LV_CUDA(cudaMemcpyAsync(pinned, small_state + 13, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost,
@@ -629,6 +630,7 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     int32_t *chunk_at = b->hub_chunk_at;
     b->hub_factor = lim.hub_factor > 0 ? lim.hub_factor : hub_table_factor(color != nullptr);
     b->blocks_per_sm = lim.blocks_per_sm;
+    b->sms = lim.sms;
     hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_factor,
                                          b->hub_off, b->hub_chunk_off);
     LV_LAUNCH_CHECK();

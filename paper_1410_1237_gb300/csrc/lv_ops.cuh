@@ -34,7 +34,8 @@ lv_status vf_recursive(DGraph *G, int64_t two_m, int32_t *map, int32_t n_orig, i
 // Jones-Plassmann distance-1 colouring with priority (d(v), h(v ^ seed), v),
 // d(v) = neighbours other than v (degree_first), else (h(v ^ seed), v).
 lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *color,
-                   int32_t *num_colors, int32_t *rounds, int *scratch_pinned, cudaStream_t s);
+                   int32_t *num_colors, int32_t *rounds, int *scratch_pinned, cudaStream_t s,
+                   int sms = 0);
 
 // Vertex order of a phase: vertices grouped by (colour class, degree bin),
 // ascending id inside a group.  order[n], bucket_off[(classes*(kBins+1))+1]
@@ -56,6 +57,7 @@ struct Buckets {
     int32_t *host_chunk = nullptr;   // host: hub_chunk_off at every bucket boundary
     int hub_factor = 2;              // hub table slots per arc (next power of two)
     int blocks_per_sm = 0;           // sweep blocks per SM (0 = as many as fit)
+    int sms = 0;                     // SMs of the sweep's grid (0 = all)
 };
 #ifndef LV_HUB_CHUNK
 #define LV_HUB_CHUNK 1024
@@ -71,11 +73,26 @@ struct BinLimits {
     // hub table slots per arc (0 = hub_table_factor of the mode) and sweep
     // blocks per SM (0 = as many as fit); the autotuner may set both
     int hub_factor = 0, blocks_per_sm = 0;
+    // SMs the persistent kernels run on (0 = all): concurrent solves of
+    // small graphs can share the GPU
+    int sms = 0;
 };
+// SMs of the persistent kernels for a phase graph of `arcs` arcs when the
+// caller leaves it open: one per kAutoArcsPerSm arcs, at least kAutoMinSms
+// (all SMs from 152 * kAutoArcsPerSm arcs on)
+#ifndef LV_AUTO_ARCS_PER_SM
+#define LV_AUTO_ARCS_PER_SM (1 << 16)
+#endif
+constexpr int64_t kAutoArcsPerSm = LV_AUTO_ARCS_PER_SM;
+constexpr int kAutoMinSms = 16;
+inline int auto_sms(int64_t arcs) {
+    const int64_t want = (arcs + kAutoArcsPerSm - 1) / kAutoArcsPerSm;
+    return (int)(want < kAutoMinSms ? kAutoMinSms : (want > (1 << 20) ? (1 << 20) : want));
+}
 // sweep blocks per SM 0..2 and hub table slots per arc 0 (the mode's default),
 // 2, 4 or 8
 inline bool valid_shape(const BinLimits &l) {
-    return l.blocks_per_sm >= 0 && l.blocks_per_sm <= 2 &&
+    return l.blocks_per_sm >= 0 && l.blocks_per_sm <= 2 && l.sms >= 0 &&
            (l.hub_factor == 0 || l.hub_factor == 2 || l.hub_factor == 4 || l.hub_factor == 8);
 }
 lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes,

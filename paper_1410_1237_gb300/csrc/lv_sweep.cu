@@ -1063,7 +1063,7 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     const int bps = b.blocks_per_sm > 0 ? std::min(b.blocks_per_sm, g_sweep_blocks_per_sm)
                                         : g_sweep_blocks_per_sm;
-    cfg.gridDim = dim3(g_num_sms * bps);
+    cfg.gridDim = dim3((b.sms > 0 && b.sms < g_num_sms ? b.sms : g_num_sms) * bps);
     cfg.blockDim = dim3(kSwBlock);
     cfg.dynamicSmemBytes = kSwSmemInts * sizeof(int);
     cfg.stream = s;

@@ -45,7 +45,7 @@ class lv_params(ctypes.Structure):
                 ("graph_capture", ctypes.c_int32), ("color_phases", ctypes.c_int32),
                 ("abs_threshold", ctypes.c_int32), ("vf_recursive", ctypes.c_int32),
                 ("color_order", ctypes.c_int32), ("sweep_blocks_per_sm", ctypes.c_int32),
-                ("hub_slots_per_arc", ctypes.c_int32)]
+                ("hub_slots_per_arc", ctypes.c_int32), ("persistent_sms", ctypes.c_int32)]
 
 
 class lv_phase_info(ctypes.Structure):
