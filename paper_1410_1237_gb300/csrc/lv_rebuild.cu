@@ -349,33 +349,97 @@ __global__ void fail_arcs_kernel(int n_next, const int32_t *__restrict__ ga,
         fail_arcs[c] = fail[c] ? ga[c + 1] - ga[c] : 0;
 }
 
-// communities with more arcs: their arcs as (c << b | c(v), w), one thread
-// per arc (the community by a search of the list's arc starts lstart)
-__global__ void __launch_bounds__(256) group_keys_kernel(
+// Communities left to the sort: their arcs as keys (c << b | c(v)) with
+// weights, pre-summed per block.  A block takes kAggArcs consecutive arcs of
+// the list's concatenated rows (the community of an arc by a search of the
+// list's arc starts lstart), sums equal keys in a shared-memory table, and
+// appends each distinct key once (at a position reserved with one atomic
+// per block), so the sort sees the distinct (community, neighbour) pairs of
+// each chunk instead of every arc.
+constexpr int kAggArcs = 4096;
+constexpr int kAggSlots = 2 * kAggArcs;
+constexpr int kAggThreads = 512;
+constexpr size_t kAggSmem = kAggSlots * (sizeof(unsigned long long) + sizeof(unsigned));
+__global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
     DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ lstart,
     int AL, const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
     const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm,
-    int b, uint64_t *keys, uint32_t *vals) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < AL; e += gridDim.x * blockDim.x) {
-        int lo = 0, hi = n_list;  // lstart[lo] <= e < lstart[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (lstart[mid] <= e) lo = mid; else hi = mid;
+    int b, uint64_t *keys, uint32_t *vals, int32_t *n_out, int *err) {
+    extern __shared__ unsigned long long agg[];
+    unsigned long long *K = agg;
+    unsigned *V = reinterpret_cast<unsigned *>(agg + kAggSlots);
+    __shared__ int s_cnt, s_base;
+    constexpr int kPer = kAggSlots / kAggThreads;
+    constexpr unsigned long long kNone = ~0ull;  // keys are below 2^62
+    for (int64_t c0 = (int64_t)blockIdx.x * kAggArcs; c0 < AL; c0 += (int64_t)gridDim.x * kAggArcs) {
+        for (int sl = threadIdx.x; sl < kAggSlots; sl += kAggThreads) {
+            K[sl] = kNone;
+            V[sl] = 0u;
         }
-        const int c = list[lo];
-        const int2 a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], e - lstart[lo]);
-        keys[e] = ((uint64_t)c << b) | cm[a.x];
-        vals[e] = (uint32_t)a.y;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        const int e1 = (int)(c0 + kAggArcs < AL ? c0 + kAggArcs : AL);
+        for (int e = (int)c0 + threadIdx.x; e < e1; e += kAggThreads) {
+            int lo = 0, hi = n_list;  // lstart[lo] <= e < lstart[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (lstart[mid] <= e) lo = mid; else hi = mid;
+            }
+            const int c = list[lo];
+            const int2 a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], e - lstart[lo]);
+            const unsigned long long key = ((unsigned long long)c << b) | cm[a.x];
+            unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kAggSlots - 1);
+            bool done = false;
+            for (int probe = 0; probe < kAggSlots && !done; ++probe) {
+                const unsigned long long prev = atomicCAS(&K[h], kNone, key);
+                if (prev == kNone || prev == key) {
+                    atomicAdd(&V[h], (unsigned)a.y);
+                    done = true;
+                }
+                h = (h + 1) & (kAggSlots - 1);
+            }
+            if (!done) atomicExch(err, 1);  // cannot happen: kAggArcs keys, 2x the slots
+        }
+        __syncthreads();
+        int mine = 0;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) mine += K[t * kAggThreads + threadIdx.x] != kNone ? 1 : 0;
+        const int off = mine ? atomicAdd(&s_cnt, mine) : 0;
+        __syncthreads();
+        if (threadIdx.x == 0) s_base = atomicAdd(n_out, s_cnt);
+        __syncthreads();
+        int o = s_base + off;
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int sl = t * kAggThreads + threadIdx.x;
+            if (K[sl] != kNone) {
+                keys[o] = K[sl];
+                vals[o] = V[sl];
+                ++o;
+            }
+        }
+        __syncthreads();
     }
 }
 
-// sorted arcs of the large communities: distinct (c, c(v)) summed into c's
-// slice at its rank (heads counted from the community's first sorted arc)
+// first and one-past-last position of each community's keys in the sorted
+// key array
+__global__ void key_bounds_kernel(const uint64_t *__restrict__ keys, int n, int b,
+                                  int32_t *cstart, int32_t *cend) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int c = (int)(keys[e] >> b);
+        if (e == 0 || (int)(keys[e - 1] >> b) != c) cstart[c] = e;
+        if (e == n - 1 || (int)(keys[e + 1] >> b) != c) cend[c] = e + 1;
+    }
+}
+
+// sorted keys of the large communities: distinct (c, c(v)) summed into c's
+// slice at its rank (heads counted from the community's first sorted key)
 __global__ void __launch_bounds__(256) group_emit_kernel(const uint64_t *__restrict__ keys,
                                                          const uint32_t *__restrict__ vals,
                                                          const int32_t *__restrict__ head,
                                                          const int32_t *__restrict__ pos,
-                                                         const int32_t *__restrict__ lpos,
+                                                         const int32_t *__restrict__ cstart,
                                                          const int32_t *__restrict__ ga, int AL, int b,
                                                          int2 *tmp) {
     const int lane = threadIdx.x & 31;
@@ -390,7 +454,7 @@ __global__ void __launch_bounds__(256) group_emit_kernel(const uint64_t *__restr
             const uint64_t k = keys[e];
             const int c = (int)(k >> b);
             const int h = head[e];
-            slot = ga[c] + (pos[e] + h - 1 - pos[lpos[c]]);
+            slot = ga[c] + (pos[e] + h - 1 - pos[cstart[c]]);
             w = (int)vals[e];
             if (h) tmp[slot].x = (int)(k & lowmask);
         }
@@ -406,12 +470,12 @@ __global__ void __launch_bounds__(256) group_emit_kernel(const uint64_t *__restr
 }
 
 __global__ void group_big_count_kernel(int n_list, const int32_t *__restrict__ list,
-                                       const int32_t *__restrict__ ga, const int32_t *__restrict__ lpos,
+                                       const int32_t *__restrict__ cstart,
+                                       const int32_t *__restrict__ cend,
                                        const int32_t *__restrict__ pos, int32_t *cnt) {
     for (int li = blockIdx.x * blockDim.x + threadIdx.x; li < n_list; li += gridDim.x * blockDim.x) {
         const int c = list[li];
-        const int o = lpos[c], na = ga[c + 1] - ga[c];
-        cnt[c] = pos[o + na] - pos[o];
+        cnt[c] = pos[cend[c]] - pos[cstart[c]];
     }
 }
 
@@ -570,18 +634,38 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
         gather_idx_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big - 1, list_big, lpos, lstart);
         LV_LAUNCH_CHECK();
         LV_CUDA(cudaMemcpyAsync(lstart + n_big, &AL, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        group_keys_kernel<<<grid_items(AL), 256, 0, s>>>(g, n_big, list_big, lstart, AL, gs, ga,
-                                                          apos, vo, cm, b, keys, vals);
+        int32_t *n_keys;
+        LV_TRY(t.get(&n_keys, 1));
+        LV_CUDA(cudaMemsetAsync(n_keys, 0, sizeof(int32_t), s));
+        static bool agg_attr = false;
+        if (!agg_attr) {
+            LV_CUDA(cudaFuncSetAttribute(group_keys_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kAggSmem));
+            agg_attr = true;
+        }
+        group_keys_kernel<<<grid_for(AL, kAggArcs, g_num_sms * 2), kAggThreads, kAggSmem, s>>>(
+            g, n_big, list_big, lstart, AL, gs, ga, apos, vo, cm, b, keys, vals, n_keys, err);
         LV_LAUNCH_CHECK();
-        LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, AL, 2 * b, s));
-        LV_TRY(t.get(&head, (size_t)AL));
-        LV_TRY(t.get(&pos, (size_t)AL + 1));
-        heads_kernel<<<grid_items(AL), 256, 0, s>>>(keys, AL, head);
+        LV_CUDA(cudaMemcpyAsync(pinned, n_keys, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        const int NK = pinned[0];
+        LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, NK, 2 * b, s));
+        int32_t *cstart, *cend;
+        LV_TRY(t.get(&cstart, (size_t)n_next + 1));
+        LV_TRY(t.get(&cend, (size_t)n_next + 1));
+        LV_TRY(t.get(&head, (size_t)NK));
+        LV_TRY(t.get(&pos, (size_t)NK + 1));
+        heads_kernel<<<grid_items(NK), 256, 0, s>>>(keys, NK, head);
         LV_LAUNCH_CHECK();
-        LV_TRY(scan_excl_i32(head, pos, AL, s));
-        group_emit_kernel<<<grid_items(AL), 256, 0, s>>>(keys, vals, head, pos, lpos, ga, AL, b, tmp);
+        key_bounds_kernel<<<grid_items(NK), 256, 0, s>>>(keys, NK, b, cstart, cend);
         LV_LAUNCH_CHECK();
-        group_big_count_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big, list_big, ga, lpos, pos, cnt);
+        LV_TRY(scan_excl_i32(head, pos, NK, s));
+        group_emit_kernel<<<grid_items(NK), 256, 0, s>>>(keys, vals, head, pos, cstart, ga, NK, b,
+                                                         tmp);
+        LV_LAUNCH_CHECK();
+        group_big_count_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big, list_big, cstart, cend,
+                                                                 pos, cnt);
         LV_LAUNCH_CHECK();
     }
     // pack the rows
