@@ -69,7 +69,8 @@ typedef struct {
     /* Degree bins of the sweep (0 = default); results do not depend on them.
      * A vertex of degree d <= bin_warp_max is swept by the smallest group of
      * G = 1, 2, ..., 32 lanes with d <= G * bin_lane_arcs (else 32 lanes);
-     * d <= bin_cta_max by one CTA; larger (hubs) by several CTAs. */
+     * d <= bin_cta_max by a quarter CTA (4 warps) up to 1,024 arcs, else by
+     * one CTA; larger (hubs) by several CTAs. */
     int32_t bin_lane_arcs;    /* 1..8, default 8 */
     int32_t bin_warp_max;     /* 1..256, default 256 */
     int32_t bin_cta_max;      /* bin_warp_max+1 .. 4096, default 4096 */

@@ -21,7 +21,8 @@
 // Vertex order: a stable radix sort of (colour, degree bin) keys, so each
 // colour class is split into the group / warp / CTA / hub bins of the sweep,
 // ascending vertex id inside each bucket.  Bins: groups of 1..32 lanes per
-// vertex (about lane_arcs arcs per lane), CTA, hub (several CTAs).
+// vertex (about lane_arcs arcs per lane), quarter CTA (up to 1,024 arcs), CTA,
+// hub (several CTAs).
 #include <cstring>
 
 #include "lv_ops.cuh"
@@ -476,7 +477,8 @@ __global__ void bucket_key_kernel(DGraph g, const int32_t *__restrict__ color, B
         else if (deg <= lim.warp_max) {
             bin = 0;  // smallest group of G = 2^bin lanes with deg <= G * lane_arcs
             while (bin < kGroupBins - 1 && deg > (1 << bin) * lim.lane_arcs) ++bin;
-        } else if (deg <= lim.cta_max) bin = kBinCta;
+        } else if (deg <= lim.cta_max && deg <= kQuadMaxArcs) bin = kBinQuad;
+        else if (deg <= lim.cta_max) bin = kBinCta;
         else bin = kBinHub;
         const int cls = color ? color[v] : 0;
         keys[v] = (uint32_t)(cls * (kBins + 1) + bin);

@@ -25,12 +25,15 @@ namespace lv {
 
 constexpr int kEmpty = -1;           // empty hash slot (labels are >= 0)
 // Sweep bins: 0..5 = groups of G = 1, 2, 4, 8, 16, 32 lanes per vertex,
-// 6 = one CTA per vertex, 7 = hubs (several CTAs per vertex).
+// 6 = a quarter CTA (4 warps) per vertex, 7 = one CTA per vertex, 8 = hubs
+// (several CTAs per vertex).
 constexpr int kGroupBins = 6;
-constexpr int kBins = 8;
+constexpr int kBins = 9;
 constexpr int kBinSkip = kBins;      // isolated vertices (no arcs)
-constexpr int kBinCta = 6;
-constexpr int kBinHub = 7;
+constexpr int kBinQuad = 6;
+constexpr int kBinCta = 7;
+constexpr int kBinHub = 8;
+constexpr int kQuadMaxArcs = 1024;   // quarter-CTA vertices have at most this many arcs
 constexpr int kLaneArcsLimit = 8;    // a group of G lanes takes <= G * lane_arcs arcs
 constexpr int kWarpMaxLimit = 256;   // warp table holds 2x this
 constexpr int kCtaMaxLimit = 4096;   // CTA-bin table holds 2x this (64 KB)

@@ -59,6 +59,10 @@ constexpr int kSwWarps = kSwBlock / 32;
 constexpr int kSwSmemInts = 2 * kCtaSlots;
 constexpr int kU = 4;                                  // loads in flight per thread
 constexpr int kCtaArcs = kCtaMaxLimit / kSwBlock;      // arcs per thread of a CTA-bin vertex
+constexpr int kQuadThreads = kSwBlock / 4;             // a quarter CTA: 4 warps
+constexpr int kQuadArcs = kQuadMaxArcs / kQuadThreads; // arcs per thread of a quarter-CTA vertex
+constexpr int kQuadSlots = kCtaSlots / 4;              // its table: 2x the arcs
+static_assert(kQuadSlots >= 2 * kQuadMaxArcs, "quarter-CTA table must fit");
 static_assert(kSwWarps * kGroupTableInts == kCtaSlots, "warp tables tile the key half");
 static_assert(2 * kWarpMaxLimit <= kGroupTableInts, "warp table must fit");
 static_assert(kCtaArcs * kSwBlock == kCtaMaxLimit, "CTA-bin arcs split evenly");
@@ -485,6 +489,82 @@ __device__ void block_vertex_sweep(const Sweep &s, const Cls &cc, int i, int *dy
     __syncthreads();
 }
 
+// Quarter-CTA vertices (warp_max < arcs <= 1,024): four per block item, each
+// swept by 4 warps with its own quarter of the shared-memory table and a
+// named barrier of its own, so a block has four vertices in flight instead
+// of one.  Group-uniform control flow: every thread of a group reaches its
+// barriers.
+__device__ __forceinline__ void quad_sync(int grp) {
+    asm volatile("bar.sync %0, %1;" ::"r"(grp + 1), "r"(kQuadThreads) : "memory");
+}
+__device__ void quad_vertex_sweep(const Sweep &s, const Cls &cc, const int32_t *verts, int nq,
+                                  int qi, int *dyn, BlockRed &red, Acc &acc) {
+    const int grp = threadIdx.x / kQuadThreads, t = threadIdx.x % kQuadThreads;
+    const int lane = threadIdx.x & 31, wig = t >> 5;
+    const int vi = qi * 4 + grp;
+    bool valid = vi < nq;
+    int i = 0;
+    if (valid) {
+        i = verts[vi];
+        valid = live(s, i);
+    }
+    int beg = 0, end = 0, ci = 0, ki = 0, lp = 0;
+    long long tm = 0;
+    unsigned long long cmi = 0;
+    unsigned mask = 0;
+    if (valid) {
+        tm = tm_of(s, i);
+        beg = s.off[i];
+        end = s.off[i + 1];
+        ci = ldC(s, i);
+        ki = s.k[i];
+        if (t == 0) {
+            cmi = __ldcg(&cc.xr[ci]);
+            lp = s.loop[i];
+        }
+        mask = (unsigned)pow2_at_least(2 * (end - beg)) - 1u;
+        if (end - beg > kQuadMaxArcs) {  // bins never give a quarter CTA more
+            acc.err = 1;
+            end = beg;
+        }
+    }
+    int *key = dyn + grp * kQuadSlots;
+    int *val = dyn + kCtaSlots + grp * kQuadSlots;
+    int own[kQuadArcs];
+    insert_owned<1, kQuadArcs>(s, i, beg + t, end, kQuadThreads, key, val, mask, own, acc);
+    quad_sync(grp);
+    Best b;
+    best_init(b);
+    int e_old = 0;
+    owner_eval<1, kQuadArcs>(cc, key, val, own, ci, ki, tm, b, e_old);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e_old += __shfl_xor_sync(0xffffffffu, e_old, o);
+        best_shfl_xor(b, o);
+    }
+    const int slot = grp * 4 + wig;
+    if (lane == 0) {
+        red.s[slot] = b.s;
+        red.c[slot] = b.c;
+        red.z[slot] = b.size;
+        red.e[slot] = b.e;
+        red.eo[slot] = e_old;
+    }
+    quad_sync(grp);
+    if (t == 0 && valid) {
+        best_init(b);
+        e_old = 0;
+        for (int q = grp * 4; q < grp * 4 + 4; ++q) {
+            best_take(b, red.s[q], red.c[q], red.z[q], red.e[q]);
+            e_old += red.eo[q];
+        }
+        int ein = 0;
+        const bool mv = decide(ci, ki, cmi, lp, tm, b, e_old, acc, ein);
+        if (mv) commit(s, cc, atomicAdd(cc.cnt, 1), i, ci, b.c, ki);
+        add_terms(s, acc, i, ein, mv);
+    }
+}
+
 // position of the hub owning arc chunk `chunk` in bucket [lo, lo + cnt)
 __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int chunk) {
     const int32_t *co = s.hub_chunk_off + lo;  // co[cnt] > chunk >= co[0]
@@ -808,7 +888,9 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
             }
         }
         const int32_t *bo = s.bucket_off + c * (kBins + 1);
+        const int b_quad = bo[kBinQuad];
         const int b_cta = bo[kBinCta], b_hub = bo[kBinHub], b_end = bo[kBins];
+        const int n_quad = b_cta - b_quad, n_qitems = (n_quad + 3) >> 2;
         const int32_t *ca = s.chunk_at + c * (kBins + 1);
         const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
         const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
@@ -819,7 +901,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         const bool hub_par = s.coloured && n_hub > 0 && nchunks <= (int)gridDim.x;
         // block items, handed out by a class counter (the next index is
         // fetched while the current item runs)
-        const int n_bitems = nchunks + n_cta;
+        const int n_bitems = nchunks + n_cta + n_qitems;
         if (n_bitems > 0) {
             int32_t *bctr = s.move_count + s.n_act + q;
             if (threadIdx.x == 0) s_item = atomicAdd(bctr, 1);
@@ -835,11 +917,16 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
                 const unsigned long long ti0 = gtimer();
 #endif
                 if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_par);
-                else block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
+                else if (it < nchunks + n_cta)
+                    block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
+                else
+                    quad_vertex_sweep(s, cc, s.order + b_quad, n_quad, it - nchunks - n_cta, dyn,
+                                      red, acc);
                 __syncthreads();
 #ifdef LV_TRACE
                 if (threadIdx.x == 0 && blockIdx.x < 64) {
-                    const int vv = it < nchunks ? -1 : s.order[b_cta + it - nchunks];
+                    const int vv =
+                        it < nchunks || it >= nchunks + n_cta ? -1 : s.order[b_cta + it - nchunks];
                     const int dd = vv < 0 ? kHubChunk : s.off[vv + 1] - s.off[vv];
                     trace4(s.tb, 0x700000000ull | (unsigned)(it < nchunks ? 0 : 1),
                            (unsigned long long)g, (unsigned long long)dd, gtimer() - ti0);
