@@ -197,8 +197,68 @@ __global__ void vf_rowlen_kernel(DGraph g, const int32_t *__restrict__ keep,
     }
 }
 
-// one warp per kept row: drop arcs to removed vertices, renumber, add the
-// merged weight to the self-loop (inserting it at its sorted place if absent)
+// Kept rows of at most kVfSmallRow arcs, four per warp with kVfLanes lanes
+// each (rows of this size fill a warp's lanes poorly): as vf_fill_kernel,
+// with the warp's ballots cut to the group's bits.
+constexpr int kVfLanes = 8;
+constexpr int kVfSmallRow = 64;
+__global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int32_t *__restrict__ keep,
+                                                            const int32_t *__restrict__ newid,
+                                                            const int32_t *__restrict__ loop,
+                                                            const int32_t *__restrict__ extra,
+                                                            const int32_t *__restrict__ off2,
+                                                            int2 *arcs2) {
+    constexpr int kGroups = 32 / kVfLanes;
+    const int lane = threadIdx.x & 31, grp = lane / kVfLanes, gl = lane % kVfLanes;
+    const unsigned gshift = grp * kVfLanes, gbits = (1u << kVfLanes) - 1u;
+    const unsigned lt = (1u << gl) - 1u;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    for (int64_t w = blockIdx.x * 8 + (threadIdx.x >> 5); w * kGroups < g.n; w += nw) {
+        const int64_t ii = w * kGroups + grp;
+        const int i = (int)ii;
+        int beg = 0, end = 0;
+        bool row = ii < g.n;
+        if (row) {
+            beg = g.off[i];
+            end = g.off[i + 1];
+            row = keep[i] && end - beg <= kVfSmallRow;
+        }
+        if (!row) end = beg;
+        const int ni = row ? newid[i] : 0;
+        const int ex = row ? extra[i] : 0;
+        bool pending = row && loop[i] == 0 && ex > 0;  // self-loop to insert
+        int run = row ? off2[ni] : 0;
+        int sh = 0;  // 1 once the inserted loop precedes the current arcs
+        const int nch = __reduce_max_sync(0xffffffffu, (end - beg + kVfLanes - 1) / kVfLanes);
+        for (int t = 0; t < nch; ++t) {
+            const int e = beg + t * kVfLanes + gl;
+            const bool valid = e < end;
+            const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
+            const bool kp = valid && (a.x == i || keep[a.x]);
+            const unsigned bk = (__ballot_sync(0xffffffffu, kp) >> gshift) & gbits;
+            const unsigned bgt =
+                (__ballot_sync(0xffffffffu, pending && kp && a.x > i) >> gshift) & gbits;
+            int lsh = sh;
+            if (bgt) {  // group-uniform: only a pending group has bits here
+                const int f = __ffs(bgt) - 1;
+                if (gl == 0) arcs2[run + __popc(bk & ((1u << f) - 1u))] = make_int2(ni, ex);
+                if (gl >= f) lsh = 1;
+                pending = false;
+                sh = 1;
+            }
+            if (kp) {
+                const int pos = run + __popc(bk & lt) + lsh;
+                arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
+            }
+            run += __popc(bk);
+        }
+        if (pending && gl == 0) arcs2[run + sh] = make_int2(ni, ex);
+    }
+}
+
+// one warp per kept row of kVfSmallRow < arcs < kBigRow: drop arcs to
+// removed vertices, renumber, add the merged weight to the self-loop
+// (inserting it at its sorted place if absent)
 __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *__restrict__ keep,
                                                       const int32_t *__restrict__ newid,
                                                       const int32_t *__restrict__ loop,
@@ -210,7 +270,8 @@ __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *_
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t ii = blockIdx.x * 8 + (threadIdx.x >> 5); ii < g.n; ii += nw) {
         const int i = (int)ii;
-        if (!keep[i] || g.off[i + 1] - g.off[i] >= kBigRow) continue;  // warp-uniform
+        const int len = g.off[i + 1] - g.off[i];
+        if (!keep[i] || len >= kBigRow || len <= kVfSmallRow) continue;  // warp-uniform
         const int ni = newid[i];
         const int ex = extra[i];
         bool pending = (loop[i] == 0 && ex > 0);  // self-loop to insert
@@ -512,6 +573,9 @@ lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, in
     LV_CUDA(cudaStreamSynchronize(s));
     h.A = scratch_pinned[0];
     LV_TRY(dalloc_n(&h.arcs, (size_t)h.A, s));
+    vf_fill_small_kernel<<<grid_rows((n + 3) / 4), 256, 0, s>>>(g, keep, newid, loop, extra, h.off,
+                                                                h.arcs);
+    LV_LAUNCH_CHECK();
     vf_fill_kernel<<<grid_rows(n), 256, 0, s>>>(g, keep, newid, loop, extra, h.off, h.arcs);
     LV_LAUNCH_CHECK();
     int32_t *big = nullptr;
