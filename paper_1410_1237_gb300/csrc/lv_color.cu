@@ -24,6 +24,7 @@
 // vertex (about lane_arcs arcs per lane), quarter CTA (up to 1,024 arcs), CTA,
 // hub (several CTAs).
 #include <cstring>
+#include <vector>
 
 #include "lv_ops.cuh"
 
@@ -502,15 +503,19 @@ __device__ __forceinline__ int next_pow2(int x) {
 }
 
 // hub hash-table size and arc-chunk count at each position of the order
-// (0 for non-hubs)
+// (0 for non-hubs); the chunk is kHubChunk << shift[class] (keys: the sorted
+// bucket keys; shift may be null)
 __global__ void hub_size_kernel(DGraph g, const int32_t *__restrict__ order, int cta_max, int factor,
-                                int32_t *tsize, int32_t *nchunks) {
+                                const uint32_t *__restrict__ keys,
+                                const uint8_t *__restrict__ shift, int32_t *tsize,
+                                int32_t *nchunks) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < g.n; p += gridDim.x * blockDim.x) {
         const int v = order[p];
         const int deg = g.off[v + 1] - g.off[v];
         const bool hub = deg > cta_max;
+        const int chunk = kHubChunk << (shift && hub ? shift[keys[p] / (kBins + 1)] : 0);
         tsize[p] = hub ? next_pow2(factor * deg) : 0;
-        nchunks[p] = hub ? (deg + kHubChunk - 1) / kHubChunk : 0;
+        nchunks[p] = hub ? (deg + chunk - 1) / chunk : 0;
     }
 }
 
@@ -633,19 +638,42 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     b->hub_factor = lim.hub_factor > 0 ? lim.hub_factor : hub_table_factor(color != nullptr);
     b->blocks_per_sm = lim.blocks_per_sm;
     b->sms = lim.sms;
-    hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_factor,
-                                         b->hub_off, b->hub_chunk_off);
-    LV_LAUNCH_CHECK();
-    LV_TRY(scan_excl_i32(b->hub_off, b->hub_off, n, s));
-    LV_TRY(scan_excl_i32(b->hub_chunk_off, b->hub_chunk_off, n, s));
-    gather_at_kernel<<<grid_for(nb + 1, 256, 1024), 256, 0, s>>>(b->hub_chunk_off, b->bucket_off,
-                                                               nb + 1, chunk_at);
-    LV_LAUNCH_CHECK();
     b->host_chunk = new int32_t[(size_t)nb + 1];
-    LV_CUDA(cudaMemcpyAsync(b->host_chunk, chunk_at, sizeof(int32_t) * ((size_t)nb + 1),
-                            cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaMemcpyAsync(pinned, b->hub_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    LV_CUDA(cudaStreamSynchronize(s));
+    auto size_hubs = [&]() -> lv_status {
+        hub_size_kernel<<<grid, 256, 0, s>>>(g, b->order, lim.cta_max, b->hub_factor, keys,
+                                             b->hub_shift, b->hub_off, b->hub_chunk_off);
+        LV_LAUNCH_CHECK();
+        LV_TRY(scan_excl_i32(b->hub_off, b->hub_off, n, s));
+        LV_TRY(scan_excl_i32(b->hub_chunk_off, b->hub_chunk_off, n, s));
+        gather_at_kernel<<<grid_for(nb + 1, 256, 1024), 256, 0, s>>>(
+            b->hub_chunk_off, b->bucket_off, nb + 1, chunk_at);
+        LV_LAUNCH_CHECK();
+        LV_CUDA(cudaMemcpyAsync(b->host_chunk, chunk_at, sizeof(int32_t) * ((size_t)nb + 1),
+                                cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaMemcpyAsync(pinned, b->hub_off + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        return LV_OK;
+    };
+    LV_TRY(size_hubs());
+    // classes whose hubs have more chunks than the sweep grid has blocks take
+    // chunks twice as long: half the block items and global-table merges
+    {
+        const int gsz = sweep_grid(*b);
+        std::vector<uint8_t> wide((size_t)classes, 0);
+        bool any = false;
+        for (int c = 0; c < classes; ++c) {
+            const size_t h = (size_t)c * (kBins + 1) + kBinHub;
+            const int nch = b->host_chunk[h + 1] - b->host_chunk[h];
+            if (nch > LV_HUB_WIDE_AT * gsz) wide[c] = 1, any = true;
+        }
+        if (any) {
+            LV_TRY(dalloc_n(&b->hub_shift, (size_t)classes, s));
+            LV_CUDA(cudaMemcpyAsync(b->hub_shift, wide.data(), (size_t)classes,
+                                    cudaMemcpyHostToDevice, s));
+            LV_TRY(size_hubs());
+        }
+    }
     b->hub_slots = pinned[0];
     if (b->hub_slots > 0) {
         LV_TRY(dalloc_n(&b->hub_table, (size_t)b->hub_slots, s));
@@ -674,6 +702,7 @@ void free_buckets(Buckets &b, cudaStream_t s) {
     dfree(b.hub_cnt, s);
     dfree(b.hub_chunk_off, s);
     dfree(b.hub_chunk_at, s);
+    dfree(b.hub_shift, s);
     dfree(b.hub_part, s);
     dfree(b.hub_done, s);
     delete[] b.host_off;

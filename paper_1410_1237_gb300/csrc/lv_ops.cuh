@@ -51,6 +51,9 @@ struct Buckets {
     int32_t *hub_cnt = nullptr;      // device, n: occupied count per position
     int32_t *hub_chunk_off = nullptr;  // device, n+1: first arc chunk of each position
     int32_t *hub_chunk_at = nullptr;   // device: hub_chunk_off at every bucket boundary
+    // device, per class: log2 of the class's hub arc chunk in units of
+    // kHubChunk (null: every class uses kHubChunk)
+    uint8_t *hub_shift = nullptr;
     void *hub_part = nullptr;          // device: partial best per hub chunk
     int32_t *hub_done = nullptr;       // device, n: finished decide chunks per position
     int32_t *host_off = nullptr;     // host copy of bucket_off
@@ -63,6 +66,11 @@ struct Buckets {
 #define LV_HUB_CHUNK 1024
 #endif
 constexpr int kHubChunk = LV_HUB_CHUNK;  // arcs (and occupied slots) per block item of a hub
+// a colour class whose hubs have more than this many kHubChunk chunks per
+// block of the sweep grid has its hubs cut into chunks of 2 kHubChunk
+#ifndef LV_HUB_WIDE_AT
+#define LV_HUB_WIDE_AT 1
+#endif
 // a hub's global table has the next power of two >= this many slots per arc:
 // 4 in coloured sweeps (shorter probe chains on the latency-bound path), 2 in
 // one-class sweeps (batches and serving, where memory is budgeted)
@@ -148,6 +156,8 @@ lv_status apply_moves(PhaseState &ps, cudaStream_t s);
 // the community-state buffer holding the current state
 unsigned long long *current_comm(const PhaseState &ps);
 size_t hub_part_bytes();
+// blocks of the sweep's cooperative grid for buckets b (after sweep_setup)
+int sweep_grid(const Buckets &b);
 
 // lv_tune.cu -------------------------------------------------------------
 // Time one sweep of the (uncoloured) phase state per candidate bin set and

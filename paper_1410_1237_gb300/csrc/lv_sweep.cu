@@ -100,6 +100,7 @@ struct Sweep {
     long long g0;  // classes swept in this phase before this launch
     int coloured;
     int hub_factor;  // hub table slots per arc (next power of two)
+    const uint8_t *__restrict__ hub_shift;  // per class: hub arc chunk = kHubChunk << shift
     int n;
     long long two_m;
     GridBarrier *bar;
@@ -572,7 +573,9 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
     return a;
 }
 
-// Hub arc chunk: kHubChunk arcs of one hub are first summed per label in a
+// Hub arc chunk: CHS arcs of one hub (kHubChunk, or twice that in classes
+// whose hubs have more chunks than the grid has blocks) are first summed per
+// label in a
 // shared-memory table of the block, then each distinct label is added to the
 // hub's global table once (so a popular label costs one global atomic per
 // chunk, not one per warp).  Global first probes are compare-and-swaps issued
@@ -582,20 +585,22 @@ __device__ __forceinline__ int hub_of_chunk(const Sweep &s, int lo, int cnt, int
 // With `par` (every chunk of the class's hubs has a block of its own), the
 // blocks of a hub then wait for all of its chunks (a bounded wait on the
 // hub's arrival counter), each evaluates the slots it claimed (at most
-// kHubChunk, one pass) and stores a partial best, and the last to finish
+// CHS, one pass) and stores a partial best, and the last to finish
 // combines the partials and decides: no grid barrier, and the evaluation is
 // spread over the hub's blocks.  Chunks are handed out before any other item
 // of the class and a block holding one claims nothing else until it is done,
 // so every block waited for is running.  Otherwise claimed slots are
 // appended to the hub's occupied list (one counter update per warp) for the
 // evaluation after a grid barrier.
-constexpr int kHubSmemSlots = 2 * kHubChunk;  // power of two, >= 2x the distinct labels
-static_assert(kHubSmemSlots <= kCtaSlots, "hub chunk table fits the key half");
+constexpr int kHubWide = 2 * kHubChunk;  // the wider chunk
+static_assert(2 * kHubWide <= kCtaSlots, "hub chunk table fits the key half");
 __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int nch, int i, int ci,
                             int ki, unsigned long long cmi, int lp, long long tm, BlockRed &red,
                             Acc &acc);
+template <int CHS>
 __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, int *dyn,
                           BlockRed &red, Acc &acc, bool par) {
+    constexpr int kHubSmemSlots = 2 * CHS;  // power of two, >= 2x the distinct labels
     __shared__ int s_flag;
     const int lane = threadIdx.x & 31;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
@@ -610,19 +615,20 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     const long long tm = tm_of(s, i);
     const int ci = ldC(s, i), ki = s.k[i], lp = s.loop[i];
     const unsigned long long cmi = __ldcg(&cc.xr[ci]);
-    const int start = beg + (chunk - first) * kHubChunk;
-    const int stop = min(end, start + kHubChunk);
+    const int start = beg + (chunk - first) * CHS;
+    const int stop = min(end, start + CHS);
     int *key = dyn, *val = dyn + kCtaSlots;  // both empty on entry
     insert_arcs<1>(s, i, start + threadIdx.x, stop, kSwBlock, key, val, kHubSmemSlots - 1, acc);
     __syncthreads();
-    static_assert(kHubSmemSlots == kU * kSwBlock, "one pass over the chunk's table");
-    int claimed[kU];
+    constexpr int kHubPer = kHubSmemSlots / kSwBlock;  // table slots per thread
+    static_assert(kHubPer * kSwBlock == kHubSmemSlots, "one pass over the chunk's table");
+    int claimed[kHubPer];
     {
-        int cl[kU], sum[kU];
-        unsigned hslot[kU];
-        int prev[kU];
+        int cl[kHubPer], sum[kHubPer];
+        unsigned hslot[kHubPer];
+        int prev[kHubPer];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kHubPer; ++u) {
             cl[u] = key[threadIdx.x + u * kSwBlock];
             sum[u] = val[threadIdx.x + u * kSwBlock];
             key[threadIdx.x + u * kSwBlock] = kEmpty;  // each thread clears the slots it read
@@ -631,7 +637,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
             prev[u] = cl[u] != kEmpty ? atomicCAS(&tab[hslot[u]].x, kEmpty, cl[u]) : 0;
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kHubPer; ++u) {
             claimed[u] = -1;
             if (cl[u] == kEmpty) continue;
             const int c = cl[u];
@@ -652,7 +658,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
         int32_t *occ = s.hub_occ + s.hub_off[p];
         int mine = 0;
 #pragma unroll
-        for (int u = 0; u < kU; ++u) mine += claimed[u] >= 0 ? 1 : 0;
+        for (int u = 0; u < kHubPer; ++u) mine += claimed[u] >= 0 ? 1 : 0;
         int incl = mine;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -665,7 +671,7 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
             if (lane == 31) base = atomicAdd(s.hub_cnt + p, total);
             base = __shfl_sync(0xffffffffu, base, 31) + incl - mine;
 #pragma unroll
-            for (int u = 0; u < kU; ++u)
+            for (int u = 0; u < kHubPer; ++u)
                 if (claimed[u] >= 0) __stcg(&occ[base++], claimed[u]);
         }
         return;
@@ -691,17 +697,17 @@ __device__ void hub_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int ch
     best_init(b);
     int e_old = 0;
     {
-        int2 kv[kU];
-        unsigned long long cm[kU];
+        int2 kv[kHubPer];
+        unsigned long long cm[kHubPer];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) kv[u] = claimed[u] >= 0 ? __ldcg(&tab[claimed[u]]) : make_int2(kEmpty, 0);
+        for (int u = 0; u < kHubPer; ++u) kv[u] = claimed[u] >= 0 ? __ldcg(&tab[claimed[u]]) : make_int2(kEmpty, 0);
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kHubPer; ++u) {
             if (claimed[u] >= 0) __stcg(&tab[claimed[u]], make_int2(kEmpty, 0));
             cm[u] = (kv[u].x != kEmpty && kv[u].x != ci) ? __ldcg(&cc.xr[kv[u].x]) : 0ull;
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kHubPer; ++u) {
             if (kv[u].x == kEmpty) continue;
             if (kv[u].x == ci) {
                 e_old = kv[u].y;
@@ -789,7 +795,7 @@ __device__ void hub_combine(const Sweep &s, const Cls &cc, int p, int first, int
 // slots (resetting them to empty) and stores a partial best; the last block
 // of the hub to finish (counted with a fenced atomic, no waiting) combines
 // the partials and decides.
-__device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk,
+__device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt, int chunk, int chs,
                                  BlockRed &red, Acc &acc) {
     __shared__ int s_last;
     const int a = hub_of_chunk(s, lo, cnt, chunk);
@@ -802,7 +808,7 @@ __device__ void hub_decide_chunk(const Sweep &s, const Cls &cc, int lo, int cnt,
     int2 *tab = s.hub_table + s.hub_off[p];
     const int32_t *occ = s.hub_occ + s.hub_off[p];
     const int n_occ = __ldcg(&s.hub_cnt[p]);
-    const int t0 = (chunk - first) * kHubChunk, t1 = min(n_occ, t0 + kHubChunk);
+    const int t0 = (chunk - first) * chs, t1 = min(n_occ, t0 + chs);
     Best b;
     best_init(b);
     int e_old = 0;
@@ -890,6 +896,7 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         const int32_t *ca = s.chunk_at + c * (kBins + 1);
         const int chunk0 = ca[kBinHub], nchunks = ca[kBins] - ca[kBinHub];
         const int n_cta = b_hub - b_cta, n_hub = b_end - b_hub;
+        const bool wide = s.hub_shift && s.hub_shift[c];
         // in coloured sweeps hubs are decided by their chunk blocks (no grid
         // barrier) when every chunk gets a block of its own; otherwise (and
         // in a one-class sweep, which has its barrier anyway) many blocks
@@ -912,7 +919,10 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
 #ifdef LV_TRACE
                 const unsigned long long ti0 = gtimer();
 #endif
-                if (it < nchunks) hub_chunk(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_par);
+                if (it < nchunks) {
+                    if (wide) hub_chunk<kHubWide>(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_par);
+                    else hub_chunk<kHubChunk>(s, cc, b_hub, n_hub, chunk0 + it, dyn, red, acc, hub_par);
+                }
                 else if (it < nchunks + n_cta)
                     block_vertex_sweep(s, cc, s.order[b_cta + it - nchunks], dyn, red, acc);
                 else
@@ -993,7 +1003,8 @@ __global__ void __launch_bounds__(kSwBlock, 2) sweep_persistent_kernel(Sweep s) 
         if (n_hub > 0 && !hub_par) {
             if (!grid_sync(s.bar, bar_passed)) return;
             for (int it = blockIdx.x; it < nchunks; it += gridDim.x)
-                hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, red, acc);
+                hub_decide_chunk(s, cc, b_hub, n_hub, chunk0 + it, wide ? kHubWide : kHubChunk,
+                                 red, acc);
 #ifdef LV_TRACE
             __syncthreads();
 #endif
@@ -1093,6 +1104,12 @@ lv_status sweep_setup() {
 
 size_t hub_part_bytes() { return sizeof(HubPart); }
 
+int sweep_grid(const Buckets &b) {
+    const int fit = g_sweep_blocks_per_sm > 0 ? g_sweep_blocks_per_sm : 1;
+    const int bps = b.blocks_per_sm > 0 ? std::min(b.blocks_per_sm, fit) : fit;
+    return (b.sms > 0 && b.sms < g_num_sms ? b.sms : g_num_sms) * bps;
+}
+
 lv_status init_phase(PhaseState &ps, cudaStream_t s) {
     LV_CUDA(cudaMemsetAsync(ps.stats, 0, sizeof(IterStats), s));
     LV_CUDA(cudaMemsetAsync(ps.move_count, 0, sizeof(int32_t) * (3 * (size_t)ps.n_act + 1), s));
@@ -1131,6 +1148,7 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     a.g0 = ps.g_total;
     a.coloured = ps.coloured ? 1 : 0;
     a.hub_factor = b.hub_factor;
+    a.hub_shift = b.hub_shift;
     a.n = ps.g.n;
     a.two_m = ps.two_m;
     a.bar = ps.bar;
@@ -1144,9 +1162,7 @@ lv_status sweep_iteration(PhaseState &ps, const Buckets &b, cudaStream_t s) {
     // cooperative launch (all blocks co-resident, as the grid barrier needs);
     // the launch-attribute form is also valid inside a stream capture
     cudaLaunchConfig_t cfg = {};
-    const int bps = b.blocks_per_sm > 0 ? std::min(b.blocks_per_sm, g_sweep_blocks_per_sm)
-                                        : g_sweep_blocks_per_sm;
-    cfg.gridDim = dim3((b.sms > 0 && b.sms < g_num_sms ? b.sms : g_num_sms) * bps);
+    cfg.gridDim = dim3(sweep_grid(b));
     cfg.blockDim = dim3(kSwBlock);
     cfg.dynamicSmemBytes = kSwSmemInts * sizeof(int);
     cfg.stream = s;
