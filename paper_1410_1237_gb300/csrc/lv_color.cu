@@ -23,6 +23,7 @@
 // ascending vertex id inside each bucket.  Bins: groups of 1..32 lanes per
 // vertex (about lane_arcs arcs per lane), quarter CTA (up to 1,024 arcs), CTA,
 // hub (several CTAs).
+#include <climits>
 #include <cstring>
 #include <vector>
 
@@ -156,7 +157,7 @@ __device__ void jp_pass(const DGraph &g, const JpState &st, int v, int e0, int e
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            if (uu[u] != v && higher[u] && res[u] < kMexWindow)
+            if (uu[u] != v && higher[u] && (unsigned)res[u] < (unsigned)kMexWindow)
                 atomicOr(&bm[res[u] >> 5], 1u << (res[u] & 31));
             push_ready(st, cnt_next, nxt_list, uu[u] != v && !higher[u] && res[u] == 1, uu[u], ob[u],
                        oe[u], stg);
@@ -240,7 +241,7 @@ __device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *lis
     unsigned long long mask = 0ull;
 #pragma unroll
     for (int a = 0; a < kA; ++a) {
-        if (uu[a] != v && higher[a] && res[a] < 64) mask |= 1ull << res[a];
+        if (uu[a] != v && higher[a] && (unsigned)res[a] < 64u) mask |= 1ull << res[a];
         push_ready(st, cnt_next, nxt_list, uu[a] != v && !higher[a] && res[a] == 1, uu[a], ob[a],
                    oe[a], stg);
     }
@@ -272,8 +273,8 @@ __global__ void nbdeg_kernel(DGraph g, int32_t *d) {
 // count of such neighbours, and the vertices that have none are queued for
 // round 0.
 __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long long seed,
-                                                      const int32_t *__restrict__ d, unsigned *hb,
-                                                      JpState st) {
+                                                      const int32_t *__restrict__ d, int core_t,
+                                                      unsigned *hb, JpState st) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * 8;
     for (int64_t vv = blockIdx.x * 8 + (threadIdx.x >> 5); vv < g.n; vv += nw) {
@@ -281,10 +282,10 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
         const unsigned long long hv = prio_hash((unsigned long long)v ^ seed);
         const int dv = d ? d[v] : 0;
         const int beg = g.off[v], end = g.off[v + 1];
-        int c = 0;
+        int c = 0, c_out = 0;  // higher-priority neighbours: all, outside the core
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int e = e0 + lane;
-            bool hi = false;
+            bool hi = false, out = false;
             if (e < end) {
                 const int u = g.arcs[e].x;
                 if (u != v) {
@@ -292,21 +293,26 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
                     hi = du > dv ||
                          (du == dv &&
                           prio_greater(prio_hash((unsigned long long)u ^ seed), u, hv, v));
+                    out = hi && du < core_t;
                 }
             }
             const unsigned m = __ballot_sync(0xffffffffu, hi);
             c += __popc(m);
+            c_out += __popc(__ballot_sync(0xffffffffu, out));
             if (lane == 0 && m) {  // the 32 arcs from e0 span two words at most
                 const int sh = e0 & 31;
                 atomicOr(&hb[e0 >> 5], m << sh);
                 if (sh && (m >> (32 - sh))) atomicOr(&hb[(e0 >> 5) + 1], m >> (32 - sh));
             }
         }
+        // a core vertex keeps its full count (the length of its list of
+        // higher-priority neighbours) and is coloured by the core pass
+        const bool core = dv >= core_t;
         if (lane == 0) {
-            st.cnt[v] = c;
+            st.cnt[v] = core ? c : c_out;
             st.color[v] = -1;
         }
-        push_ready(st, st.counts, 0, lane == 0 && c == 0, v, beg, end);  // round 0, ring slot 0
+        push_ready(st, st.counts, 0, lane == 0 && !core && c_out == 0, v, beg, end);  // round 0
     }
 }
 
@@ -352,8 +358,15 @@ __device__ void jp_flush(const JpState &st, JpStage *stg, int32_t *cnt_next, int
 __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpState st) {
     extern __shared__ int4 jp_dyn[];
     JpStage *stg = reinterpret_cast<JpStage *>(jp_dyn);
+    __shared__ int s_abort;
     if (threadIdx.x < kJpKinds) stg->cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {  // the core pass failed: its colours are incomplete
+        unsigned long long w;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(&st.bar->word) : "memory");
+        s_abort = (w >> kBarrierFlagShift) != 0;
+    }
     __syncthreads();
+    if (s_abort) return;
     __shared__ unsigned bm_warp[kJpWarps][32];
     __shared__ unsigned bm_cta[32];
     __shared__ int s_last_part;
@@ -531,6 +544,270 @@ __global__ void gather_at_kernel(const int32_t *__restrict__ vals, const int32_t
         out[q] = vals[idx[q]];
 }
 
+// ------------------------------------------------------------------ core
+// With the largest-degree-first priority the vertices of degree >= T form
+// a prefix of the priority order, so every higher-priority neighbour of
+// such a vertex is one of them too.  This core (T the smallest power of two
+// >= 64 that leaves at most kCoreMax vertices in it) holds the long
+// priority chains of a skewed graph: hubs adjacent to hubs, one or a few
+// ready per round, each round costing a grid barrier.  It is coloured first
+// by one launch without rounds: its vertices are sorted by priority, warp w
+// of the W in the grid takes ranks w, w + W, ..., and colours each vertex
+// with the smallest colour that none of its higher-priority neighbours has,
+// waiting (bounded) for those not coloured yet.  Those all have smaller
+// ranks, the smallest unfinished rank never waits and every warp is resident
+// (a cooperative launch), so the waits end.  The colour a vertex gets is
+// the one a Jones-Plassmann round gives it, as both are the smallest colour
+// absent from its higher-priority neighbours; the rounds then colour the
+// rest, the core's colours already in place.
+constexpr int kCoreMinLog = 6;                    // T >= 64
+constexpr int kCoreMax = 1 << 20;                 // vertices in the core at most
+constexpr int kCoreBlock = 512;
+constexpr int kCoreWarps = kCoreBlock / 32;
+constexpr int kCoreU = 4;                         // 32-entry chunks in flight per warp
+constexpr unsigned kCoreSpinLimit = 1u << 22;     // polls of one colour, x >= 32 ns sleeps
+
+__device__ __forceinline__ int ld_relaxed_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_i32(int32_t *p, int v) {
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// vertices per bin floor(log2 d) for d >= 2^kCoreMinLog
+__global__ void core_hist_kernel(const int32_t *__restrict__ d, int n, int32_t *hist) {
+    __shared__ int h[32];
+    if (threadIdx.x < 32) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int x = d[v];
+        if (x >= (1 << kCoreMinLog)) atomicAdd(&h[31 - __clz(x)], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// the core's vertices with the hash part of their priority, inverted so
+// that an ascending sort puts the higher priority first
+__global__ void core_collect_kernel(const int32_t *__restrict__ d, int n, int core_t,
+                                    unsigned long long seed, uint64_t *keys, uint32_t *vals,
+                                    int32_t *count) {
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    for (int v0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n; v0 += stride) {
+        const int v = v0 + lane;
+        const bool in = v < n && d[v] >= core_t;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (!m) continue;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(count, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0) + __popc(m & ((1u << lane) - 1u));
+        if (in) {
+            keys[base] = ~prio_hash((unsigned long long)v ^ seed);
+            vals[base] = (uint32_t)v;
+        }
+    }
+}
+
+// second sort key: the degree, inverted
+__global__ void core_dkey_kernel(const uint32_t *__restrict__ vals, const int32_t *__restrict__ d,
+                                 int k, uint32_t *keys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x)
+        keys[i] = ~(uint32_t)d[vals[i]];
+}
+
+// list of the higher-priority neighbours of each core vertex, in rank order
+// (one warp per vertex, a lane per 32-arc word of the priority bits; only
+// the arcs whose bit is set are read)
+__global__ void core_lists_kernel(DGraph g, const int32_t *__restrict__ order, int k,
+                                  const int32_t *__restrict__ hoff,
+                                  const unsigned *__restrict__ hb, int32_t *hcol) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < k; r += nw) {
+        const int v = order[r];
+        const int beg = g.off[v], end = g.off[v + 1];
+        int pos = hoff[r];
+        if (end <= beg) continue;
+        const int wlast = (end - 1) >> 5;
+        for (int w0 = beg >> 5; w0 <= wlast; w0 += 32) {
+            const int w = w0 + lane;
+            unsigned bits = 0u;
+            if (w <= wlast) {
+                const int lo = max(beg - 32 * w, 0), hi = min(end - 32 * w, 32);
+                const unsigned mhi = hi == 32 ? 0xffffffffu : (1u << hi) - 1u;
+                bits = __ldg(&hb[w]) & mhi & ~((1u << lo) - 1u);
+            }
+            const int c = __popc(bits);
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            int p = pos + incl - c;
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1u;
+                hcol[p++] = g.arcs[32 * w + b].x;
+            }
+            pos += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+}
+
+// colour of *p once it is written (>= 0), or -1 when the wait expires or
+// another warp has raised an error
+__device__ int core_wait(const int32_t *p, GridBarrier *bar) {
+    for (unsigned spins = 1;; ++spins) {
+        __nanosleep(32);
+        const int c = ld_relaxed_i32(p);
+        if (c >= 0) return c;
+        if (spins >= kCoreSpinLimit) return -1;
+        if ((spins & 255u) == 0u) {
+            unsigned long long w;
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(&bar->word) : "memory");
+            if (w >> kBarrierFlagShift) return -1;
+        }
+    }
+}
+
+// smallest colour absent from the list [e0, e1) (all coloured) whose first
+// window is held in word0 (word l in lane l), as warp_mex does for a row
+__device__ int core_mex(const int32_t *__restrict__ hcol, int e0, int e1, const int32_t *color,
+                        unsigned word0, unsigned *scratch32) {
+    const int lane = threadIdx.x & 31;
+    unsigned word = word0;
+    for (int base = 0;; base += kMexWindow) {
+        const unsigned notfull = __ballot_sync(0xffffffffu, word != 0xffffffffu);
+        if (notfull) {
+            const int f = __ffs(notfull) - 1;
+            const unsigned wf = __shfl_sync(0xffffffffu, word, f);
+            return base + 32 * f + __ffs(~wf) - 1;
+        }
+        const int nb = base + kMexWindow;
+        scratch32[lane] = 0u;
+        __syncwarp();
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int c = ld_relaxed_i32(&color[hcol[e]]) - nb;
+            if (c >= 0 && c < kMexWindow) atomicOr(&scratch32[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        word = scratch32[lane];
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kCoreBlock) jp_core_kernel(const int32_t *__restrict__ order,
+                                                             const int32_t *__restrict__ hoff,
+                                                             const int32_t *__restrict__ hcol,
+                                                             int k, JpState st) {
+    __shared__ unsigned bm[kCoreWarps][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nw = gridDim.x * kCoreWarps;
+    int top = -1;
+    for (int r = blockIdx.x * kCoreWarps + wib; r < k; r += nw) {
+        const int v = order[r], e0 = hoff[r], e1 = hoff[r + 1];
+        bm[wib][lane] = 0u;
+        __syncwarp();
+        bool fail = false;
+        for (int b = e0; b < e1; b += 32 * kCoreU) {
+            int u[kCoreU], c[kCoreU];
+#pragma unroll
+            for (int q = 0; q < kCoreU; ++q) {
+                const int e = b + q * 32 + lane;
+                u[q] = e < e1 ? __ldg(&hcol[e]) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < kCoreU; ++q) c[q] = u[q] >= 0 ? ld_relaxed_i32(&st.color[u[q]]) : 0;
+#pragma unroll
+            for (int q = 0; q < kCoreU; ++q) {
+                if (u[q] < 0) continue;
+                if (c[q] < 0) c[q] = core_wait(&st.color[u[q]], st.bar);
+                if (c[q] < 0) fail = true;
+                else if (c[q] < kMexWindow) atomicOr(&bm[wib][c[q] >> 5], 1u << (c[q] & 31));
+            }
+            if (__any_sync(0xffffffffu, fail)) break;
+        }
+        if (__any_sync(0xffffffffu, fail)) {  // warp-uniform: give up, flag the error
+            if (lane == 0) barrier_raise(st.bar, 1);
+            return;
+        }
+        __syncwarp();
+        const unsigned w0 = bm[wib][lane];
+        __syncwarp();
+        const int mex = core_mex(hcol, e0, e1, st.color, w0, bm[wib]);
+        if (lane == 0) st_relaxed_i32(&st.color[v], mex);
+        top = max(top, mex);
+        __syncwarp();
+    }
+    if (lane == 0 && top >= 0) atomicMax(st.max_color, top);
+}
+
+// Colours the core of degree >= core_t (k vertices): sorts it by priority
+// (degree, then hash; distinct vertices have distinct hashes), lists each
+// vertex's higher-priority neighbours (their number is st.cnt) and runs the
+// core kernel on `sms` SMs (0 = all).
+lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int core_t,
+                    const JpState &st, int *pinned, cudaStream_t s, int sms) {
+    uint64_t *keys = nullptr, *keys_alt = nullptr;
+    uint32_t *vals = nullptr, *vals_alt = nullptr, *dkeys = nullptr, *dkeys_alt = nullptr;
+    int32_t *count = nullptr, *hoff = nullptr, *hcol = nullptr;
+    LV_TRY(dalloc_n(&keys, (size_t)k, s));
+    LV_TRY(dalloc_n(&keys_alt, (size_t)k, s));
+    LV_TRY(dalloc_n(&vals, (size_t)k, s));
+    LV_TRY(dalloc_n(&vals_alt, (size_t)k, s));
+    LV_TRY(dalloc_n(&dkeys, (size_t)k, s));
+    LV_TRY(dalloc_n(&dkeys_alt, (size_t)k, s));
+    LV_TRY(dalloc_n(&count, 1, s));
+    LV_TRY(dalloc_n(&hoff, (size_t)k + 1, s));
+    LV_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
+    core_collect_kernel<<<grid_for(g.n, 256, g_num_sms * 8), 256, 0, s>>>(d, g.n, core_t, seed, keys,
+                                                                         vals, count);
+    LV_LAUNCH_CHECK();
+    LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, k, 64, s));
+    core_dkey_kernel<<<grid_for(k, 256, g_num_sms * 4), 256, 0, s>>>(vals, d, k, dkeys);
+    LV_LAUNCH_CHECK();
+    LV_TRY(radix_sort_u32(dkeys, vals, dkeys_alt, vals_alt, k, 32, s));
+    const int32_t *order = reinterpret_cast<const int32_t *>(vals);
+    gather_at_kernel<<<grid_for(k, 256, g_num_sms * 4), 256, 0, s>>>(st.cnt, order, k, hoff);
+    LV_LAUNCH_CHECK();
+    LV_TRY(scan_excl_i32(hoff, hoff, k, s));
+    LV_CUDA(cudaMemcpyAsync(pinned, hoff + k, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    LV_CUDA(cudaStreamSynchronize(s));
+    const int total = pinned[0];
+    LV_TRY(dalloc_n(&hcol, (size_t)total + 1, s));
+    core_lists_kernel<<<grid_for(k, 8, g_num_sms * 16), 256, 0, s>>>(g, order, k, hoff, st.hb,
+                                                                     hcol);
+    LV_LAUNCH_CHECK();
+    static int core_bps = 0;
+    if (!core_bps) {
+        LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&core_bps, jp_core_kernel,
+                                                              kCoreBlock, 0));
+        if (core_bps < 1) return LV_ERR_CUDA;
+    }
+    const int grid = (sms > 0 && sms < g_num_sms ? sms : g_num_sms) * core_bps;
+    JpState sarg = st;
+    const int32_t *hoff_c = hoff, *hcol_c = hcol;
+    int karg = k;
+    void *args[] = {&order, &hoff_c, &hcol_c, &karg, &sarg};
+    LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_core_kernel, dim3(grid), dim3(kCoreBlock), args,
+                                        0, s));
+    LV_LAUNCH_CHECK();
+    dfree(keys, s);
+    dfree(keys_alt, s);
+    dfree(vals, s);
+    dfree(vals_alt, s);
+    dfree(dkeys, s);
+    dfree(dkeys_alt, s);
+    dfree(count, s);
+    dfree(hoff, s);
+    dfree(hcol, s);
+    return LV_OK;
+}
+
 }  // namespace
 
 lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *color,
@@ -569,8 +846,33 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
     st.max_color = small_state + 13;
     st.bar = reinterpret_cast<GridBarrier *>(small_state + 14);
     st.rounds = small_state + 16;
-    jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, d, hb, st);
+    // the core: the smallest T = 2^b >= 64 with at most kCoreMax vertices of
+    // degree >= T (none without the degree in the priority)
+    int core_t = INT_MAX, core_k = 0;
+    if (degree_first) {
+        int32_t *hist = nullptr;
+        LV_TRY(dalloc_n(&hist, 32, s));
+        LV_CUDA(cudaMemsetAsync(hist, 0, 32 * sizeof(int32_t), s));
+        core_hist_kernel<<<grid_for(n, 256, g_num_sms * 8), 256, 0, s>>>(d, n, hist);
+        LV_LAUNCH_CHECK();
+        LV_CUDA(cudaMemcpyAsync(pinned, hist, 32 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        LV_CUDA(cudaStreamSynchronize(s));
+        dfree(hist, s);
+        int64_t above = 0;  // vertices of degree >= 2^b, b descending
+        int64_t at_least[33] = {};
+        for (int b = 31; b >= 0; --b) at_least[b] = above += pinned[b];
+        for (int b = kCoreMinLog; b < 31; ++b)
+            if (at_least[b] <= kCoreMax) {
+                if (at_least[b] > 0) {
+                    core_t = 1 << b;
+                    core_k = (int)at_least[b];
+                }
+                break;
+            }
+    }
+    jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, d, core_t, hb, st);
     LV_LAUNCH_CHECK();
+    if (core_k > 0) LV_TRY(core_pass(g, seed, d, core_k, core_t, st, pinned, s, sms));
     static int blocks_per_sm = 0;
     const int stage_bytes = (int)sizeof(JpStage);
     if (!blocks_per_sm) {

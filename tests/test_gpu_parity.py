@@ -201,6 +201,36 @@ def test_variant_first_phase_colouring(lv):
     assert res.phases[0].colored and not any(p.colored for p in res.phases[1:])
 
 
+def _core_graph(case):
+    rng = np.random.default_rng(11)
+    if case == "clique":  # every vertex in the degree >= 64 core
+        n = 80
+        return gg.from_edges(n, [(i, j) for i in range(n) for j in range(i + 1, n)])
+    if case == "equal_degrees":  # the core ordered by the hash alone
+        n, k = 2000, 35
+        return gg.from_edges(n, [(i, (i + j) % n) for i in range(n) for j in range(1, k + 1)])
+    # hubs joined to each other (a deep core chain) and to leaves, weighted
+    hubs, leaves = 200, 100
+    edges = [(i, j, int(rng.integers(1, 4))) for i in range(hubs) for j in range(i + 1, hubs)
+             if rng.random() < 0.5]
+    n = hubs + hubs * leaves
+    for h in range(hubs):
+        for t in range(leaves):
+            edges.append((h, hubs + h * leaves + t, 1))
+    edges += [(int(a), int(b), 1) for a, b in rng.integers(hubs, n, size=(3 * n, 2)) if a != b]
+    return gg.from_edges(n, edges)
+
+
+@pytest.mark.parametrize("case", ["clique", "equal_degrees", "hubs"])
+def test_colouring_core_without_rounds(lv, case):
+    """Graphs whose vertices of degree >= 64 are coloured before the rounds:
+    the colourings (and the runs) equal the oracle's."""
+    g = _core_graph(case)
+    for vf in (0, 1):
+        res, ref = compare(lv, g, graphs=True, vertex_following=vf, coloring=1, color_cutoff=0)
+        assert res.phases[0].colored
+
+
 def test_variant_colour_phase_theta(lv):
     g = gg.rmat(16, 8, seed=32)
     compare(lv, g, graphs=False, color_cutoff=0, theta_high=1e-4)
