@@ -197,9 +197,16 @@ __device__ int warp_mex(const DGraph &g, const JpState &st, int v, unsigned word
     }
 }
 
-__device__ __forceinline__ void set_color(const JpState &st, int v, int mex) {
+// the largest colour is kept per thread (`top`) and added to max_color once
+// per warp when the kernel ends: one global atomic per vertex on a single
+// word serialised the rounds that colour 10^5 vertices
+__device__ __forceinline__ void set_color(const JpState &st, int v, int mex, int &top) {
     __stcg(&st.color[v], mex);
-    atomicMax(st.max_color, mex);
+    top = max(top, mex);
+}
+__device__ __forceinline__ void flush_max(const JpState &st, int top) {
+    const int t = __reduce_max_sync(0xffffffffu, top);
+    if ((threadIdx.x & 31) == 0 && t >= 0) atomicMax(st.max_color, t);
 }
 
 // Tiny vertices (at most kJpTiny arcs), 32 / LANES per warp with LANES
@@ -211,7 +218,7 @@ __device__ __forceinline__ void set_color(const JpState &st, int v, int mex) {
 // Every lane of the warp calls this (t >= n marks an empty group).
 template <int LANES>
 __device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *list, int t, int n,
-                             int32_t *cnt_next, int nxt_list, JpStage *stg) {
+                             int32_t *cnt_next, int nxt_list, JpStage *stg, int &top) {
     constexpr int kA = kJpTiny / LANES;
     const int lane = threadIdx.x & 31, gl = lane & (LANES - 1);
     const bool has = t < n;
@@ -248,9 +255,7 @@ __device__ void jp_tiny_warp(const DGraph &g, const JpState &st, const int4 *lis
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) mask |= __shfl_xor_sync(0xffffffffu, mask, o);
     const int mex = __ffsll((long long)~mask) - 1;
-    if (has && gl == 0) __stcg(&st.color[v], mex);
-    const int top = __reduce_max_sync(0xffffffffu, (has && gl == 0) ? mex : -1);
-    if (lane == 0 && top >= 0) atomicMax(st.max_color, top);
+    if (has && gl == 0) set_color(st, v, mex, top);
 }
 
 // d(v) = neighbours of v other than v itself (rows are sorted, so the
@@ -269,9 +274,9 @@ __global__ void nbdeg_kernel(DGraph g, int32_t *d) {
 
 // Priority pi(v) = (d(v), h(v ^ seed), v) compared lexicographically (R11;
 // d = nullptr leaves the degree out).  One warp per vertex: the bit of every
-// arc whose neighbour has the higher priority (hb, cleared before), the
-// count of such neighbours, and the vertices that have none are queued for
-// round 0.
+// arc whose neighbour has the higher priority (hb, cleared before) and the
+// count of such neighbours (outside the core of degree >= core_t, for a
+// vertex outside it).
 __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long long seed,
                                                       const int32_t *__restrict__ d, int core_t,
                                                       unsigned *hb, JpState st) {
@@ -312,7 +317,59 @@ __global__ void __launch_bounds__(256) jp_init_kernel(DGraph g, unsigned long lo
             st.cnt[v] = core ? c : c_out;
             st.color[v] = -1;
         }
-        push_ready(st, st.counts, 0, lane == 0 && !core && c_out == 0, v, beg, end);  // round 0
+    }
+}
+
+// Round 0: the vertices outside the core with no higher-priority neighbour
+// outside it, listed by kind.  Each block counts its range's vertices per
+// kind in shared memory (one atomic per warp and kind) and reserves room
+// with one global atomic per kind; queuing them from jp_init_kernel cost a
+// global atomic per warp on the same four counters, millions of them on a
+// skewed graph.
+constexpr int kR0PerThread = 8;
+__global__ void __launch_bounds__(256) jp_round0_kernel(DGraph g, const int32_t *__restrict__ d,
+                                                        int core_t, JpState st) {
+    __shared__ int cnt[kJpKinds], base[kJpKinds];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    constexpr int kSpan = 256 * kR0PerThread;
+    for (int64_t b0 = (int64_t)blockIdx.x * kSpan; b0 < g.n; b0 += (int64_t)gridDim.x * kSpan) {
+        if (threadIdx.x < kJpKinds) cnt[threadIdx.x] = 0;
+        __syncthreads();
+        int kind[kR0PerThread], pos[kR0PerThread];
+#pragma unroll
+        for (int q = 0; q < kR0PerThread; ++q) {
+            const int64_t vv = b0 + q * 256 + threadIdx.x;
+            kind[q] = -1;
+            if (vv < g.n) {
+                const int v = (int)vv;
+                const bool core = (d ? d[v] : 0) >= core_t;
+                if (!core && __ldcg(&st.cnt[v]) == 0) {
+                    const int deg = g.off[v + 1] - g.off[v];
+                    kind[q] = deg >= kJpHuge ? 2 : (deg >= kJpBig ? 1 : (deg <= kJpTiny ? 3 : 0));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kJpKinds; ++k) {
+                const unsigned m = __ballot_sync(0xffffffffu, kind[q] == k);
+                if (!m) continue;
+                int p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&cnt[k], __popc(m));
+                p0 = __shfl_sync(0xffffffffu, p0, 0);
+                if (kind[q] == k) pos[q] = p0 + __popc(m & lt);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < kJpKinds)
+            base[threadIdx.x] = cnt[threadIdx.x] ? atomicAdd(&st.counts[threadIdx.x], cnt[threadIdx.x]) : 0;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kR0PerThread; ++q) {
+            if (kind[q] < 0) continue;
+            const int v = (int)(b0 + q * 256 + threadIdx.x);
+            st.list[kind[q]][0][base[kind[q]] + pos[q]] = make_int4(v, g.off[v], g.off[v + 1], 0);
+        }
+        __syncthreads();
     }
 }
 
@@ -372,6 +429,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
     __shared__ int s_last_part;
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned bar_passed = 0;
+    int top = -1;  // largest colour this thread set
     int n_small = __ldcg(&st.counts[0]), n_big = __ldcg(&st.counts[1]),
         n_huge = __ldcg(&st.counts[2]), n_tiny = __ldcg(&st.counts[3]);
     for (int r = 0;; ++r) {
@@ -410,7 +468,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                     __stcg(&gbm[lane], 0u);
                     const int mex = warp_mex(g, st, v, w0, bm_warp[0]);
                     if (lane == 0) {
-                        set_color(st, v, mex);
+                        set_color(st, v, mex, top);
                         st.huge_done[t] = 0;
                     }
                 }
@@ -424,14 +482,14 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                 __syncthreads();
                 if (wib == 0) {
                     const int mex = warp_mex(g, st, v, bm_cta[lane], bm_warp[0]);
-                    if (lane == 0) set_color(st, v, mex);
+                    if (lane == 0) set_color(st, v, mex, top);
                 }
                 __syncthreads();
             } else if (unit >= huge_units + n_big + small_units) {
                 const int u0 = (unit - huge_units - n_big - small_units) * tiny_per_unit;
                 jp_tiny_warp<kJpTinyLanes>(g, st, st.list[3][in_list],
                                            u0 + wib * kJpTinyPerWarp + lane / kJpTinyLanes,
-                                           n_tiny, cnt_next, out_list, rs);
+                                           n_tiny, cnt_next, out_list, rs, top);
             } else {
                 const int t = (unit - huge_units - n_big) * kJpWarps + wib;
                 if (t < n_small) {
@@ -445,7 +503,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                     const unsigned w0 = bm[lane];
                     __syncwarp();
                     const int mex = warp_mex(g, st, v, w0, bm);
-                    if (lane == 0) set_color(st, v, mex);
+                    if (lane == 0) set_color(st, v, mex, top);
                     __syncwarp();
                 }
             }
@@ -461,7 +519,10 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
         const unsigned long long tr1 = LV_TRACE_ON ? gtimer() : 0;
         if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 8)
             trace4(st.tb, 0x100000000ull | (unsigned)r, (unsigned long long)blockIdx.x, tr0, tr1);
-        if (!grid_sync(st.bar, bar_passed)) return;
+        if (!grid_sync(st.bar, bar_passed)) {
+            flush_max(st, top);
+            return;
+        }
         if (LV_TRACE_ON && blockIdx.x == 0 && threadIdx.x == 0)
             trace4(st.tb, 0x200000000ull | (unsigned)r,
                    ((unsigned long long)n_small << 32) | (unsigned)n_tiny, gtimer(),
@@ -472,6 +533,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
         n_tiny = __ldcg(&cnt_next[3]);
         if (n_small + n_big + n_huge + n_tiny == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *st.rounds = r + 1;
+            flush_max(st, top);
             return;
         }
         if (r > g.n) {  // every round colours at least one vertex
@@ -618,12 +680,19 @@ __global__ void core_dkey_kernel(const uint32_t *__restrict__ vals, const int32_
         keys[i] = ~(uint32_t)d[vals[i]];
 }
 
-// list of the higher-priority neighbours of each core vertex, in rank order
-// (one warp per vertex, a lane per 32-arc word of the priority bits; only
-// the arcs whose bit is set are read)
+// rank_of[order[r]] = r
+__global__ void core_rank_kernel(const int32_t *__restrict__ order, int k, int32_t *rank_of) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < k; r += gridDim.x * blockDim.x)
+        rank_of[order[r]] = r;
+}
+
+// the ranks of the higher-priority neighbours of each core vertex, in rank
+// order (one warp per vertex, a lane per 32-arc word of the priority bits;
+// only the arcs whose bit is set are read)
 __global__ void core_lists_kernel(DGraph g, const int32_t *__restrict__ order, int k,
                                   const int32_t *__restrict__ hoff,
-                                  const unsigned *__restrict__ hb, int32_t *hcol) {
+                                  const unsigned *__restrict__ hb,
+                                  const int32_t *__restrict__ rank_of, int32_t *hcol) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < k; r += nw) {
@@ -651,7 +720,7 @@ __global__ void core_lists_kernel(DGraph g, const int32_t *__restrict__ order, i
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1u;
-                hcol[p++] = g.arcs[32 * w + b].x;
+                hcol[p++] = rank_of[g.arcs[32 * w + b].x];
             }
             pos += __shfl_sync(0xffffffffu, incl, 31);
         }
@@ -700,16 +769,134 @@ __device__ int core_mex(const int32_t *__restrict__ hcol, int e0, int e1, const 
     }
 }
 
+// smallest colour absent from the ranks listed in [e0, e1) (all coloured,
+// colours in shared memory) whose first window is held in word0
+__device__ int core_mex_smem(const int32_t *__restrict__ hcol, int e0, int e1, const int *sc,
+                             unsigned word0, unsigned *scratch32) {
+    const int lane = threadIdx.x & 31;
+    unsigned word = word0;
+    for (int base = 0;; base += kMexWindow) {
+        const unsigned notfull = __ballot_sync(0xffffffffu, word != 0xffffffffu);
+        if (notfull) {
+            const int f = __ffs(notfull) - 1;
+            const unsigned wf = __shfl_sync(0xffffffffu, word, f);
+            return base + 32 * f + __ffs(~wf) - 1;
+        }
+        const int nb = base + kMexWindow;
+        scratch32[lane] = 0u;
+        __syncwarp();
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const int c = ((const volatile int *)sc)[hcol[e]] - nb;
+            if (c >= 0 && c < kMexWindow) atomicOr(&scratch32[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        word = scratch32[lane];
+        __syncwarp();
+    }
+}
+
+// The top of the core (ranks [0, r1), r1 <= kTopMax with at most kTopEntries
+// list entries) on one block: the deepest priority chains run through the
+// largest hubs, and there a colour reaches the warps waiting for it through
+// shared memory (a wait of a few hundred nanoseconds instead of a round trip
+// to L2 per link).  Warp w takes ranks w, w + 32, ...; colours go to shared
+// memory, to rc (by rank) and to the vertex.
+constexpr int kTopThreads = 1024;
+constexpr int kTopWarps = kTopThreads / 32;
+constexpr int kTopMax = 40960;                     // ranks at most
+constexpr int kTopEntries = 1 << 24;               // list entries at most
+constexpr int kTopU = 8;                           // 32-entry chunks in flight per warp
+constexpr unsigned kTopSpinLimit = 1u << 24;       // polls of one colour, x >= 20 ns sleeps
+__global__ void __launch_bounds__(kTopThreads) jp_core_top_kernel(
+    const int32_t *__restrict__ order, const int32_t *__restrict__ hoff,
+    const int32_t *__restrict__ hcol, int k, int32_t *rc, int32_t *r1_out, JpState st) {
+    extern __shared__ int sc[];  // colours of ranks [0, r1)
+    __shared__ unsigned bm[kTopWarps][32];
+    __shared__ int s_r1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {  // largest r1 <= min(k, kTopMax) with hoff[r1] <= kTopEntries
+        int lo = 0, hi = min(k, kTopMax);
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (hoff[mid] <= kTopEntries) lo = mid; else hi = mid - 1;
+        }
+        s_r1 = lo;
+        *r1_out = lo;
+    }
+    __syncthreads();
+    const int r1 = s_r1;
+    for (int i = threadIdx.x; i < r1; i += kTopThreads) sc[i] = -1;
+    __syncthreads();
+    volatile int *vsc = sc;
+    int top = -1;
+    for (int r = wib; r < r1; r += kTopWarps) {
+        const int e0 = hoff[r], e1 = hoff[r + 1];
+        bm[wib][lane] = 0u;
+        __syncwarp();
+        bool fail = false;
+        for (int b = e0; b < e1; b += 32 * kTopU) {
+            int x[kTopU];
+#pragma unroll
+            for (int q = 0; q < kTopU; ++q) {
+                const int e = b + q * 32 + lane;
+                x[q] = e < e1 ? __ldg(&hcol[e]) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < kTopU; ++q) {
+                if (x[q] < 0) continue;
+                if (x[q] >= r) {  // not an earlier rank: the lists are inconsistent
+                    fail = true;
+                    continue;
+                }
+                int c = vsc[x[q]];
+                for (unsigned spins = 0; c < 0;) {  // an earlier rank still running
+                    if (++spins > kTopSpinLimit) break;
+                    __nanosleep(20);
+                    c = vsc[x[q]];
+                }
+                if (c < 0) fail = true;
+                else if (c < kMexWindow) atomicOr(&bm[wib][c >> 5], 1u << (c & 31));
+            }
+            if (__any_sync(0xffffffffu, fail)) break;
+        }
+        if (__any_sync(0xffffffffu, fail)) {  // warp-uniform: give up, flag the error
+            if (lane == 0) barrier_raise(st.bar, 1);
+            return;
+        }
+        __syncwarp();
+        const unsigned w0 = bm[wib][lane];
+        __syncwarp();
+        const int mex = core_mex_smem(hcol, e0, e1, sc, w0, bm[wib]);
+        if (lane == 0) {
+            vsc[r] = mex;
+            rc[r] = mex;
+            __stcg(&st.color[order[r]], mex);
+        }
+        if (LV_TRACE_ON && lane == 0 && (r & 15) == 0)
+            trace4(st.tb, 0xB00000000ull, (unsigned long long)r, gtimer(),
+                   (unsigned long long)(e1 - e0));
+        top = max(top, mex);
+        __syncwarp();
+    }
+    if (lane == 0 && top >= 0) atomicMax(st.max_color, top);
+}
+
+// The rest of the core, ranks [r1, k), on the whole grid: warp w of the W
+// takes ranks r1 + w, r1 + w + W, ...; colours are read from and written to
+// rc (by rank) in L2.
 __global__ void __launch_bounds__(kCoreBlock) jp_core_kernel(const int32_t *__restrict__ order,
                                                              const int32_t *__restrict__ hoff,
                                                              const int32_t *__restrict__ hcol,
-                                                             int k, JpState st) {
+                                                             int k, int32_t *rc,
+                                                             const int32_t *__restrict__ r1_in,
+                                                             JpState st) {
     __shared__ unsigned bm[kCoreWarps][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nw = gridDim.x * kCoreWarps;
+    const int r1 = *r1_in;
     int top = -1;
-    for (int r = blockIdx.x * kCoreWarps + wib; r < k; r += nw) {
-        const int v = order[r], e0 = hoff[r], e1 = hoff[r + 1];
+    for (int r = r1 + blockIdx.x * kCoreWarps + wib; r < k; r += nw) {
+        const int e0 = hoff[r], e1 = hoff[r + 1];
         bm[wib][lane] = 0u;
         __syncwarp();
         bool fail = false;
@@ -721,11 +908,16 @@ __global__ void __launch_bounds__(kCoreBlock) jp_core_kernel(const int32_t *__re
                 u[q] = e < e1 ? __ldg(&hcol[e]) : -1;
             }
 #pragma unroll
-            for (int q = 0; q < kCoreU; ++q) c[q] = u[q] >= 0 ? ld_relaxed_i32(&st.color[u[q]]) : 0;
+            for (int q = 0; q < kCoreU; ++q) {  // a rank not below r: inconsistent lists
+                if (u[q] >= r) fail = true;
+                if (u[q] >= r) u[q] = -1;
+            }
+#pragma unroll
+            for (int q = 0; q < kCoreU; ++q) c[q] = u[q] >= 0 ? ld_relaxed_i32(&rc[u[q]]) : 0;
 #pragma unroll
             for (int q = 0; q < kCoreU; ++q) {
                 if (u[q] < 0) continue;
-                if (c[q] < 0) c[q] = core_wait(&st.color[u[q]], st.bar);
+                if (c[q] < 0) c[q] = core_wait(&rc[u[q]], st.bar);
                 if (c[q] < 0) fail = true;
                 else if (c[q] < kMexWindow) atomicOr(&bm[wib][c[q] >> 5], 1u << (c[q] & 31));
             }
@@ -738,8 +930,14 @@ __global__ void __launch_bounds__(kCoreBlock) jp_core_kernel(const int32_t *__re
         __syncwarp();
         const unsigned w0 = bm[wib][lane];
         __syncwarp();
-        const int mex = core_mex(hcol, e0, e1, st.color, w0, bm[wib]);
-        if (lane == 0) st_relaxed_i32(&st.color[v], mex);
+        const int mex = core_mex(hcol, e0, e1, rc, w0, bm[wib]);
+        if (lane == 0) {
+            st_relaxed_i32(&rc[r], mex);
+            __stcg(&st.color[order[r]], mex);
+        }
+        if (LV_TRACE_ON && lane == 0 && (r & 15) == 0)
+            trace4(st.tb, 0xB00000000ull, (unsigned long long)r, gtimer(),
+                   (unsigned long long)(e1 - e0));
         top = max(top, mex);
         __syncwarp();
     }
@@ -754,7 +952,8 @@ lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int
                     const JpState &st, int *pinned, cudaStream_t s, int sms) {
     uint64_t *keys = nullptr, *keys_alt = nullptr;
     uint32_t *vals = nullptr, *vals_alt = nullptr, *dkeys = nullptr, *dkeys_alt = nullptr;
-    int32_t *count = nullptr, *hoff = nullptr, *hcol = nullptr;
+    int32_t *count = nullptr, *hoff = nullptr, *hcol = nullptr, *rank_of = nullptr, *rc = nullptr;
+    int32_t *r1 = nullptr;
     LV_TRY(dalloc_n(&keys, (size_t)k, s));
     LV_TRY(dalloc_n(&keys_alt, (size_t)k, s));
     LV_TRY(dalloc_n(&vals, (size_t)k, s));
@@ -771,6 +970,7 @@ lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int
     core_dkey_kernel<<<grid_for(k, 256, g_num_sms * 4), 256, 0, s>>>(vals, d, k, dkeys);
     LV_LAUNCH_CHECK();
     LV_TRY(radix_sort_u32(dkeys, vals, dkeys_alt, vals_alt, k, 32, s));
+    trace_stamp(s, 4);
     const int32_t *order = reinterpret_cast<const int32_t *>(vals);
     gather_at_kernel<<<grid_for(k, 256, g_num_sms * 4), 256, 0, s>>>(st.cnt, order, k, hoff);
     LV_LAUNCH_CHECK();
@@ -779,20 +979,35 @@ lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int
     LV_CUDA(cudaStreamSynchronize(s));
     const int total = pinned[0];
     LV_TRY(dalloc_n(&hcol, (size_t)total + 1, s));
-    core_lists_kernel<<<grid_for(k, 8, g_num_sms * 16), 256, 0, s>>>(g, order, k, hoff, st.hb,
-                                                                     hcol);
+    LV_TRY(dalloc_n(&rank_of, (size_t)g.n, s));
+    LV_TRY(dalloc_n(&rc, (size_t)k, s));
+    LV_TRY(dalloc_n(&r1, 1, s));
+    LV_CUDA(cudaMemsetAsync(rc, 0xff, sizeof(int32_t) * (size_t)k, s));  // -1: not coloured
+    core_rank_kernel<<<grid_for(k, 256, g_num_sms * 4), 256, 0, s>>>(order, k, rank_of);
     LV_LAUNCH_CHECK();
+    trace_stamp(s, 5);
+    core_lists_kernel<<<grid_for(k, 8, g_num_sms * 16), 256, 0, s>>>(g, order, k, hoff, st.hb,
+                                                                     rank_of, hcol);
+    LV_LAUNCH_CHECK();
+    trace_stamp(s, 6);
     static int core_bps = 0;
     if (!core_bps) {
+        LV_CUDA(cudaFuncSetAttribute(jp_core_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kTopMax * (int)sizeof(int)));
         LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&core_bps, jp_core_kernel,
                                                               kCoreBlock, 0));
         if (core_bps < 1) return LV_ERR_CUDA;
     }
+    jp_core_top_kernel<<<1, kTopThreads, kTopMax * sizeof(int), s>>>(order, hoff, hcol, k, rc, r1,
+                                                                     st);
+    LV_LAUNCH_CHECK();
+    trace_stamp(s, 13);
     const int grid = (sms > 0 && sms < g_num_sms ? sms : g_num_sms) * core_bps;
     JpState sarg = st;
-    const int32_t *hoff_c = hoff, *hcol_c = hcol;
+    const int32_t *hoff_c = hoff, *hcol_c = hcol, *r1_c = r1;
+    int32_t *rc_c = rc;
     int karg = k;
-    void *args[] = {&order, &hoff_c, &hcol_c, &karg, &sarg};
+    void *args[] = {&order, &hoff_c, &hcol_c, &karg, &rc_c, &r1_c, &sarg};
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_core_kernel, dim3(grid), dim3(kCoreBlock), args,
                                         0, s));
     LV_LAUNCH_CHECK();
@@ -805,6 +1020,9 @@ lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int
     dfree(count, s);
     dfree(hoff, s);
     dfree(hcol, s);
+    dfree(rank_of, s);
+    dfree(rc, s);
+    dfree(r1, s);
     return LV_OK;
 }
 
@@ -849,6 +1067,7 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
     // the core: the smallest T = 2^b >= 64 with at most kCoreMax vertices of
     // degree >= T (none without the degree in the priority)
     int core_t = INT_MAX, core_k = 0;
+    trace_stamp(s, 1);
     if (degree_first) {
         int32_t *hist = nullptr;
         LV_TRY(dalloc_n(&hist, 32, s));
@@ -870,9 +1089,15 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
                 break;
             }
     }
+    trace_stamp(s, 2);
     jp_init_kernel<<<grid_for(n, 8, g_num_sms * 16), 256, 0, s>>>(g, seed, d, core_t, hb, st);
     LV_LAUNCH_CHECK();
+    jp_round0_kernel<<<grid_for(n, 256 * kR0PerThread, g_num_sms * 8), 256, 0, s>>>(g, d, core_t,
+                                                                                     st);
+    LV_LAUNCH_CHECK();
+    trace_stamp(s, 3);
     if (core_k > 0) LV_TRY(core_pass(g, seed, d, core_k, core_t, st, pinned, s, sms));
+    trace_stamp(s, 7);
     static int blocks_per_sm = 0;
     const int stage_bytes = (int)sizeof(JpStage);
     if (!blocks_per_sm) {
@@ -889,6 +1114,7 @@ lv_status jp_color(const DGraph &g, uint64_t seed, bool degree_first, int32_t *c
     LV_CUDA(cudaLaunchCooperativeKernel((void *)jp_persistent_kernel, dim3(grid),
                                         dim3(kJpBlock), args, stage_bytes, s));
     LV_LAUNCH_CHECK();
+    trace_stamp(s, 8);
     LV_CUDA(cudaMemcpyAsync(pinned, small_state + 13, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost,
                             s));
     LV_CUDA(cudaStreamSynchronize(s));
@@ -914,6 +1140,7 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     const int n = g.n;
     const int nb = classes * (kBins + 1);
     b->classes = classes;
+    trace_stamp(s, 9);
     uint32_t *keys = nullptr, *keys_alt = nullptr, *vals_alt = nullptr;
     LV_TRY(dalloc_n(&keys, (size_t)n, s));
     LV_TRY(dalloc_n(&keys_alt, (size_t)n, s));
@@ -957,7 +1184,9 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
         LV_CUDA(cudaStreamSynchronize(s));
         return LV_OK;
     };
+    trace_stamp(s, 10);
     LV_TRY(size_hubs());
+    trace_stamp(s, 11);
     // classes whose hubs have more chunks than the sweep grid has blocks take
     // chunks twice as long: half the block items and global-table merges
     {
@@ -992,6 +1221,7 @@ lv_status bucket_vertices(const DGraph &g, const int32_t *color, int32_t classes
     dfree(keys, s);
     dfree(keys_alt, s);
     dfree(vals_alt, s);
+    trace_stamp(s, 12);
     return LV_OK;
 }
 

@@ -245,6 +245,13 @@ struct TraceBuf {
 #endif
 TraceBuf trace_buffer();  // the process-wide buffer (null unless LV_TRACE)
 constexpr unsigned kTraceCap = 1u << 20;
+// host side: record {0xA << 32 | tag, device time} on stream s when it gets
+// there (profiling builds; nothing otherwise)
+#ifdef LV_TRACE
+void trace_stamp(cudaStream_t s, unsigned tag);
+#else
+inline void trace_stamp(cudaStream_t, unsigned) {}
+#endif
 __device__ __forceinline__ unsigned long long gtimer() {
 #ifdef LV_TRACE
     unsigned long long t;

@@ -308,6 +308,14 @@ lv_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uin
 extern "C" const char *lv_last_error(void) { return lv::t_last_error; }
 
 #ifdef LV_TRACE
+namespace lv {
+namespace {
+__global__ void trace_stamp_kernel(TraceBuf tb, unsigned tag) {
+    trace4(tb, 0xA00000000ull | tag, gtimer(), 0, 0);
+}
+}  // namespace
+void trace_stamp(cudaStream_t s, unsigned tag) { trace_stamp_kernel<<<1, 1, 0, s>>>(trace_buffer(), tag); }
+}  // namespace lv
 // profiling builds only: read and reset the stage timestamps
 extern "C" int lv_trace_read(unsigned long long *out, int max) {
     lv::TraceBuf tb = lv::trace_buffer();
