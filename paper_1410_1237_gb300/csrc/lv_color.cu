@@ -769,8 +769,56 @@ __device__ int core_mex(const int32_t *__restrict__ hcol, int e0, int e1, const 
     }
 }
 
+// The top of the core (ranks [0, r1), r1 <= kTopMax with at most kTopEntries
+// list entries) on one thread-block cluster: the deepest priority chains
+// run through the largest hubs, and there a colour reaches the warps
+// waiting for it through shared memory: every block of the cluster keeps
+// all of the top's colours, and the warp that colours a rank stores the
+// colour into each block's copy (distributed shared memory), so a wait is a
+// poll of the block's own shared memory.  Warp w of the cluster's W takes
+// ranks w, w + W, ...; colours also go to rc (by rank) and to the vertex.
+// Blocks do not return early (a failing warp stops working and flags the
+// error), and a cluster barrier at the end keeps every block's shared
+// memory alive until the last store into it.
+constexpr int kTopThreads = 1024;
+constexpr int kTopWarps = kTopThreads / 32;
+constexpr int kTopMax = 40960;                     // ranks at most
+constexpr int kTopEntries = 1 << 24;               // list entries at most
+constexpr int kTopU = 8;                           // 32-entry chunks in flight per warp
+constexpr unsigned kTopSpinLimit = 1u << 24;       // polls of one colour, x >= 20 ns sleeps
+constexpr int kTopMaxCluster = 16;
+constexpr int kTopPend = 256;                      // ranks a warp sets aside to wait for
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_blocks() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// *p of block `cta` of the cluster (p: this block's copy) = v
+__device__ __forceinline__ void st_cluster_i32(const int *p, unsigned cta, int v) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(cta));
+    asm volatile("st.relaxed.cluster.shared::cluster.b32 [%0], %1;" ::"r"(ra), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_cluster_local_i32(const int *p) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    int v;
+    asm volatile("ld.relaxed.cluster.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
 // smallest colour absent from the ranks listed in [e0, e1) (all coloured,
-// colours in shared memory) whose first window is held in word0
+// colours in this block's shared memory) whose first window is in word0
 __device__ int core_mex_smem(const int32_t *__restrict__ hcol, int e0, int e1, const int *sc,
                              unsigned word0, unsigned *scratch32) {
     const int lane = threadIdx.x & 31;
@@ -786,7 +834,7 @@ __device__ int core_mex_smem(const int32_t *__restrict__ hcol, int e0, int e1, c
         scratch32[lane] = 0u;
         __syncwarp();
         for (int e = e0 + lane; e < e1; e += 32) {
-            const int c = ((const volatile int *)sc)[hcol[e]] - nb;
+            const int c = ld_cluster_local_i32(&sc[hcol[e]]) - nb;
             if (c >= 0 && c < kMexWindow) atomicOr(&scratch32[c >> 5], 1u << (c & 31));
         }
         __syncwarp();
@@ -795,25 +843,15 @@ __device__ int core_mex_smem(const int32_t *__restrict__ hcol, int e0, int e1, c
     }
 }
 
-// The top of the core (ranks [0, r1), r1 <= kTopMax with at most kTopEntries
-// list entries) on one block: the deepest priority chains run through the
-// largest hubs, and there a colour reaches the warps waiting for it through
-// shared memory (a wait of a few hundred nanoseconds instead of a round trip
-// to L2 per link).  Warp w takes ranks w, w + 32, ...; colours go to shared
-// memory, to rc (by rank) and to the vertex.
-constexpr int kTopThreads = 1024;
-constexpr int kTopWarps = kTopThreads / 32;
-constexpr int kTopMax = 40960;                     // ranks at most
-constexpr int kTopEntries = 1 << 24;               // list entries at most
-constexpr int kTopU = 8;                           // 32-entry chunks in flight per warp
-constexpr unsigned kTopSpinLimit = 1u << 24;       // polls of one colour, x >= 20 ns sleeps
 __global__ void __launch_bounds__(kTopThreads) jp_core_top_kernel(
     const int32_t *__restrict__ order, const int32_t *__restrict__ hoff,
     const int32_t *__restrict__ hcol, int k, int32_t *rc, int32_t *r1_out, JpState st) {
     extern __shared__ int sc[];  // colours of ranks [0, r1)
     __shared__ unsigned bm[kTopWarps][32];
+    __shared__ int pend[kTopWarps][kTopPend];
     __shared__ int s_r1;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned crank = cluster_rank(), nblocks = cluster_blocks();
     if (threadIdx.x == 0) {  // largest r1 <= min(k, kTopMax) with hoff[r1] <= kTopEntries
         int lo = 0, hi = min(k, kTopMax);
         while (lo < hi) {
@@ -821,54 +859,95 @@ __global__ void __launch_bounds__(kTopThreads) jp_core_top_kernel(
             if (hoff[mid] <= kTopEntries) lo = mid; else hi = mid - 1;
         }
         s_r1 = lo;
-        *r1_out = lo;
+        if (crank == 0) *r1_out = lo;
     }
     __syncthreads();
     const int r1 = s_r1;
     for (int i = threadIdx.x; i < r1; i += kTopThreads) sc[i] = -1;
-    __syncthreads();
-    volatile int *vsc = sc;
+    cluster_barrier();  // every copy initialised before the first remote store
+    const int nw = (int)nblocks * kTopWarps;
     int top = -1;
-    for (int r = wib; r < r1; r += kTopWarps) {
+    bool fail = false;
+    for (int r = (int)crank * kTopWarps + wib; r < r1 && !fail; r += nw) {
         const int e0 = hoff[r], e1 = hoff[r + 1];
         bm[wib][lane] = 0u;
         __syncwarp();
-        bool fail = false;
-        for (int b = e0; b < e1; b += 32 * kTopU) {
+        // pass 1: the ranks already coloured are marked, the others set
+        // aside; pass 2 polls those together, so that once the last of them
+        // is coloured only shared-memory work is left (the chain of waits
+        // runs through that step)
+        int npend = 0;
+        for (int b = e0; b < e1 && !fail; b += 32 * kTopU) {
             int x[kTopU];
 #pragma unroll
             for (int q = 0; q < kTopU; ++q) {
                 const int e = b + q * 32 + lane;
                 x[q] = e < e1 ? __ldg(&hcol[e]) : -1;
             }
+            bool bad = false;
 #pragma unroll
             for (int q = 0; q < kTopU; ++q) {
-                if (x[q] < 0) continue;
                 if (x[q] >= r) {  // not an earlier rank: the lists are inconsistent
-                    fail = true;
+                    bad = true;
+                    x[q] = -1;
+                }
+                const int c = x[q] >= 0 ? ld_cluster_local_i32(&sc[x[q]]) : 0;
+                const bool wait = x[q] >= 0 && c < 0;
+                const unsigned m = __ballot_sync(0xffffffffu, wait);
+                bool parked = false;
+                if (m && npend + __popc(m) <= kTopPend) {
+                    if (wait) pend[wib][npend + __popc(m & ((1u << lane) - 1u))] = x[q];
+                    npend += __popc(m);
+                    parked = wait;
+                }
+                int cc = c;
+                for (unsigned spins = 1; wait && !parked && cc < 0; ++spins) {  // no room: wait now
+                    if (spins > kTopSpinLimit) break;
+                    __nanosleep(20);
+                    cc = ld_cluster_local_i32(&sc[x[q]]);
+                }
+                if (x[q] < 0 || parked) continue;
+                if (cc < 0) bad = true;
+                else if (cc < kMexWindow) atomicOr(&bm[wib][cc >> 5], 1u << (cc & 31));
+            }
+            fail = __any_sync(0xffffffffu, bad);
+        }
+        __syncwarp();
+        for (unsigned spins = 1; npend > 0 && !fail; ++spins) {
+            bool left = false;
+            for (int t = lane; t < npend; t += 32) {
+                const int x = pend[wib][t];
+                if (x < 0) continue;
+                const int c = ld_cluster_local_i32(&sc[x]);
+                if (c < 0) {
+                    left = true;
                     continue;
                 }
-                int c = vsc[x[q]];
-                for (unsigned spins = 0; c < 0;) {  // an earlier rank still running
-                    if (++spins > kTopSpinLimit) break;
-                    __nanosleep(20);
-                    c = vsc[x[q]];
-                }
-                if (c < 0) fail = true;
-                else if (c < kMexWindow) atomicOr(&bm[wib][c >> 5], 1u << (c & 31));
+                if (c < kMexWindow) atomicOr(&bm[wib][c >> 5], 1u << (c & 31));
+                pend[wib][t] = -1;
             }
-            if (__any_sync(0xffffffffu, fail)) break;
+            if (!__any_sync(0xffffffffu, left)) break;
+            bool stop = spins > kTopSpinLimit;
+            if ((spins & 255u) == 0u) {
+                unsigned long long w = 0;
+                if (lane == 0)
+                    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];"
+                                 : "=l"(w) : "l"(&st.bar->word) : "memory");
+                stop |= (__shfl_sync(0xffffffffu, w, 0) >> kBarrierFlagShift) != 0;
+            }
+            fail = stop;
+            if (!stop) __nanosleep(20);
         }
-        if (__any_sync(0xffffffffu, fail)) {  // warp-uniform: give up, flag the error
+        if (fail) {  // warp-uniform: stop, flag the error
             if (lane == 0) barrier_raise(st.bar, 1);
-            return;
+            break;
         }
         __syncwarp();
         const unsigned w0 = bm[wib][lane];
         __syncwarp();
         const int mex = core_mex_smem(hcol, e0, e1, sc, w0, bm[wib]);
+        if (lane < (int)nblocks) st_cluster_i32(&sc[r], (unsigned)lane, mex);
         if (lane == 0) {
-            vsc[r] = mex;
             rc[r] = mex;
             __stcg(&st.color[order[r]], mex);
         }
@@ -879,6 +958,7 @@ __global__ void __launch_bounds__(kTopThreads) jp_core_top_kernel(
         __syncwarp();
     }
     if (lane == 0 && top >= 0) atomicMax(st.max_color, top);
+    cluster_barrier();  // no block leaves while stores into its copy may follow
 }
 
 // The rest of the core, ranks [r1, k), on the whole grid: warp w of the W
@@ -990,17 +1070,54 @@ lv_status core_pass(const DGraph &g, uint64_t seed, const int32_t *d, int k, int
                                                                      rank_of, hcol);
     LV_LAUNCH_CHECK();
     trace_stamp(s, 6);
-    static int core_bps = 0;
+    static int core_bps = 0, top_cluster = 0;
+    const int top_smem = kTopMax * (int)sizeof(int);
     if (!core_bps) {
         LV_CUDA(cudaFuncSetAttribute(jp_core_top_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kTopMax * (int)sizeof(int)));
+                                     top_smem));
+        LV_CUDA(cudaFuncSetAttribute(jp_core_top_kernel,
+                                     cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        // the largest cluster (up to kTopMaxCluster blocks) that fits
+        for (int c = kTopMaxCluster; c >= 1 && !top_cluster; c >>= 1) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3(c);
+            q.blockDim = dim3(kTopThreads);
+            q.dynamicSmemBytes = top_smem;
+            cudaLaunchAttribute qa[1];
+            qa[0].id = cudaLaunchAttributeClusterDimension;
+            qa[0].val.clusterDim.x = c;
+            qa[0].val.clusterDim.y = 1;
+            qa[0].val.clusterDim.z = 1;
+            q.attrs = qa;
+            q.numAttrs = 1;
+            int fit = 0;
+            if (cudaOccupancyMaxActiveClusters(&fit, jp_core_top_kernel, &q) == cudaSuccess && fit >= 1)
+                top_cluster = c;
+            else
+                cudaGetLastError();
+        }
+        if (!top_cluster) return LV_ERR_CUDA;
         LV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&core_bps, jp_core_kernel,
                                                               kCoreBlock, 0));
         if (core_bps < 1) return LV_ERR_CUDA;
     }
-    jp_core_top_kernel<<<1, kTopThreads, kTopMax * sizeof(int), s>>>(order, hoff, hcol, k, rc, r1,
-                                                                     st);
-    LV_LAUNCH_CHECK();
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(top_cluster);
+        cfg.blockDim = dim3(kTopThreads);
+        cfg.dynamicSmemBytes = top_smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = top_cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const int32_t *hoff_t = hoff, *hcol_t = hcol;
+        LV_CUDA(cudaLaunchKernelEx(&cfg, jp_core_top_kernel, order, hoff_t, hcol_t, k, rc, r1, st));
+        LV_LAUNCH_CHECK();
+    }
     trace_stamp(s, 13);
     const int grid = (sms > 0 && sms < g_num_sms ? sms : g_num_sms) * core_bps;
     JpState sarg = st;
