@@ -72,12 +72,10 @@ __device__ __forceinline__ bool higher_arc(const JpState &st, int e) {
 // barrier).  A push that does not fit goes straight to the global list.
 // Without it, every warp's push was a global atomic on the same four
 // counters, which serialised the rounds that release 10^5 vertices.
-constexpr int kJpStage = 512;  // entries per kind
-constexpr int kJpStageMinReady = 8192;  // ready vertices from which a round stages
+constexpr int kJpWB = 32;  // entries per warp and kind (small, tiny)
 struct JpStage {
-    int cnt[kJpKinds];
-    int base[kJpKinds];
-    int4 q[kJpKinds][kJpStage];
+    int n[kJpWarps][2];
+    int4 q[kJpWarps][2][kJpWB];
 };
 
 // append u (arcs [beg, end)) to the next round's list of its kind;
@@ -98,23 +96,26 @@ __device__ __forceinline__ void push_ready(const JpState &st, int32_t *cnt_next,
         const unsigned bm = __ballot_sync(0xffffffffu, mine);
         if (bm) {
             const int c = __popc(bm);
-            int pos = -1;
-            if (lane == 0 && stg) {  // reserve in the stage only if all c fit
-                int old = ((volatile int *)stg->cnt)[k];
-                while (old + c <= kJpStage) {
-                    const int prev = atomicCAS(&stg->cnt[k], old, old + c);
-                    if (prev == old) {
-                        pos = old;
-                        break;
-                    }
-                    old = prev;
+            const int slot = k == 0 ? 0 : (k == 3 ? 1 : -1);
+            if (stg && slot >= 0) {  // the warp's own buffer, written out when full
+                const int w = threadIdx.x >> 5;
+                int n0 = ((volatile int *)stg->n[w])[slot];
+                if (n0 + c > kJpWB) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&cnt_next[k], n0);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    for (int t = lane; t < n0; t += 32)
+                        st.list[k][nxt_list][base + t] = stg->q[w][slot][t];
+                    n0 = 0;
+                    __syncwarp();
                 }
-            }
-            pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (pos >= 0) {
-                if (mine) stg->q[k][pos + __popc(bm & lt)] = make_int4(u, beg, end, 0);
+                if (mine) stg->q[w][slot][n0 + __popc(bm & lt)] = make_int4(u, beg, end, 0);
+                __syncwarp();
+                if (lane == 0) stg->n[w][slot] = n0 + c;
+                __syncwarp();
                 continue;
             }
+            int pos = 0;
             if (lane == 0) pos = atomicAdd(&cnt_next[k], c);
             pos = __shfl_sync(0xffffffffu, pos, 0);
             if (mine) st.list[k][nxt_list][pos + __popc(bm & lt)] = make_int4(u, beg, end, 0);
@@ -373,33 +374,6 @@ __global__ void __launch_bounds__(256) jp_round0_kernel(DGraph g, const int32_t 
     }
 }
 
-// Appends the block's staged entries to the global lists (one global
-// atomic per kind) and empties the stage.  Called by the whole block at a
-// block-uniform point; `more` = pushes follow before the next grid barrier
-// (which otherwise orders the emptied stage before the next round's pushes).
-__device__ void jp_flush(const JpState &st, JpStage *stg, int32_t *cnt_next, int nxt_list,
-                         bool more) {
-    __syncthreads();
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < kJpKinds; ++k) any |= stg->cnt[k] > 0;
-    if (!any) return;  // block-uniform: every thread read the same counts
-    __syncthreads();   // every thread has read the counts before they change
-    if (threadIdx.x < kJpKinds) {
-        const int c = stg->cnt[threadIdx.x];
-        stg->base[threadIdx.x] = c ? atomicAdd(&cnt_next[threadIdx.x], c) : 0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kJpKinds; ++k) {
-        const int c = stg->cnt[k], b = stg->base[k];
-        for (int t = threadIdx.x; t < c; t += blockDim.x) st.list[k][nxt_list][b + t] = stg->q[k][t];
-    }
-    __syncthreads();
-    if (threadIdx.x < kJpKinds) stg->cnt[threadIdx.x] = 0;
-    if (more) __syncthreads();
-}
-
 // All rounds of Jones-Plassmann in one cooperative launch.  Round r colours
 // the vertices queued in round r - 1, in units of one block each:
 //   huge  split over P blocks each, which mark a global bitmap and release
@@ -416,7 +390,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
     extern __shared__ int4 jp_dyn[];
     JpStage *stg = reinterpret_cast<JpStage *>(jp_dyn);
     __shared__ int s_abort;
-    if (threadIdx.x < kJpKinds) stg->cnt[threadIdx.x] = 0;
+    if (threadIdx.x < kJpWarps * 2) (&stg->n[0][0])[threadIdx.x] = 0;
     if (threadIdx.x == 0) {  // the core pass failed: its colours are incomplete
         unsigned long long w;
         asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(&st.bar->word) : "memory");
@@ -448,7 +422,7 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
         const int units = huge_units + n_big + small_units + tiny_units;
         // heavy rounds stage their pushes in the block; light ones (the long
         // tail of the priority DAG) push straight to the global lists
-        JpStage *rs = n_small + n_tiny + n_big >= kJpStageMinReady ? stg : nullptr;
+        JpStage *rs = stg;
         for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
             if (unit < huge_units) {
                 const int t = unit % n_huge, part = unit / n_huge;
@@ -507,15 +481,20 @@ __global__ void __launch_bounds__(kJpBlock) jp_persistent_kernel(DGraph g, JpSta
                     __syncwarp();
                 }
             }
-            if (rs && unit + (int)gridDim.x < units) {  // block-uniform: more units follow
-                __syncthreads();
-                bool half = false;
-#pragma unroll
-                for (int k = 0; k < kJpKinds; ++k) half |= stg->cnt[k] > kJpStage / 2;
-                if (half) jp_flush(st, stg, cnt_next, out_list, true);
+        }
+        for (int slot = 0; slot < 2; ++slot) {  // the warp's last entries of the round
+            const int k = slot ? 3 : 0;
+            const int n0 = stg->n[wib][slot];
+            if (n0) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&cnt_next[k], n0);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                for (int t = lane; t < n0; t += 32) st.list[k][out_list][base + t] = stg->q[wib][slot][t];
+                __syncwarp();
+                if (lane == 0) stg->n[wib][slot] = 0;
+                __syncwarp();
             }
         }
-        if (rs) jp_flush(st, stg, cnt_next, out_list, false);  // the round's last entries
         const unsigned long long tr1 = LV_TRACE_ON ? gtimer() : 0;
         if (LV_TRACE_ON && threadIdx.x == 0 && blockIdx.x < 8)
             trace4(st.tb, 0x100000000ull | (unsigned)r, (unsigned long long)blockIdx.x, tr0, tr1);

@@ -244,13 +244,16 @@ struct TraceBuf {
 #define LV_TRACE_ON 0
 #endif
 TraceBuf trace_buffer();  // the process-wide buffer (null unless LV_TRACE)
-constexpr unsigned kTraceCap = 1u << 20;
-// host side: record {0xA << 32 | tag, device time} on stream s when it gets
-// there (profiling builds; nothing otherwise)
+#ifndef LV_TRACE_CAP
+#define LV_TRACE_CAP (1u << 20)
+#endif
+constexpr unsigned kTraceCap = LV_TRACE_CAP;  // 64-bit words
+// host side: record {0xA << 32 | tag, device time, val} on stream s when it
+// gets there (profiling builds; nothing otherwise)
 #ifdef LV_TRACE
-void trace_stamp(cudaStream_t s, unsigned tag);
+void trace_stamp(cudaStream_t s, unsigned tag, unsigned long long val = 0);
 #else
-inline void trace_stamp(cudaStream_t, unsigned) {}
+inline void trace_stamp(cudaStream_t, unsigned, unsigned long long = 0) {}
 #endif
 __device__ __forceinline__ unsigned long long gtimer() {
 #ifdef LV_TRACE

@@ -310,11 +310,13 @@ extern "C" const char *lv_last_error(void) { return lv::t_last_error; }
 #ifdef LV_TRACE
 namespace lv {
 namespace {
-__global__ void trace_stamp_kernel(TraceBuf tb, unsigned tag) {
-    trace4(tb, 0xA00000000ull | tag, gtimer(), 0, 0);
+__global__ void trace_stamp_kernel(TraceBuf tb, unsigned tag, unsigned long long val) {
+    trace4(tb, 0xA00000000ull | tag, gtimer(), val, 0);
 }
 }  // namespace
-void trace_stamp(cudaStream_t s, unsigned tag) { trace_stamp_kernel<<<1, 1, 0, s>>>(trace_buffer(), tag); }
+void trace_stamp(cudaStream_t s, unsigned tag, unsigned long long val) {
+    trace_stamp_kernel<<<1, 1, 0, s>>>(trace_buffer(), tag, val);
+}
 }  // namespace lv
 // profiling builds only: read and reset the stage timestamps
 extern "C" int lv_trace_read(unsigned long long *out, int max) {

@@ -350,60 +350,119 @@ __global__ void fail_arcs_kernel(int n_next, const int32_t *__restrict__ ga,
 }
 
 // Communities left to the sort: their arcs as keys (c << b | c(v)) with
-// weights, pre-summed per block.  A block takes kAggArcs consecutive arcs of
-// the list's concatenated rows (the community of an arc by a search of the
-// list's arc starts lstart), sums equal keys in a shared-memory table, and
-// appends each distinct key once (at a position reserved with one atomic
-// per block), so the sort sees the distinct (community, neighbour) pairs of
-// each chunk instead of every arc.
+// weights, pre-summed per block.  A block takes a chunk of kAggArcs
+// consecutive arcs of one community (chunks numbered over the listed
+// communities: coff holds the first chunk of each, coff[n_list] the total),
+// finds the members holding the chunk's first and last arcs, loads those
+// members' arc starts into shared memory and maps each arc to its member by
+// a search there (not over all of the community's members in global
+// memory).  It sums equal keys in a shared-memory table and appends each
+// distinct key once (at a position reserved with one atomic per block), so
+// the sort sees the distinct (community, neighbour) pairs of each chunk
+// instead of every arc.
 constexpr int kAggArcs = 4096;
 constexpr int kAggSlots = 2 * kAggArcs;
 constexpr int kAggThreads = 512;
-constexpr size_t kAggSmem = kAggSlots * (sizeof(unsigned long long) + sizeof(unsigned));
+constexpr size_t kAggSmem =
+    kAggSlots * (sizeof(unsigned long long) + sizeof(unsigned)) + (kAggArcs + 1) * sizeof(int);
+
+// chunks of kAggArcs arcs of each listed community
+__global__ void agg_chunks_kernel(int n_list, const int32_t *__restrict__ list,
+                                  const int32_t *__restrict__ ga, int32_t *chunks) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_list; i += gridDim.x * blockDim.x) {
+        const int c = list[i];
+        chunks[i] = (ga[c + 1] - ga[c] + kAggArcs - 1) / kAggArcs;
+    }
+}
+
 __global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
-    DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ lstart,
-    int AL, const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
+    DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ coff,
+    const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
     const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm,
     int b, uint64_t *keys, uint32_t *vals, int32_t *n_out, int *err) {
     extern __shared__ unsigned long long agg[];
     unsigned long long *K = agg;
     unsigned *V = reinterpret_cast<unsigned *>(agg + kAggSlots);
-    __shared__ int s_cnt, s_base;
+    int *mo = reinterpret_cast<int *>(V + kAggSlots);  // arc starts of the chunk's members
+    __shared__ int s_cnt, s_base, s_c, s_p0, s_p1, s_m0, s_nm;
     constexpr int kPer = kAggSlots / kAggThreads;
     constexpr unsigned long long kNone = ~0ull;  // keys are below 2^62
-    for (int64_t c0 = (int64_t)blockIdx.x * kAggArcs; c0 < AL; c0 += (int64_t)gridDim.x * kAggArcs) {
-        for (int sl = threadIdx.x; sl < kAggSlots; sl += kAggThreads) {
+    const int n_chunks = coff[n_list];
+    for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_list;  // coff[lo] <= chunk < coff[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (coff[mid] <= chunk) lo = mid; else hi = mid;
+            }
+            const int c = list[lo], a0 = ga[c];
+            const int p0 = a0 + (chunk - coff[lo]) * kAggArcs;
+            const int p1 = min(ga[c + 1], p0 + kAggArcs);
+            // members holding arc positions p0 and p1 - 1 (apos[m] <= p < apos[m + 1])
+            int m[2];
+            for (int q = 0; q < 2; ++q) {
+                const int p = q ? p1 - 1 : p0;
+                int l = gs[c], h = gs[c + 1];
+                while (h - l > 1) {
+                    const int mid = (l + h) >> 1;
+                    if (apos[mid] <= p) l = mid; else h = mid;
+                }
+                m[q] = l;
+            }
+            s_c = c;
+            s_p0 = p0;
+            s_p1 = p1;
+            s_m0 = m[0];
+            s_nm = m[1] + 1 - m[0];
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int c = s_c, p0 = s_p0, p1 = s_p1, m0 = s_m0, nm = s_nm;
+        // table: the next power of two >= 2x the chunk's arcs (a short last
+        // chunk clears and scans only that much)
+        int tsz = kAggThreads;
+        while (tsz < 2 * (p1 - p0)) tsz <<= 1;
+        const unsigned tmask = (unsigned)tsz - 1u;
+        for (int sl = threadIdx.x; sl < tsz; sl += kAggThreads) {
             K[sl] = kNone;
             V[sl] = 0u;
         }
-        if (threadIdx.x == 0) s_cnt = 0;
+        const bool local = nm <= kAggArcs;  // else members without arcs: search globally
+        if (local)
+            for (int t = threadIdx.x; t <= nm; t += kAggThreads) mo[t] = apos[m0 + t];
         __syncthreads();
-        const int e1 = (int)(c0 + kAggArcs < AL ? c0 + kAggArcs : AL);
-        for (int e = (int)c0 + threadIdx.x; e < e1; e += kAggThreads) {
-            int lo = 0, hi = n_list;  // lstart[lo] <= e < lstart[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (lstart[mid] <= e) lo = mid; else hi = mid;
+        for (int p = p0 + threadIdx.x; p < p1; p += kAggThreads) {
+            int2 a;
+            if (local) {
+                int lo = 0, hi = nm;  // mo[lo] <= p < mo[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (mo[mid] <= p) lo = mid; else hi = mid;
+                }
+                const int u = (int)vo[m0 + lo];
+                a = g.arcs[g.off[u] + (p - mo[lo])];
+            } else {
+                a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], p - ga[c]);
             }
-            const int c = list[lo];
-            const int2 a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], e - lstart[lo]);
             const unsigned long long key = ((unsigned long long)c << b) | cm[a.x];
-            unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kAggSlots - 1);
+            unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & tmask;
             bool done = false;
-            for (int probe = 0; probe < kAggSlots && !done; ++probe) {
+            for (int probe = 0; probe < tsz && !done; ++probe) {
                 const unsigned long long prev = atomicCAS(&K[h], kNone, key);
                 if (prev == kNone || prev == key) {
                     atomicAdd(&V[h], (unsigned)a.y);
                     done = true;
                 }
-                h = (h + 1) & (kAggSlots - 1);
+                h = (h + 1) & tmask;
             }
-            if (!done) atomicExch(err, 1);  // cannot happen: kAggArcs keys, 2x the slots
+            if (!done) atomicExch(err, 1);  // cannot happen: 2x the slots of the keys
         }
         __syncthreads();
+        const int per = tsz / kAggThreads;
         int mine = 0;
 #pragma unroll
-        for (int t = 0; t < kPer; ++t) mine += K[t * kAggThreads + threadIdx.x] != kNone ? 1 : 0;
+        for (int t = 0; t < kPer; ++t)
+            if (t < per) mine += K[t * kAggThreads + threadIdx.x] != kNone ? 1 : 0;
         const int off = mine ? atomicAdd(&s_cnt, mine) : 0;
         __syncthreads();
         if (threadIdx.x == 0) s_base = atomicAdd(n_out, s_cnt);
@@ -412,7 +471,7 @@ __global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
 #pragma unroll
         for (int t = 0; t < kPer; ++t) {
             const int sl = t * kAggThreads + threadIdx.x;
-            if (K[sl] != kNone) {
+            if (t < per && K[sl] != kNone) {
                 keys[o] = K[sl];
                 vals[o] = V[sl];
                 ++o;
@@ -480,14 +539,57 @@ __global__ void group_big_count_kernel(int n_list, const int32_t *__restrict__ l
 }
 
 // pack: row c = tmp[ga[c], ga[c] + cnt[c]) at off[c]; one warp per community
-__global__ void __launch_bounds__(256) group_pack_kernel(int n_next, const int32_t *__restrict__ ga,
-                                                         const int32_t *__restrict__ off,
+// A block per chunk of kPackArcs coarse arcs: the rows the chunk touches
+// are found by two searches of off, their starts loaded into shared memory,
+// and each arc's row by a search there (a global search when the chunk
+// touches more rows than that, i.e. many empty rows).  So a community with
+// 10^5 distinct neighbours is not copied by one warp, and a batch of small
+// ones does not search all of off per arc.
+constexpr int kPackArcs = 4096;
+__global__ void __launch_bounds__(512) group_pack_kernel(int n_next, const int32_t *__restrict__ ga,
+                                                         const int32_t *__restrict__ off, int A,
                                                          const int2 *__restrict__ tmp, int2 *arcs) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * 8;
-    for (int c = blockIdx.x * 8 + (threadIdx.x >> 5); c < n_next; c += nw) {
-        const int a0 = ga[c], o = off[c], d = off[c + 1] - o;
-        for (int x = lane; x < d; x += 32) arcs[o + x] = tmp[a0 + x];
+    __shared__ int so[kPackArcs + 1], sg[kPackArcs];
+    __shared__ int s_c0, s_nc;
+    for (int64_t e0 = (int64_t)blockIdx.x * kPackArcs; e0 < A; e0 += (int64_t)gridDim.x * kPackArcs) {
+        const int e1 = (int)min((int64_t)A, e0 + kPackArcs);
+        if (threadIdx.x < 2) {  // rows of the chunk's first and last arcs
+            const int e = threadIdx.x ? e1 - 1 : (int)e0;
+            int lo = 0, hi = n_next;  // off[lo] <= e < off[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (off[mid] <= e) lo = mid; else hi = mid;
+            }
+            if (threadIdx.x) s_nc = lo; else s_c0 = lo;
+        }
+        __syncthreads();
+        const int c0 = s_c0, nc = s_nc - s_c0 + 1;
+        const bool local = nc <= kPackArcs;
+        if (local)
+            for (int t = threadIdx.x; t <= nc; t += blockDim.x) {
+                so[t] = off[c0 + t];
+                if (t < nc) sg[t] = ga[c0 + t];
+            }
+        __syncthreads();
+        for (int e = (int)e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int lo, hi;
+            if (local) {
+                lo = 0, hi = nc;  // so[lo] <= e < so[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (so[mid] <= e) lo = mid; else hi = mid;
+                }
+                arcs[e] = tmp[sg[lo] + (e - so[lo])];
+            } else {
+                lo = 0, hi = n_next;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (off[mid] <= e) lo = mid; else hi = mid;
+                }
+                arcs[e] = tmp[ga[lo] + (e - off[lo])];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -563,6 +665,7 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     LV_TRY(t.get(&err, 1));
     LV_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     LV_CUDA(cudaMemsetAsync(tmp, 0, sizeof(int2) * (size_t)A, s));
+    trace_stamp(s, 20);
     // vertices grouped by coarse id (ascending id inside a group)
     cmap_kernel<<<grid_items(n), 256, 0, s>>>(n, C, newid, cm);
     LV_LAUNCH_CHECK();
@@ -591,10 +694,12 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     LV_CUDA(cudaStreamSynchronize(s));
     const int n_mid = pinned[0];
     int n_big = pinned[1], AL = 0;
+    trace_stamp(s, 21, (unsigned long long)n_mid << 32 | (unsigned)n_big);
     // small and medium communities
     group_warp_kernel<<<grid_for(n_next, kGrpWarps, g_num_sms * 16), kGrpWarps * 32, 0, s>>>(
         g, n_next, gs, ga, apos, vo, cm, tmp, cnt, err);
     LV_LAUNCH_CHECK();
+    trace_stamp(s, 22);
     if (n_mid > 0) {
         group_block_kernel<<<std::min(n_mid, g_num_sms * 4), kGrpBlockThreads, 0, s>>>(
             g, n_mid, list_mid, gs, ga, apos, vo, cm, tmp, cnt, err);
@@ -603,11 +708,13 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     // large communities: one block each while their distinct neighbours fit
     // its table; the others sort their arcs by (community, neighbour)
     if (n_big > 0) {
+        trace_stamp(s, 23);
         int32_t *fail = f_big;  // reused: one flag per community
         LV_CUDA(cudaMemsetAsync(fail, 0, sizeof(int32_t) * ((size_t)n_next + 1), s));
         group_big_kernel<<<std::min(n_big, g_num_sms * 4), kGrpBigThreads, 0, s>>>(
             g, n_big, list_big, gs, ga, vo, cm, tmp, cnt, fail);
         LV_LAUNCH_CHECK();
+        trace_stamp(s, 24);
         fail_arcs_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, ga, fail, big_arcs);
         LV_LAUNCH_CHECK();
         LV_TRY(scan_excl_i32(fail, pbig, n_next, s));
@@ -620,6 +727,7 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
         LV_CUDA(cudaStreamSynchronize(s));
         n_big = pinned[0];
         AL = pinned[1];
+        trace_stamp(s, 25, (unsigned long long)n_big << 32 | (unsigned)AL);
     }
     if (n_big > 0) {
         uint64_t *keys, *keys_alt;
@@ -629,11 +737,11 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
         LV_TRY(t.get(&keys_alt, (size_t)AL));
         LV_TRY(t.get(&vals, (size_t)AL));
         LV_TRY(t.get(&vals_alt, (size_t)AL));
-        int32_t *lstart;
-        LV_TRY(t.get(&lstart, (size_t)n_big + 1));
-        gather_idx_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big - 1, list_big, lpos, lstart);
+        int32_t *coff;  // first chunk of each listed community; coff[n_big] = all chunks
+        LV_TRY(t.get(&coff, (size_t)n_big + 1));
+        agg_chunks_kernel<<<grid_items(n_big), 256, 0, s>>>(n_big, list_big, ga, coff);
         LV_LAUNCH_CHECK();
-        LV_CUDA(cudaMemcpyAsync(lstart + n_big, &AL, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        LV_TRY(scan_excl_i32(coff, coff, n_big, s));
         int32_t *n_keys;
         LV_TRY(t.get(&n_keys, 1));
         LV_CUDA(cudaMemsetAsync(n_keys, 0, sizeof(int32_t), s));
@@ -644,13 +752,17 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
                                          (int)kAggSmem));
             agg_attr = true;
         }
-        group_keys_kernel<<<grid_for(AL, kAggArcs, g_num_sms * 2), kAggThreads, kAggSmem, s>>>(
-            g, n_big, list_big, lstart, AL, gs, ga, apos, vo, cm, b, keys, vals, n_keys, err);
+        group_keys_kernel<<<grid_for((int64_t)AL + (int64_t)n_big * kAggArcs, kAggArcs,
+                                     g_num_sms * 2),
+                            kAggThreads, kAggSmem, s>>>(g, n_big, list_big, coff, gs, ga, apos, vo,
+                                                        cm, b, keys, vals, n_keys, err);
         LV_LAUNCH_CHECK();
         LV_CUDA(cudaMemcpyAsync(pinned, n_keys, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         LV_CUDA(cudaStreamSynchronize(s));
         const int NK = pinned[0];
+        trace_stamp(s, 26, (unsigned)NK);
         LV_TRY(radix_sort_u64(keys, vals, keys_alt, vals_alt, NK, 2 * b, s));
+        trace_stamp(s, 27);
         int32_t *cstart, *cend;
         LV_TRY(t.get(&cstart, (size_t)n_next + 1));
         LV_TRY(t.get(&cend, (size_t)n_next + 1));
@@ -668,6 +780,7 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
                                                                  pos, cnt);
         LV_LAUNCH_CHECK();
     }
+    trace_stamp(s, 28);
     // pack the rows
     DGraph h;
     h.n = n_next;
@@ -682,9 +795,10 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
     }
     h.A = pinned[0];
     LV_TRY(dalloc_n(&h.arcs, (size_t)std::max(h.A, 1), s));
-    group_pack_kernel<<<grid_for(n_next, 8, g_num_sms * 16), 256, 0, s>>>(n_next, ga, h.off, tmp,
-                                                                           h.arcs);
+    group_pack_kernel<<<grid_for(h.A, kPackArcs, g_num_sms * 4), 512, 0, s>>>(n_next, ga, h.off,
+                                                                              h.A, tmp, h.arcs);
     LV_LAUNCH_CHECK();
+    trace_stamp(s, 29, (unsigned)h.A);
     *out = h;
     return LV_OK;
 }
