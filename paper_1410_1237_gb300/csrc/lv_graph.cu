@@ -202,8 +202,7 @@ __global__ void vf_rowlen_kernel(DGraph g, const int32_t *__restrict__ keep,
 // with the warp's ballots cut to the group's bits.
 constexpr int kVfLanes = 8;
 constexpr int kVfSmallRow = 64;
-__global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int32_t *__restrict__ keep,
-                                                            const int32_t *__restrict__ newid,
+__global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int32_t *__restrict__ nid,
                                                             const int32_t *__restrict__ loop,
                                                             const int32_t *__restrict__ extra,
                                                             const int32_t *__restrict__ off2,
@@ -221,10 +220,10 @@ __global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int3
         if (row) {
             beg = g.off[i];
             end = g.off[i + 1];
-            row = keep[i] && end - beg <= kVfSmallRow;
+            row = nid[i] >= 0 && end - beg <= kVfSmallRow;
         }
         if (!row) end = beg;
-        const int ni = row ? newid[i] : 0;
+        const int ni = row ? nid[i] : 0;
         const int ex = row ? extra[i] : 0;
         bool pending = row && loop[i] == 0 && ex > 0;  // self-loop to insert
         int run = row ? off2[ni] : 0;
@@ -234,7 +233,8 @@ __global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int3
             const int e = beg + t * kVfLanes + gl;
             const bool valid = e < end;
             const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
-            const bool kp = valid && (a.x == i || keep[a.x]);
+            const int nv = valid && a.x != i ? nid[a.x] : -1;  // new id, -1: removed
+            const bool kp = valid && (a.x == i || nv >= 0);
             const unsigned bk = (__ballot_sync(0xffffffffu, kp) >> gshift) & gbits;
             const unsigned bgt =
                 (__ballot_sync(0xffffffffu, pending && kp && a.x > i) >> gshift) & gbits;
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int3
             }
             if (kp) {
                 const int pos = run + __popc(bk & lt) + lsh;
-                arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
+                arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(nv, a.y);
             }
             run += __popc(bk);
         }
@@ -259,8 +259,7 @@ __global__ void __launch_bounds__(256) vf_fill_small_kernel(DGraph g, const int3
 // one warp per kept row of kVfSmallRow < arcs < kBigRow: drop arcs to
 // removed vertices, renumber, add the merged weight to the self-loop
 // (inserting it at its sorted place if absent)
-__global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *__restrict__ keep,
-                                                      const int32_t *__restrict__ newid,
+__global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *__restrict__ nid,
                                                       const int32_t *__restrict__ loop,
                                                       const int32_t *__restrict__ extra,
                                                       const int32_t *__restrict__ off2,
@@ -271,35 +270,52 @@ __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *_
     for (int64_t ii = blockIdx.x * 8 + (threadIdx.x >> 5); ii < g.n; ii += nw) {
         const int i = (int)ii;
         const int len = g.off[i + 1] - g.off[i];
-        if (!keep[i] || len >= kBigRow || len <= kVfSmallRow) continue;  // warp-uniform
-        const int ni = newid[i];
+        const int ni = nid[i];
+        if (ni < 0 || len >= kBigRow || len <= kVfSmallRow) continue;  // warp-uniform
         const int ex = extra[i];
         bool pending = (loop[i] == 0 && ex > 0);  // self-loop to insert
         int run = off2[ni];
         int sh = 0;  // 1 once the inserted loop precedes the current arcs
         const int beg = g.off[i], end = g.off[i + 1];
-        for (int base = beg; base < end; base += 32) {
-            const int e = base + lane;
-            const bool valid = e < end;
-            const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
-            const bool kp = valid && (a.x == i || keep[a.x]);
-            const unsigned bk = __ballot_sync(0xffffffffu, kp);
-            int lsh = sh;
-            if (pending) {
-                const unsigned bgt = __ballot_sync(0xffffffffu, kp && a.x > i);
-                if (bgt) {
-                    const int f = __ffs(bgt) - 1;
-                    if (lane == 0) arcs2[run + __popc(bk & ((1u << f) - 1u))] = make_int2(ni, ex);
-                    if (lane >= f) lsh = 1;
-                    pending = false;
-                    sh = 1;
+        for (int base0 = beg; base0 < end; base0 += 64) {
+            // two 32-arc chunks' loads in flight, then each chunk in order
+            int2 a2[2];
+            int nv2[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int e = base0 + 32 * h + lane;
+                a2[h] = e < end ? g.arcs[e] : make_int2(-1, 0);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)  // new id, -1: removed
+                nv2[h] = a2[h].x >= 0 && a2[h].x != i ? nid[a2[h].x] : -1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int base = base0 + 32 * h;
+                if (base >= end) break;  // warp-uniform
+                const bool valid = base + lane < end;
+                const int2 a = a2[h];
+                const int nv = nv2[h];
+                const bool kp = valid && (a.x == i || nv >= 0);
+                const unsigned bk = __ballot_sync(0xffffffffu, kp);
+                int lsh = sh;
+                if (pending) {
+                    const unsigned bgt = __ballot_sync(0xffffffffu, kp && a.x > i);
+                    if (bgt) {
+                        const int f = __ffs(bgt) - 1;
+                        if (lane == 0)
+                            arcs2[run + __popc(bk & ((1u << f) - 1u))] = make_int2(ni, ex);
+                        if (lane >= f) lsh = 1;
+                        pending = false;
+                        sh = 1;
+                    }
                 }
+                if (kp) {
+                    const int pos = run + __popc(bk & lt) + lsh;
+                    arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(nv, a.y);
+                }
+                run += __popc(bk);
             }
-            if (kp) {
-                const int pos = run + __popc(bk & lt) + lsh;
-                arcs2[pos] = (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
-            }
-            run += __popc(bk);
         }
         if (pending && lane == 0) arcs2[run + sh] = make_int2(ni, ex);
     }
@@ -307,10 +323,9 @@ __global__ void __launch_bounds__(256) vf_fill_kernel(DGraph g, const int32_t *_
 
 // the same for kept rows of at least kBigRow arcs, one 1024-thread block each:
 // positions come from a block-wide prefix over the kept flags of each chunk
-__global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32_t *__restrict__ keep,
+__global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32_t *__restrict__ nid,
                                                            const int32_t *__restrict__ list,
                                                            const int32_t *__restrict__ count,
-                                                           const int32_t *__restrict__ newid,
                                                            const int32_t *__restrict__ loop,
                                                            const int32_t *__restrict__ extra,
                                                            const int32_t *__restrict__ off2,
@@ -322,7 +337,7 @@ __global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32
     for (int t = blockIdx.x; t < nbig; t += gridDim.x) {
         const int i = list[t];
         const int beg = g.off[i], end = g.off[i + 1];
-        const int ni = newid[i];
+        const int ni = nid[i];
         const int ex = extra[i];
         bool pending = (loop[i] == 0 && ex > 0);
         int run = off2[ni];
@@ -331,7 +346,8 @@ __global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32
             const int e = base + (int)threadIdx.x;
             const bool valid = e < end;
             const int2 a = valid ? g.arcs[e] : make_int2(-1, 0);
-            const bool kp = valid && (a.x == i || keep[a.x]);
+            const int nv = valid && a.x != i ? nid[a.x] : -1;  // new id, -1: removed
+            const bool kp = valid && (a.x == i || nv >= 0);
             const unsigned wb = __ballot_sync(0xffffffffu, kp);
             if (lane == 0) s_wcnt[w] = __popc(wb);
             if (threadIdx.x == 0) s_first = 1 << 30;
@@ -355,7 +371,7 @@ __global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32
                 if ((int)threadIdx.x >= s_first) lsh = 1;
             }
             if (kp) arcs2[run + rank + lsh] =
-                (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(newid[a.x], a.y);
+                (a.x == i) ? make_int2(ni, a.y + ex) : make_int2(nv, a.y);
             if (pending && s_first < (1 << 30)) {
                 pending = false;
                 sh = 1;
@@ -366,6 +382,13 @@ __global__ void __launch_bounds__(1024) vf_fill_big_kernel(DGraph g, const int32
         if (pending && threadIdx.x == 0) arcs2[run + sh] = make_int2(ni, ex);
         __syncthreads();
     }
+}
+
+// nid[v] = new id of v, -1 if v is removed
+__global__ void vf_nid_kernel(int32_t n, const int32_t *__restrict__ keep,
+                              const int32_t *__restrict__ newid, int32_t *nid) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        nid[v] = keep[v] ? newid[v] : -1;
 }
 
 __global__ void vf_map_kernel(int32_t n, const int32_t *__restrict__ keep,
@@ -573,22 +596,27 @@ lv_status vertex_following(const DGraph &g, const int32_t *loop, DGraph *out, in
     LV_CUDA(cudaStreamSynchronize(s));
     h.A = scratch_pinned[0];
     LV_TRY(dalloc_n(&h.arcs, (size_t)h.A, s));
-    vf_fill_small_kernel<<<grid_rows((n + 3) / 4), 256, 0, s>>>(g, keep, newid, loop, extra, h.off,
-                                                                h.arcs);
+    // new id of every vertex, -1 for the removed: one gather per arc
+    int32_t *nid = nullptr;
+    LV_TRY(dalloc_n(&nid, (size_t)n, s));
+    vf_nid_kernel<<<grid_items(n), 256, 0, s>>>(n, keep, newid, nid);
     LV_LAUNCH_CHECK();
-    vf_fill_kernel<<<grid_rows(n), 256, 0, s>>>(g, keep, newid, loop, extra, h.off, h.arcs);
+    vf_fill_small_kernel<<<grid_rows((n + 3) / 4), 256, 0, s>>>(g, nid, loop, extra, h.off, h.arcs);
+    LV_LAUNCH_CHECK();
+    vf_fill_kernel<<<grid_rows(n), 256, 0, s>>>(g, nid, loop, extra, h.off, h.arcs);
     LV_LAUNCH_CHECK();
     int32_t *big = nullptr;
     LV_TRY(dalloc_n(&big, (size_t)g.A / kBigRow + 2, s));
     LV_CUDA(cudaMemsetAsync(big, 0, sizeof(int32_t), s));
     big_rows_kernel<<<grid_items(n), 256, 0, s>>>(g, keep, big + 1, big);
     LV_LAUNCH_CHECK();
-    vf_fill_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, keep, big + 1, big, newid, loop, extra,
-                                                      h.off, h.arcs);
+    vf_fill_big_kernel<<<g_num_sms * 2, 1024, 0, s>>>(g, nid, big + 1, big, loop, extra, h.off,
+                                                      h.arcs);
     LV_LAUNCH_CHECK();
     dfree(big, s);
     vf_map_kernel<<<grid_items(n), 256, 0, s>>>(n, keep, newid, target, map);
     LV_LAUNCH_CHECK();
+    dfree(nid, s);
     dfree(d1, s);
     dfree(keep, s);
     dfree(target, s);
