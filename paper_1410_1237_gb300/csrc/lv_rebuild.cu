@@ -62,6 +62,7 @@ constexpr int kGrpBigSlots = 4096;
 constexpr int kGrpBigDistinct = kGrpBigSlots / 2;
 constexpr int kGrpBigThreads = 512;
 constexpr int kGrpBigArcs = 1 << 16;
+constexpr int kGrpBigChunk = 2048;  // arcs per step of a large community
 
 __global__ void group_starts_kernel(int n, const uint32_t *__restrict__ cm_sorted, int n_next,
                                     int32_t *gs) {
@@ -244,12 +245,14 @@ __global__ void __launch_bounds__(kGrpBlockThreads) group_block_kernel(
 // community goes to the sort of its arcs.
 __global__ void __launch_bounds__(kGrpBigThreads) group_big_kernel(
     DGraph g, int n_list, const int32_t *__restrict__ list, const int32_t *__restrict__ gs,
-    const int32_t *__restrict__ ga, const uint32_t *__restrict__ vo,
-    const uint32_t *__restrict__ cm, int2 *tmp, int32_t *cnt, int32_t *fail) {
+    const int32_t *__restrict__ ga, const int32_t *__restrict__ apos,
+    const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm, int2 *tmp, int32_t *cnt,
+    int32_t *fail) {
     // the table (keys, then values) and, once its entries are in registers,
     // the sort buffer of up to kGrpBigDistinct packed (key, value) pairs
     __shared__ unsigned long long KV[kGrpBigSlots];
-    __shared__ int s_d, s_over;
+    __shared__ int mo[kGrpBigChunk + 1];  // arc starts of the chunk's members
+    __shared__ int s_d, s_over, s_mlo, s_nm;
     int *K = reinterpret_cast<int *>(KV), *V = K + kGrpBigSlots;
     unsigned long long *S = KV;
     static_assert(2 * kGrpBigSlots * sizeof(int) == sizeof(KV) && kGrpBigDistinct <= kGrpBigSlots,
@@ -273,12 +276,40 @@ __global__ void __launch_bounds__(kGrpBigThreads) group_big_kernel(
             s_over = 0;
         }
         __syncthreads();
-        for (int m = m0 + w; m < m1; m += kWarps) {
-            if (((volatile int *)&s_over)[0]) break;  // warp-uniform (one read per row)
-            const int u = (int)vo[m];
-            const int beg = g.off[u], end = g.off[u + 1];
-            for (int e = beg + lane; e < end; e += 32) {
-                const int2 a = g.arcs[e];
+        // the community's arcs in chunks of kGrpBigChunk, one thread per arc:
+        // its member by a search of the chunk's members' arc starts in
+        // shared memory (a warp per member row idled on rows of a few arcs)
+        const int a1 = ga[c + 1];
+        for (int p0 = a0; p0 < a1; p0 += kGrpBigChunk) {
+            const int p1 = min(a1, p0 + kGrpBigChunk);
+            if (threadIdx.x < 2) {  // members holding positions p0 and p1 - 1
+                const int p = threadIdx.x ? p1 - 1 : p0;
+                int l = m0, h = m1;  // apos[l] <= p < apos[h]
+                while (h - l > 1) {
+                    const int mid = (l + h) >> 1;
+                    if (apos[mid] <= p) l = mid; else h = mid;
+                }
+                if (threadIdx.x) s_nm = l; else s_mlo = l;
+            }
+            __syncthreads();
+            const int mlo = s_mlo, nm = s_nm + 1 - s_mlo;
+            const bool local = nm <= kGrpBigChunk;  // else members without arcs
+            if (local)
+                for (int t = threadIdx.x; t <= nm; t += kGrpBigThreads) mo[t] = apos[mlo + t];
+            __syncthreads();
+            for (int p = p0 + (int)threadIdx.x; p < p1; p += kGrpBigThreads) {
+                int2 a;
+                if (local) {
+                    int l = 0, h = nm;  // mo[l] <= p < mo[h]
+                    while (h - l > 1) {
+                        const int mid = (l + h) >> 1;
+                        if (mo[mid] <= p) l = mid; else h = mid;
+                    }
+                    const int u = (int)vo[mlo + l];
+                    a = g.arcs[g.off[u] + (p - mo[l])];
+                } else {
+                    a = group_arc(g, vo, apos, m0, m1, a0, p - a0);
+                }
                 const int cv = (int)cm[a.x];
                 unsigned h = hash32(cv) & (kGrpBigSlots - 1);
                 bool done = false;
@@ -294,6 +325,8 @@ __global__ void __launch_bounds__(kGrpBigThreads) group_big_kernel(
                 }
                 if (!done) s_over = 1;
             }
+            __syncthreads();
+            if (s_over) break;  // block-uniform after the barrier
         }
         __syncthreads();
         if (s_over) {  // block-uniform
@@ -712,7 +745,7 @@ lv_status coarsen(const DGraph &g, const int32_t *C, const int32_t *newid, int32
         int32_t *fail = f_big;  // reused: one flag per community
         LV_CUDA(cudaMemsetAsync(fail, 0, sizeof(int32_t) * ((size_t)n_next + 1), s));
         group_big_kernel<<<std::min(n_big, g_num_sms * 4), kGrpBigThreads, 0, s>>>(
-            g, n_big, list_big, gs, ga, vo, cm, tmp, cnt, fail);
+            g, n_big, list_big, gs, ga, apos, vo, cm, tmp, cnt, fail);
         LV_LAUNCH_CHECK();
         trace_stamp(s, 24);
         fail_arcs_kernel<<<grid_items(n_next), 256, 0, s>>>(n_next, ga, fail, big_arcs);
