@@ -48,17 +48,17 @@ SWEEP_SOURCES = ("lv_sweep.cu", "lv_ops.cuh", "lv_internal.cuh", "lv_engine.cuh"
 # entry no longer applies and the line reports traffic as null.
 MEASURED_TRAFFIC: dict = {
     # sweep_persistent_kernel on chunglu20 (2^20-vertex member of the Chung-Lu
-    # family), phase-0 iteration 2: 354,168,064 + 36,743,936 B against
+    # family), phase-0 iteration 2: 354,682,368 + 39,672,832 B against
     # 369,528,704 algorithmic (12 x 29,082,750 arcs + 28 x 733,418 vertices);
     # applied to a phase-0 launch of the 2^24-vertex graph by that ratio
-    "chunglu24": {"sources": "996b16eaa8776618", "ratio": 390_912_000 / 369_528_704,
+    "chunglu24": {"sources": "80dff76642570e5e", "ratio": 394_355_200 / 369_528_704,
                   "scope": "one phase-0 sweep launch, scaled by units from a capture of a "
-                           "2^20-vertex Chung-Lu phase-0 launch (ratio 1.058)"},
-    # the batched sweep on 512 planted graphs, phase-0 sweep 7 (324 graphs
-    # iterating): 265,677,568 + 16,336,128 B against 230,483,328 algorithmic
-    # (12 x 16,401,407 arcs + 28 x 1,202,373 vertices)
-    "planted_batch4096": {"sources": "996b16eaa8776618",
-                          "ratio": 282_013_696 / 230_483_328,
+                           "2^20-vertex Chung-Lu phase-0 launch (ratio 1.067)"},
+    # the batched sweep on 512 planted graphs, phase-0 sweep 9 (262 graphs
+    # iterating): 261,973,504 + 16,466,688 B against 227,837,952 algorithmic
+    # (12 x 16,233,207 arcs + 28 x 1,179,981 vertices)
+    "planted_batch4096": {"sources": "80dff76642570e5e",
+                          "ratio": 278_440_192 / 227_837_952,
                           "scope": "one phase-0 sweep launch of all 4,096 graphs, scaled by "
                                    "units from a 512-graph capture (ratio 1.22)"},
 }
