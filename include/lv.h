@@ -131,7 +131,8 @@ typedef struct {
     int32_t colored;    /* 1 if the phase swept colour classes */
     int32_t num_colors; /* colour classes (0 if not coloured) */
     int32_t iterations; /* iterations of Alg. 1's while-loop */
-    int32_t color_rounds; /* rounds of the Jones-Plassmann colouring (0 if not coloured) */
+    int32_t color_rounds; /* Jones-Plassmann rounds after the degree core (coloured first,
+                             without rounds); 0 if not coloured */
     double ms_color;    /* CUDA-event times (collect_timing), else -1 */
     double ms_iterate;
     double ms_rebuild;
