@@ -231,6 +231,17 @@ def test_colouring_core_without_rounds(lv, case):
         assert res.phases[0].colored
 
 
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("graph", ["rmat16", "hubs"])
+def test_colour_orders(lv, order, graph):
+    """Both colouring priorities (R11) against the oracle: largest degree
+    first (its degree core coloured before the rounds) and hash only (no
+    core: rounds alone)."""
+    g = gg.rmat(16, 8, seed=33) if graph == "rmat16" else _core_graph("hubs")
+    res, ref = compare(lv, g, graphs=True, color_cutoff=0, color_order=order)
+    assert res.phases[0].colored
+
+
 def test_variant_colour_phase_theta(lv):
     g = gg.rmat(16, 8, seed=32)
     compare(lv, g, graphs=False, color_cutoff=0, theta_high=1e-4)
