@@ -9,9 +9,16 @@
 // decrements the counts of its lower-priority neighbours.  The result equals
 // greedy colouring in decreasing priority order, whatever the timing, because
 // a vertex's colour depends only on its higher-priority neighbours' colours.
-// On power-law graphs the priority DAG is deep (1,600 to 3,800 rounds on the
-// R-MAT and Chung-Lu inputs), so all rounds run inside one cooperative launch
-// separated by a bounded grid barrier.  Ready vertices are handled by size:
+// On power-law graphs the priority DAG is deep (1,500 to 3,500 levels on the
+// R-MAT and Chung-Lu inputs), and almost all of its depth lies among the
+// largest vertices.  With the degree first in the priority, the vertices of
+// degree >= T form a prefix of the priority order (their higher-priority
+// neighbours are all among them): this core is coloured first without rounds
+// (sorted by priority, each vertex waiting for its earlier neighbours; the
+// top of it on one thread-block cluster with the colours in distributed
+// shared memory, the rest on the grid), and the other vertices in rounds,
+// all inside one cooperative launch separated by a bounded grid barrier
+// (about 20-30 rounds on those inputs).  Ready vertices are handled by size:
 // small (< 256 arcs) one warp each; big (< 4,096 arcs) one block each; huge
 // ones are split over the blocks left over, which mark a shared global colour
 // bitmap; the last of them to finish computes the colour; tiny ones (at
