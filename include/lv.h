@@ -286,6 +286,17 @@ lv_status lv_modularity_noalloc(int64_t n, const int64_t *rowptr, const int32_t 
                                 const int32_t *w, const int32_t *labels, int64_t *num_hi,
                                 uint64_t *num_lo, int64_t *den, void *cuda_stream);
 
+/* Check of the bounded device waits (every grid barrier and wait of the
+ * persistent kernels gives up after a bounded number of polls, raises an
+ * error flag and returns, so a fault cannot hang the GPU): launches four
+ * blocks on the current device whose block 0 never arrives at their grid
+ * barrier; the other three give up after `polls` polls of the barrier word
+ * and raise the wait flag.  Returns LV_ERR_TIMEOUT when they did (the
+ * expected result; the device stays usable), LV_ERR_STATE if the barrier
+ * completed anyway, LV_ERR_ARG for polls outside [1, 2^24], LV_ERR_CUDA on
+ * a CUDA error.  Synchronises the current device's default stream. */
+lv_status lv_check_bounded_wait(int32_t polls);
+
 /* Static description of a status code. */
 const char *lv_status_string(lv_status s);
 

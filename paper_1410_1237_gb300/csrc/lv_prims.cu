@@ -307,6 +307,53 @@ lv_status radix_sort_u32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uin
 
 extern "C" const char *lv_last_error(void) { return lv::t_last_error; }
 
+namespace lv {
+namespace {
+// The grid barrier's wait (arrive with a release add on the one-word
+// barrier, poll it with acquire loads, give up after `limit` polls and raise
+// flag 1; see grid_sync) with block 0 never arriving.
+__global__ void wait_check_kernel(GridBarrier *bar, unsigned long long limit) {
+    if (blockIdx.x == 0) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long target = gridDim.x;  // the first barrier of the launch
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(&bar->word) : "memory");
+        for (unsigned long long spins = 0;;) {
+            unsigned long long w;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(&bar->word) : "memory");
+            if (w >> kBarrierFlagShift) break;
+            if ((w & kBarrierCountMask) >= target) break;
+            if (++spins > limit) {
+                barrier_raise(bar, 1);
+                break;
+            }
+            __nanosleep(20);
+        }
+    }
+    __syncthreads();
+}
+}  // namespace
+}  // namespace lv
+
+extern "C" lv_status lv_check_bounded_wait(int32_t polls) {
+    using namespace lv;
+    if (polls < 1 || polls > (1 << 24)) return LV_ERR_ARG;
+    GridBarrier *bar = nullptr;
+    LV_CUDA(cudaMalloc(&bar, sizeof(GridBarrier)));
+    lv_status st = LV_OK;
+    GridBarrier h;
+    if (cudaMemset(bar, 0, sizeof(GridBarrier)) != cudaSuccess) st = LV_ERR_CUDA;
+    if (st == LV_OK) {
+        wait_check_kernel<<<4, 32>>>(bar, (unsigned long long)polls);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy(&h, bar, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = LV_ERR_CUDA;
+    }
+    cudaFree(bar);
+    if (st != LV_OK) return st;
+    return (barrier_flags(h) & 1) ? LV_ERR_TIMEOUT : LV_ERR_STATE;
+}
+
 #ifdef LV_TRACE
 namespace lv {
 namespace {

@@ -124,6 +124,7 @@ SIGNATURES = {
     "lv_params_default": (None, [_P(lv_params)]),
     "lv_graph_create": (ctypes.c_int, [_P(_vp), ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "lv_run": (ctypes.c_int, [_vp, _P(lv_params)]),
+    "lv_check_bounded_wait": (ctypes.c_int, [ctypes.c_int32]),
     "lv_num_phases": (ctypes.c_int, [_vp, _P(ctypes.c_int32)]),
     "lv_get_labels": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int]),
     "lv_get_modularity": (ctypes.c_int, [_vp, ctypes.c_int32, _P(ctypes.c_double),
@@ -342,6 +343,11 @@ def lv_modularity_noalloc(n: int, rowptr, col, w, labels, stream: int = 0) -> tu
                                         ctypes.byref(lo), ctypes.byref(den), stream or None),
            "lv_modularity_noalloc")
     return (hi.value << 64) | lo.value, den.value
+
+
+def lv_check_bounded_wait(polls: int = 10_000) -> int:
+    """Status of the bounded-wait check (LV_ERR_TIMEOUT expected)."""
+    return int(load().lv_check_bounded_wait(int(polls)))
 
 
 def lv_compare_partitions(labels_s, labels_p, stream: int = 0) -> dict:

@@ -93,3 +93,10 @@ def test_server_rejects_bad_config_without_gpu():
     cfg.params = lv.make_params()
     cfg.max_graphs = -1
     assert lv.load().lv_server_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1
+
+
+def test_bounded_wait_check_rejects_bad_polls_without_gpu():
+    from paper_1410_1237_gb300 import lv
+    lv.load()
+    for polls in (0, -1, (1 << 24) + 1):
+        assert lv.lv_check_bounded_wait(polls) == -1  # LV_ERR_ARG, before any GPU work
