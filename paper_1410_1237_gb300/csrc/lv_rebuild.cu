@@ -396,8 +396,7 @@ __global__ void fail_arcs_kernel(int n_next, const int32_t *__restrict__ ga,
 constexpr int kAggArcs = 4096;
 constexpr int kAggSlots = 2 * kAggArcs;
 constexpr int kAggThreads = 512;
-constexpr size_t kAggSmem =
-    kAggSlots * (sizeof(unsigned long long) + sizeof(unsigned)) + (kAggArcs + 1) * sizeof(int);
+constexpr size_t kAggSmem = kAggSlots * 2 * sizeof(unsigned) + (kAggArcs + 1) * sizeof(int);
 
 // chunks of kAggArcs arcs of each listed community
 __global__ void agg_chunks_kernel(int n_list, const int32_t *__restrict__ list,
@@ -413,13 +412,16 @@ __global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
     const int32_t *__restrict__ gs, const int32_t *__restrict__ ga,
     const int32_t *__restrict__ apos, const uint32_t *__restrict__ vo, const uint32_t *__restrict__ cm,
     int b, uint64_t *keys, uint32_t *vals, int32_t *n_out, int *err) {
-    extern __shared__ unsigned long long agg[];
-    unsigned long long *K = agg;
-    unsigned *V = reinterpret_cast<unsigned *>(agg + kAggSlots);
+    // a chunk's arcs all belong to one community, so the table keys are the
+    // neighbours' communities alone (32 bits); the 64-bit key is formed on
+    // the way out
+    extern __shared__ unsigned agg[];
+    unsigned *K = agg;
+    unsigned *V = agg + kAggSlots;
     int *mo = reinterpret_cast<int *>(V + kAggSlots);  // arc starts of the chunk's members
     __shared__ int s_cnt, s_base, s_c, s_p0, s_p1, s_m0, s_nm;
     constexpr int kPer = kAggSlots / kAggThreads;
-    constexpr unsigned long long kNone = ~0ull;  // keys are below 2^62
+    constexpr unsigned kNone = ~0u;  // community ids are below 2^31
     const int n_chunks = coff[n_list];
     for (int chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
         if (threadIdx.x == 0) {
@@ -477,11 +479,11 @@ __global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
             } else {
                 a = group_arc(g, vo, apos, gs[c], gs[c + 1], ga[c], p - ga[c]);
             }
-            const unsigned long long key = ((unsigned long long)c << b) | cm[a.x];
-            unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & tmask;
+            const unsigned key = cm[a.x];
+            unsigned h = hash32((int)key) & tmask;
             bool done = false;
             for (int probe = 0; probe < tsz && !done; ++probe) {
-                const unsigned long long prev = atomicCAS(&K[h], kNone, key);
+                const unsigned prev = atomicCAS(&K[h], kNone, key);
                 if (prev == kNone || prev == key) {
                     atomicAdd(&V[h], (unsigned)a.y);
                     done = true;
@@ -505,7 +507,7 @@ __global__ void __launch_bounds__(kAggThreads) group_keys_kernel(
         for (int t = 0; t < kPer; ++t) {
             const int sl = t * kAggThreads + threadIdx.x;
             if (t < per && K[sl] != kNone) {
-                keys[o] = K[sl];
+                keys[o] = ((unsigned long long)c << b) | K[sl];
                 vals[o] = V[sl];
                 ++o;
             }
