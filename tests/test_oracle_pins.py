@@ -332,6 +332,64 @@ def _independent_greedy_colouring(g, seed, order=0):
     return col
 
 
+def _core_first_colouring(g, seed, T):
+    # The GPU's schedule restated in Python: the vertices with at least T
+    # neighbours other than themselves, in decreasing priority, each taking
+    # the smallest colour free among its coloured neighbours; then rounds
+    # over the others (a vertex is ready once its higher-priority neighbours
+    # are coloured; a round colours all ready vertices at once).
+    M = (1 << 64) - 1
+
+    def h(x):
+        x = ((x ^ (x >> 30)) * 0xBF58476D1CE4E5B9) & M
+        x = ((x ^ (x >> 27)) * 0x94D049BB133111EB) & M
+        return x ^ (x >> 31)
+
+    nb = [[u for u in g.col[g.rowptr[v]:g.rowptr[v + 1]] if u != v] for v in range(g.n)]
+    pr = [(len(nb[v]), h(v ^ seed), v) for v in range(g.n)]
+    higher = [[u for u in nb[v] if pr[u] > pr[v]] for v in range(g.n)]
+    col = [-1] * g.n
+
+    def mex(v):
+        used = {col[u] for u in higher[v]}
+        c = 0
+        while c in used:
+            c += 1
+        return c
+
+    core = sorted((v for v in range(g.n) if len(nb[v]) >= T), key=lambda v: pr[v], reverse=True)
+    incore = set(core)
+    for v in core:
+        assert all(u in incore for u in higher[v])  # the core is a prefix of the order
+        assert all(col[u] >= 0 for u in higher[v])
+        col[v] = mex(v)
+    rest = [v for v in range(g.n) if v not in incore]
+    rounds = 0
+    while rest:
+        ready = [v for v in rest if all(col[u] >= 0 for u in higher[v])]
+        assert ready
+        for v in ready:
+            col[v] = mex(v)
+        done = set(ready)
+        rest = [v for v in rest if v not in done]
+        rounds += 1
+    return col, rounds
+
+
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("T", [2, 8, 32, 1 << 20])
+def test_core_first_schedule_gives_the_oracle_colouring(seed, T):
+    """Colouring a degree core first (without rounds) and the rest by rounds
+    gives the colouring of the priority order: the largest-degree-first
+    priority makes the core a prefix of that order."""
+    g = gg.rmat(9, 8, seed=40 + seed)
+    K, c = oracle.color(g.rowptr, g.col, 91 + seed, 0)
+    got, rounds = _core_first_colouring(g, 91 + seed, T)
+    assert got == list(c)
+    if T == 2:  # nearly everything in the core: few rounds remain
+        assert rounds <= 3
+
+
 @pytest.mark.parametrize("seed", range(4))
 @pytest.mark.parametrize("order", [0, 1])
 def test_colouring_matches_independent_greedy(seed, order):
