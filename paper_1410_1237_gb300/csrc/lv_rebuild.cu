@@ -257,9 +257,7 @@ __global__ void __launch_bounds__(kGrpBigThreads) group_big_kernel(
     unsigned long long *S = KV;
     static_assert(2 * kGrpBigSlots * sizeof(int) == sizeof(KV) && kGrpBigDistinct <= kGrpBigSlots,
                   "table and sort buffer share the array");
-    constexpr int kWarps = kGrpBigThreads / 32;
     constexpr int kPer = kGrpBigSlots / kGrpBigThreads;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int li = blockIdx.x; li < n_list; li += gridDim.x) {
         const int c = list[li];
         const int a0 = ga[c], m0 = gs[c], m1 = gs[c + 1];
